@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark of the TPA hot path on one GB300 (or N replicas).
+
+Workload (one step): R-MAT scale 22 (4,194,304 nodes, 67,108,864 raw edges,
+a/b/c/d = .57/.19/.19/.05, key 1; self-loops dropped and duplicates merged by
+the graph builder), c = 0.15, S = 5, T = 10, eps = 1e-9:
+  1. build the row-normalised CSR of A~^T and A~ from the edge list (resident in HBM),
+  2. TPA preprocessing (Algorithm 2: PageRank CPI, stranger part from T on),
+  3. 1,000 single-seed TPA queries (Algorithm 3), seeds uniform over nodes
+     with an out-edge (key 2), answered in batches.
+value = seeds answered per second over whole steps (all ranks).  Each rank is an
+independent replica with its own 1,000 seeds (weak scaling, no data-path
+collective).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (one query per step plus its 1/1000 share of the oracle's measured
+build and preprocessing time).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "TPA seeds/s and SpMV HBM GB/s vs peak, batched vs per-seed CPI at L1≤1e-5"
+C, S, T, EPS = 0.15, 5, 10, 1e-9
+WORKLOAD = "TPA preprocessing + 1000 single-seed queries on R-MAT scale 22 (ef 16), c=0.15 S=5 T=10 eps=1e-9"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--edge-factor", type=int, default=16)
+    ap.add_argument("--queries", type=int, default=1000)
+    ap.add_argument("--batch", type=int, default=0, help="seeds per tpa_query call (0 = all at once)")
+    ap.add_argument("--cpi-seeds", type=int, default=8, help="seeds for the per-seed exact CPI comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------ multi-rank ---
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def shard_seeds(all_seeds, rank: int, world: int, per_rank: int):
+    """Rank r answers seeds [r*per_rank, (r+1)*per_rank) of one global seed stream."""
+    return all_seeds[rank * per_rank:(rank + 1) * per_rank]
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks ---
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.dev = device_id
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-i", self.dev, "-lms", "200"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.p.terminate()
+        try:
+            out = self.p.communicate(timeout=10)[0]
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out = self.p.communicate()[0]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def nvsmi_device_id() -> str:
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(torch.cuda.current_device())
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return "0"
+
+
+# -------------------------------------------------------------- roofline ---
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("cpi.cu", "tpa_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1708_02574_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, variant: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel source.
+
+    profiles/ncu_traffic.txt lines: kernel variant source_hash bytes_per_launch workload..."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = kernel_source_hash()
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == variant and f[2] == cur:
+            return float(f[3])
+    return None
+
+
+# ------------------------------------------------------------ reference ---
+def run_reference(args):
+    """FP64 oracle on the host cores, bounded sample of the same workload."""
+    import numpy as np
+    import oracle
+    import synth
+    n = 1 << args.scale
+    src, dst = synth.rmat_edges(args.scale, args.edge_factor)
+    cand = synth.nodes_with_out_edge(n, src, dst)
+    seeds = synth.query_seeds(cand, args.queries)
+    t0 = time.perf_counter()
+    og = oracle.build_graph(n, src, dst)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rs, pre_it = oracle.preprocess(og, C, T, EPS)
+    t_pre = time.perf_counter() - t0
+    share = (t_build + t_pre) / args.queries
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.query(og, int(seeds[i % len(seeds)]), C, S, T, rs, EPS)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt + share)
+    total = sum(times)
+    value = len(times) / total
+    sample = (f"per step: 1 oracle TPA query (4 SpMV over m={og.m}) plus 1/{args.queries} of the oracle's "
+              f"measured CSR build ({t_build:.1f} s) and preprocessing ({t_pre:.1f} s, {pre_it} iterations)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": n, "m": og.m, "queries": args.queries},
+            "cpu_baseline": {"value": value, "unit": "seeds/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "seeds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- ours ---
+def cpu_baseline(args, src, dst, seeds, gpu_pre_iters):
+    """Time the oracle as it stands on a bounded sample: full CSR build, 3 preprocessing
+    iterations (scaled to the iteration count), 2 queries (scaled to the query count)."""
+    import numpy as np
+    import oracle
+    n = 1 << args.scale
+    t0 = time.perf_counter()
+    og = oracle.build_graph(n, src, dst)
+    t_build = time.perf_counter() - t0
+    q = np.full(n, 1.0 / n)
+    t0 = time.perf_counter()
+    oracle.cpi(og, q, C, EPS, T, 3)
+    t_it = (time.perf_counter() - t0) / 3
+    rs = np.zeros(n)
+    t0 = time.perf_counter()
+    for sd in seeds[:2]:
+        oracle.query(og, int(sd), C, S, T, rs, EPS)
+    t_q = (time.perf_counter() - t0) / 2
+    est = t_build + gpu_pre_iters * t_it + args.queries * t_q
+    return {"value": args.queries / est, "unit": "seeds/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle CSR build timed in full ({t_build:.1f} s); 3 preprocessing iterations timed "
+                       f"({t_it:.2f} s each) and scaled to {gpu_pre_iters}; 2 queries timed ({t_q:.2f} s each) "
+                       f"and scaled to {args.queries}")}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return 0
+
+    import numpy as np
+    import torch
+    import synth
+    import paper_1708_02574_gb300 as tpa
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = 1 << args.scale
+    src, dst = synth.rmat_edges(args.scale, args.edge_factor)
+    cand = synth.nodes_with_out_edge(n, src, dst)
+    all_seeds = synth.query_seeds(cand, args.queries * world)
+    seeds = shard_seeds(all_seeds, rank, world, args.queries)
+    Q = len(seeds)
+    src_d = torch.from_numpy(src).cuda()
+    dst_d = torch.from_numpy(dst).cuda()
+    seeds_d = torch.from_numpy(seeds).cuda()
+    out_d = torch.empty((n, Q), dtype=torch.float32, device="cuda")
+    batch = args.batch if args.batch > 0 else Q
+
+    def step():
+        g = tpa.build_graph(n, src_d, dst_d)
+        tpa.preprocess(g, C, T, EPS)
+        if batch >= Q:
+            tpa.query(g, seeds_d, S, out=out_d)
+        else:
+            for j0 in range(0, Q, batch):
+                tpa.query(g, seeds_d[j0:j0 + batch], S, out=torch.empty((n, min(batch, Q - j0)),
+                                                                          dtype=torch.float32, device="cuda"))
+        g.free()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(nvsmi_device_id()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    tpa.profile_reset(timing=True)
+    l0 = tpa.launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = tpa.launch_count() - l0
+    stats = tpa.profile_read()
+    tpa.profile_reset(timing=False)
+    clk = clocks.stop() if clocks else None
+    t_rank = e0.elapsed_time(e1) / 1000.0
+    t = max_over_ranks(t_rank, world)
+    value = Q * world * args.steps / t
+
+    # phase breakdown and per-seed exact CPI on the same GPU (untimed by the contract)
+    g = tpa.build_graph(n, src_d, dst_d)
+    m = g.m
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    g.free()
+    g = tpa.build_graph(n, src_d, dst_d)
+    ev[1].record(stream)
+    tpa.preprocess(g, C, T, EPS)
+    ev[2].record(stream)
+    tpa.query(g, seeds_d, S, out=out_d)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    _, pre_iters = tpa.get_stranger(g)
+    phases = {"build": ev[0].elapsed_time(ev[1]), "preprocess": ev[1].elapsed_time(ev[2]),
+              "queries": ev[2].elapsed_time(ev[3])}
+    cpi_seeds = seeds[:args.cpi_seeds]
+    tpa.cpi_exact(g, int(cpi_seeds[0]), C, EPS)
+    torch.cuda.synchronize()
+    c0 = time.perf_counter()
+    for sd in cpi_seeds:
+        tpa.cpi_exact(g, int(sd), C, EPS)
+    torch.cuda.synchronize()
+    cpi_sps = len(cpi_seeds) / (time.perf_counter() - c0)
+
+    hbm, peak_kind = peaks()
+    sp = stats.get("spmm", {})
+    roof = None
+    if sp.get("total_ms", 0) > 0:
+        achieved = sp["alg_bytes"] / (sp["total_ms"] / 1000.0) / 1e9
+        per_launch = sp["alg_bytes"] / max(1, sp["launches"])
+        traffic = ncu_traffic("spmm_tile_k", f"KP{min(256, 1 << max(0, (Q - 1).bit_length()))}")
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "kernel": "spmm_tile_k (merge-path SpMV/SpMM over CSR(A~^T))",
+                "launches": sp["launches"], "avg_launch_ms": sp["total_ms"] / max(1, sp["launches"]),
+                "alg_bytes_per_launch": per_launch, "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                "kernel_share_of_step": sp["total_ms"] / (1000.0 * t_rank)}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args, tpa, torch, n, src, dst, seeds)
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(args, src, dst, seeds, pre_iters)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "graph": f"R-MAT scale {args.scale} ef {args.edge_factor}",
+                           "n": n, "m": m, "m_raw": int(src.size), "queries_per_rank": Q, "query_batch": batch,
+                           "c": C, "S": S, "T": T, "eps": EPS, "parallelism": f"replicas x{world} (seed-sharded)",
+                           "l2": "inputs larger than L2 (CSR 0.5 GB, scores 16.8 GB per step)"},
+                "roofline": roof, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk,
+                "phases_ms": phases, "preprocess_iters": pre_iters,
+                "online_seeds_per_s": Q / (phases["queries"] / 1000.0),
+                "per_seed_cpi": {"value": cpi_sps, "unit": "seeds/s", "seeds": len(cpi_seeds), "eps": EPS},
+                "kernels": stats}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_e2e(args, tpa, torch, n, src, dst, seeds):
+    """Same step through the C ABI with host buffers: edges from pinned host memory,
+    scores read back into pinned host memory, copies inside the timed region."""
+    Q = len(seeds)
+    src_h = torch.from_numpy(src).pin_memory()
+    dst_h = torch.from_numpy(dst).pin_memory()
+    seeds_h = torch.from_numpy(seeds).pin_memory()
+    out_h = torch.empty((n, Q), dtype=torch.float32, pin_memory=True)
+
+    def step():
+        g = tpa.build_graph(n, src_h, dst_h)
+        tpa.preprocess(g, C, T, EPS)
+        tpa.query(g, seeds_h, S, out=out_h)
+        g.free()
+
+    step()
+    torch.cuda.synchronize()
+    k = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    del out_h
+    return {"value": Q * k / dt, "unit": "seeds/s", "steps": k,
+            "h2d_bytes_per_step": int(src.nbytes + dst.nbytes + seeds.nbytes),
+            "d2h_bytes_per_step": int(4 * n * Q)}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

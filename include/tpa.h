@@ -1,0 +1,147 @@
+/*
+ * tpa.h -- C ABI of libtpa, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of TPA (Yoon, Jung and Kang, "TPA: Fast, Scalable,
+ * and Accurate Method for Approximate Random Walk with Restart on Billion
+ * Scale Graphs", arXiv 1708.02574).
+ *
+ * Notation (Table 1): n nodes, m edges, c restart probability, eps
+ * convergence tolerance, A~ the row-normalised adjacency matrix, S and T the
+ * first iterations of the neighbour and stranger parts.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers may be host or device memory; the kind is detected with
+ *     cudaPointerGetAttributes.  Inputs are copied; the caller keeps
+ *     ownership of every array it passes.  Outputs are written into
+ *     caller-provided buffers.  When an output is in host memory the call
+ *     returns after the data has arrived; otherwise it is stream-ordered.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All device
+ *     work of a call is issued on that stream.
+ *   - Calls on one tpa_graph must not overlap (the graph owns one workspace);
+ *     different graphs are independent.
+ *   - Every call returns a tpa_status and never aborts.  On failure,
+ *     tpa_last_error() returns a message for the calling thread.
+ *   - Score vectors are float32, laid out node-major: out[v * k + j] is the
+ *     score of node v for seed j.
+ */
+#ifndef TPA_H
+#define TPA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tpa_graph tpa_graph;
+
+typedef enum {
+    TPA_OK = 0,
+    TPA_EINVAL = 1,    /* argument out of range (ids, sizes, c, S, T, eps) */
+    TPA_ENOMEM = 2,    /* device or host allocation failed */
+    TPA_ECUDA = 3,     /* a CUDA call failed (message in tpa_last_error) */
+    TPA_ESTATE = 4,    /* call out of order, e.g. tpa_query before tpa_preprocess */
+    TPA_ETIMEOUT = 5   /* a bounded device wait gave up */
+} tpa_status;
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *tpa_last_error(void);
+
+/*
+ * Build the row-normalised adjacency A~ of Table 1 from a raw edge list
+ * (src[e] -> dst[e], 0 <= id < n, m_edges entries, int32).  Self-loops are
+ * dropped and duplicate edges are kept once; A~_uv = 1/outdeg(u) rounded to
+ * float32, and nodes without out-edges keep an all-zero row.  The graph
+ * holds CSR(A~^T) (rows = destinations, sources ascending) for the pull
+ * products of Algorithm 1 and CSR(A~) (rows = sources) for the push step
+ * and the adjoint, both on the device of `stream`.
+ * Errors: TPA_EINVAL for n < 1, n >= 2^31, m_edges < 0, an id out of range;
+ * TPA_ENOMEM, TPA_ECUDA.  *out is set only on success.
+ */
+tpa_status tpa_build_graph(int64_t n, int64_t m_edges, const int32_t *src, const int32_t *dst,
+                           void *stream, tpa_graph **out);
+
+/* Release a graph and all device memory it owns.  NULL is ignored. */
+void tpa_free_graph(tpa_graph *g);
+
+/* Number of nodes and of distinct non-self-loop edges. */
+tpa_status tpa_graph_info(const tpa_graph *g, int64_t *n, int64_t *m);
+
+/*
+ * Copy one CSR of the graph out: which = 0 for A~^T, 1 for A~.
+ * row_ptr holds n+1 int64, col m int32, val m float32; any may be NULL.
+ */
+tpa_status tpa_get_csr(const tpa_graph *g, int which, int64_t *row_ptr, int32_t *col,
+                       float *val, void *stream);
+
+/*
+ * Algorithm 2 (preprocessing phase): PageRank by CPI from x0 = (c/n) 1,
+ * keeping the sum of iterations i >= T until ||x_i||_1 < eps.  The result
+ * r~_stranger (float32[n]) stays resident in the graph together with c, T
+ * and eps.  Requires 0 < c < 1, T >= 1, eps > 0.
+ */
+tpa_status tpa_preprocess(tpa_graph *g, double c, int T, double eps, void *stream);
+
+/* Copy r~_stranger out (float32[n]) and the CPI iteration count. */
+tpa_status tpa_get_stranger(const tpa_graph *g, float *out, int64_t *iters, void *stream);
+
+/*
+ * Algorithm 3 (online phase) for k independent single-seed queries:
+ * for each seed s_j, r_family = x0 + ... + x_{S-1} by CPI from x0 = c e_s
+ * (with the preprocessing eps), then
+ *   r_TPA = (1 + alpha) r_family + r~_stranger,
+ *   alpha = ((1-c)^S - (1-c)^T) / (1 - (1-c)^S)   (Section III-B),
+ * using the c and T of tpa_preprocess.  out is float32[n * k], node-major.
+ * Requires 1 <= S <= T, k >= 1, 0 <= seeds[j] < n.
+ * Errors: TPA_ESTATE before tpa_preprocess; TPA_EINVAL.
+ */
+tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *out, void *stream);
+
+/*
+ * Algorithm 1 (CPI) for k single-seed vectors q = e_{s_j}: returns
+ * r_j = sum of x_i for s_iter <= i <= t_iter (t_iter < 0: no limit), each
+ * column stopping after the first i with ||x_i||_1 < eps.  out is
+ * float32[n * k], node-major; iters (int32[k], may be NULL) receives the
+ * last iteration computed for each column.
+ */
+tpa_status tpa_cpi(tpa_graph *g, const int32_t *seeds, int k, double c, double eps, int s_iter,
+                   int t_iter, float *out, int32_t *iters, void *stream);
+
+/* Exact RWR by CPI for one seed (Algorithm 1 with s_iter = 0, t_iter = inf). */
+tpa_status tpa_cpi_exact(tpa_graph *g, int32_t seed, double c, double eps, float *out,
+                         int32_t *iters, void *stream);
+
+/*
+ * Save / load the preprocessed data (Theorem 4: O(n) floats) as a binary
+ * file: magic, n, m, c, T, eps, iteration count, then float32[n].  Loading
+ * checks that n and m match the graph.
+ */
+tpa_status tpa_save_preprocessed(const tpa_graph *g, const char *path);
+tpa_status tpa_load_preprocessed(tpa_graph *g, const char *path, void *stream);
+
+/* ------------------------------------------------------ measurement ---
+ * Not part of the paper's method: launch accounting and kernel timing for
+ * benchmarks.  The statistics are process-wide and thread-safe. */
+typedef struct {
+    char name[32];        /* kernel family, e.g. "spmm", "fixup", "sort" */
+    int64_t launches;     /* launches since the last tpa_profile_reset */
+    double total_ms;      /* summed CUDA-event durations (0 unless timing is on) */
+    double alg_bytes;     /* algorithmic bytes of the timed launches */
+} tpa_kernel_stat;
+
+/* Number of CUDA kernel launches issued by the library since it was loaded. */
+uint64_t tpa_launch_count(void);
+
+/* Clear the per-family statistics.  With timing != 0, every SpMV/SpMM and
+ * fixup launch of Algorithm 1 is bracketed by CUDA events recorded on its
+ * own stream until the next reset. */
+tpa_status tpa_profile_reset(int timing);
+
+/* Read the statistics (waits for the recorded events).  Writes up to cap
+ * entries to out and the number of families to *count. */
+tpa_status tpa_profile_read(tpa_kernel_stat *out, int cap, int *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPA_H */

@@ -1,0 +1,30 @@
+"""GB300-native TPA: approximate Random Walk with Restart (arXiv 1708.02574).
+
+Thin Python binding over the C ABI of ``libtpa.so`` (declared in
+``include/tpa.h``).  Every step of the hot path -- CSR construction, the
+cumulative power iteration (Algorithm 1), preprocessing (Algorithm 2) and the
+online query (Algorithm 3) -- runs in the library's CUDA kernels; this module
+only marshals arguments.  PyTorch provides device memory and the current
+stream.  There is no CPU fallback: if the library cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+from .tpa import (  # noqa: F401
+    TpaError,
+    Graph,
+    build_graph,
+    cpi,
+    cpi_exact,
+    get_csr,
+    get_stranger,
+    graph_info,
+    launch_count,
+    library,
+    profile_read,
+    profile_reset,
+    load_preprocessed,
+    preprocess,
+    query,
+    save_preprocessed,
+)

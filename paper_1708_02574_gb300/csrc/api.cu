@@ -1,0 +1,410 @@
+// C-ABI entry points of libtpa (declared in include/tpa.h).
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tpa_internal.cuh"
+
+namespace tpa {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+void DevBuf::ensure(size_t b, cudaStream_t s)
+{
+    if (b <= bytes && p) return;
+    release(s);
+    void *q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, b ? b : 16, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation of %zu bytes failed: %s", b, cudaGetErrorString(e));
+        throw Fail{TPA_ENOMEM};
+    }
+    p = q;
+    bytes = b;
+}
+
+void DevBuf::release(cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    bytes = 0;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+void copy_in(void *dst_dev, const void *src_any, size_t bytes, cudaStream_t s)
+{
+    if (bytes) TPA_CUDA(cudaMemcpyAsync(dst_dev, src_any, bytes, cudaMemcpyDefault, s));
+}
+
+static double alpha_of(double c, int S, int T)
+{
+    // Section III-B: ||r_neighbor||_1 / ||r_family||_1 by Lemma 2
+    const double a = std::pow(1.0 - c, (double)S), b = std::pow(1.0 - c, (double)T);
+    return (a - b) / (1.0 - a);
+}
+
+// Copy k seeds to the host (from host or device memory) and check 0 <= s < n.
+static std::vector<int32_t> read_seeds(const int32_t *seeds, int k, int64_t n, cudaStream_t s)
+{
+    std::vector<int32_t> h((size_t)k);
+    if (is_device_ptr(seeds)) {
+        TPA_CUDA(cudaMemcpyAsync(h.data(), seeds, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        TPA_CUDA(cudaStreamSynchronize(s));
+    } else {
+        memcpy(h.data(), seeds, (size_t)k * sizeof(int32_t));
+    }
+    for (int j = 0; j < k; ++j) TPA_REQUIRE(h[j] >= 0 && h[j] < n, "seed %d (index %d) is outside [0, %lld)", h[j], j, (long long)n);
+    return h;
+}
+
+}  // namespace tpa
+
+using namespace tpa;
+
+#define API_BEGIN \
+    g_err.clear(); \
+    try {
+#define API_END                                   \
+    }                                             \
+    catch (const Fail &f) {                       \
+        return f.st;                              \
+    }                                             \
+    catch (const std::bad_alloc &) {              \
+        set_error("host allocation failed");      \
+        return TPA_ENOMEM;                        \
+    }                                             \
+    catch (...) {                                 \
+        set_error("unexpected C++ exception");    \
+        return TPA_ECUDA;                         \
+    }                                             \
+    return TPA_OK;
+
+extern "C" {
+
+const char *tpa_last_error(void) { return g_err.c_str(); }
+
+tpa_status tpa_build_graph(int64_t n, int64_t m_edges, const int32_t *src, const int32_t *dst, void *stream,
+                           tpa_graph **out)
+{
+    API_BEGIN
+    TPA_REQUIRE(out != nullptr, "tpa_build_graph: out is NULL");
+    TPA_REQUIRE(n >= 1 && n < ((int64_t)1 << 31), "tpa_build_graph: n = %lld outside [1, 2^31)", (long long)n);
+    TPA_REQUIRE(m_edges >= 0 && m_edges < ((int64_t)1 << 31) - 1, "tpa_build_graph: m_edges = %lld outside [0, 2^31-1)",
+                (long long)m_edges);
+    TPA_REQUIRE(m_edges == 0 || (src && dst), "tpa_build_graph: NULL edge arrays");
+    cudaStream_t s = (cudaStream_t)stream;
+    tpa_graph *g = new tpa_graph();
+    try {
+        TPA_CUDA(cudaGetDevice(&g->device));
+        g->n = n;
+        DevBuf dsrc, ddst;
+        const int32_t *ps = src, *pd = dst;
+        if (m_edges > 0 && !is_device_ptr(src)) {
+            dsrc.ensure((size_t)m_edges * sizeof(int32_t), s);
+            copy_in(dsrc.p, src, (size_t)m_edges * sizeof(int32_t), s);
+            ps = dsrc.as<int32_t>();
+        }
+        if (m_edges > 0 && !is_device_ptr(dst)) {
+            ddst.ensure((size_t)m_edges * sizeof(int32_t), s);
+            copy_in(ddst.p, dst, (size_t)m_edges * sizeof(int32_t), s);
+            pd = ddst.as<int32_t>();
+        }
+        build_csr(g, ps, pd, m_edges, s);
+        dsrc.release(s);
+        ddst.release(s);
+    } catch (...) {
+        tpa_free_graph(g);
+        throw;
+    }
+    *out = g;
+    API_END
+}
+
+void tpa_free_graph(tpa_graph *g)
+{
+    if (!g) return;
+    cudaStream_t s = 0;
+    cudaDeviceSynchronize();
+    DevBuf *bufs[] = {&g->rp_t, &g->col_t, &g->val_t, &g->rp_a, &g->col_a, &g->val_a, &g->outdeg, &g->r_str,
+                      &g->ws.x, &g->ws.y, &g->ws.r, &g->ws.carry, &g->ws.head, &g->ws.tl1, &g->ws.fix,
+                      &g->ws.ctl, &g->ws.seeds, &g->ws.out, &g->ws.iters};
+    for (DevBuf *b : bufs) b->release(s);
+    for (auto &kv : g->plans_t) {
+        kv.second.tile_x.release(s);
+        kv.second.tile_y.release(s);
+        kv.second.head_row.release(s);
+        kv.second.head_first.release(s);
+    }
+    if (g->ws.hflag) cudaFreeHost(g->ws.hflag);
+    cudaStreamSynchronize(s);
+    delete g;
+}
+
+tpa_status tpa_graph_info(const tpa_graph *g, int64_t *n, int64_t *m)
+{
+    API_BEGIN
+    TPA_REQUIRE(g != nullptr, "tpa_graph_info: NULL graph");
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    API_END
+}
+
+tpa_status tpa_get_csr(const tpa_graph *g, int which, int64_t *row_ptr, int32_t *col, float *val, void *stream)
+{
+    API_BEGIN
+    TPA_REQUIRE(g != nullptr, "tpa_get_csr: NULL graph");
+    TPA_REQUIRE(which == 0 || which == 1, "tpa_get_csr: which must be 0 (A~^T) or 1 (A~)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const DevBuf &rp = which ? g->rp_a : g->rp_t;
+    const DevBuf &cl = which ? g->col_a : g->col_t;
+    const DevBuf &vl = which ? g->val_a : g->val_t;
+    bool host = false;
+    if (row_ptr) {
+        TPA_CUDA(cudaMemcpyAsync(row_ptr, rp.p, (size_t)(g->n + 1) * sizeof(int64_t), cudaMemcpyDefault, s));
+        host |= !is_device_ptr(row_ptr);
+    }
+    if (col && g->m) {
+        TPA_CUDA(cudaMemcpyAsync(col, cl.p, (size_t)g->m * sizeof(int32_t), cudaMemcpyDefault, s));
+        host |= !is_device_ptr(col);
+    }
+    if (val && g->m) {
+        TPA_CUDA(cudaMemcpyAsync(val, vl.p, (size_t)g->m * sizeof(float), cudaMemcpyDefault, s));
+        host |= !is_device_ptr(val);
+    }
+    if (host) TPA_CUDA(cudaStreamSynchronize(s));
+    API_END
+}
+
+tpa_status tpa_preprocess(tpa_graph *g, double c, int T, double eps, void *stream)
+{
+    API_BEGIN
+    TPA_REQUIRE(g != nullptr, "tpa_preprocess: NULL graph");
+    TPA_REQUIRE(c > 0.0 && c < 1.0, "tpa_preprocess: c = %g outside (0, 1)", c);
+    TPA_REQUIRE(T >= 1, "tpa_preprocess: T = %d < 1", T);
+    TPA_REQUIRE(eps > 0.0 && std::isfinite(eps), "tpa_preprocess: eps must be positive");
+    cudaStream_t s = (cudaStream_t)stream;
+    g->has_pre = false;
+    g->r_str.ensure((size_t)g->n * sizeof(float), s);
+    g->ws.iters.ensure(sizeof(int32_t), s);
+    CpiArgs a;
+    a.seeds = nullptr;
+    a.k = 1;
+    a.c = c;
+    a.eps = eps;
+    a.s_iter = T;
+    a.t_iter = -1;
+    a.r = g->r_str.as<float>();
+    a.ldr = 1;
+    a.iters_out = g->ws.iters.as<int32_t>();
+    run_cpi(g, a, s);
+    int32_t it = 0;
+    TPA_CUDA(cudaMemcpyAsync(&it, a.iters_out, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TPA_CUDA(cudaStreamSynchronize(s));
+    g->pre_iters = it;
+    g->c = c;
+    g->T = T;
+    g->eps = eps;
+    g->has_pre = true;
+    API_END
+}
+
+tpa_status tpa_get_stranger(const tpa_graph *g, float *out, int64_t *iters, void *stream)
+{
+    API_BEGIN
+    TPA_REQUIRE(g != nullptr, "tpa_get_stranger: NULL graph");
+    if (!g->has_pre) {
+        set_error("tpa_get_stranger: tpa_preprocess has not run");
+        return TPA_ESTATE;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (out) {
+        TPA_CUDA(cudaMemcpyAsync(out, g->r_str.p, (size_t)g->n * sizeof(float), cudaMemcpyDefault, s));
+        if (!is_device_ptr(out)) TPA_CUDA(cudaStreamSynchronize(s));
+    }
+    if (iters) *iters = g->pre_iters;
+    API_END
+}
+
+tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *out, void *stream)
+{
+    API_BEGIN
+    TPA_REQUIRE(g != nullptr, "tpa_query: NULL graph");
+    if (!g->has_pre) {
+        set_error("tpa_query: tpa_preprocess has not run");
+        return TPA_ESTATE;
+    }
+    TPA_REQUIRE(k >= 1, "tpa_query: k = %d < 1", k);
+    TPA_REQUIRE(S >= 1 && S <= g->T, "tpa_query: S = %d outside [1, T = %d]", S, g->T);
+    TPA_REQUIRE(seeds && out, "tpa_query: NULL seeds or out");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int32_t> hs = read_seeds(seeds, k, g->n, s);
+    g->ws.seeds.ensure((size_t)k * sizeof(int32_t), s);
+    TPA_CUDA(cudaMemcpyAsync(g->ws.seeds.p, hs.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    const bool host_out = !is_device_ptr(out);
+    float *dout = out;
+    if (host_out) {
+        g->ws.out.ensure((size_t)g->n * k * sizeof(float), s);
+        dout = g->ws.out.as<float>();
+    }
+    CpiArgs a;
+    a.seeds = g->ws.seeds.as<int32_t>();
+    a.k = k;
+    a.c = g->c;
+    a.eps = g->eps;
+    a.s_iter = 0;
+    a.t_iter = S - 1;
+    a.r_internal = true;
+    a.tpa_final = true;
+    a.alpha = alpha_of(g->c, S, g->T);
+    a.r_str = g->r_str.as<float>();
+    a.out = dout;
+    a.ldo = k;
+    run_cpi(g, a, s);
+    if (host_out) {
+        TPA_CUDA(cudaMemcpyAsync(out, dout, (size_t)g->n * k * sizeof(float), cudaMemcpyDeviceToHost, s));
+        TPA_CUDA(cudaStreamSynchronize(s));
+    }
+    API_END
+}
+
+tpa_status tpa_cpi(tpa_graph *g, const int32_t *seeds, int k, double c, double eps, int s_iter, int t_iter,
+                   float *out, int32_t *iters, void *stream)
+{
+    API_BEGIN
+    TPA_REQUIRE(g != nullptr, "tpa_cpi: NULL graph");
+    TPA_REQUIRE(k >= 1, "tpa_cpi: k = %d < 1", k);
+    TPA_REQUIRE(c > 0.0 && c < 1.0, "tpa_cpi: c = %g outside (0, 1)", c);
+    TPA_REQUIRE(eps > 0.0 && std::isfinite(eps), "tpa_cpi: eps must be positive");
+    TPA_REQUIRE(s_iter >= 0, "tpa_cpi: s_iter < 0");
+    TPA_REQUIRE(seeds && out, "tpa_cpi: NULL seeds or out");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int32_t> hs = read_seeds(seeds, k, g->n, s);
+    g->ws.seeds.ensure((size_t)k * sizeof(int32_t), s);
+    TPA_CUDA(cudaMemcpyAsync(g->ws.seeds.p, hs.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    const bool host_out = !is_device_ptr(out);
+    float *dout = out;
+    if (host_out) {
+        g->ws.out.ensure((size_t)g->n * k * sizeof(float), s);
+        dout = g->ws.out.as<float>();
+    }
+    g->ws.iters.ensure((size_t)k * sizeof(int32_t), s);
+    CpiArgs a;
+    a.seeds = g->ws.seeds.as<int32_t>();
+    a.k = k;
+    a.c = c;
+    a.eps = eps;
+    a.s_iter = s_iter;
+    a.t_iter = t_iter;
+    a.r = dout;
+    a.ldr = k;
+    a.iters_out = g->ws.iters.as<int32_t>();
+    run_cpi(g, a, s);
+    if (iters) {
+        TPA_CUDA(cudaMemcpyAsync(iters, a.iters_out, (size_t)k * sizeof(int32_t), cudaMemcpyDefault, s));
+        if (!is_device_ptr(iters)) TPA_CUDA(cudaStreamSynchronize(s));
+    }
+    if (host_out) {
+        TPA_CUDA(cudaMemcpyAsync(out, dout, (size_t)g->n * k * sizeof(float), cudaMemcpyDeviceToHost, s));
+        TPA_CUDA(cudaStreamSynchronize(s));
+    }
+    API_END
+}
+
+tpa_status tpa_cpi_exact(tpa_graph *g, int32_t seed, double c, double eps, float *out, int32_t *iters, void *stream)
+{
+    return tpa_cpi(g, &seed, 1, c, eps, 0, -1, out, iters, stream);
+}
+
+struct PreHeader {
+    char magic[8];
+    int64_t n, m;
+    double c;
+    int64_t T;
+    double eps;
+    int64_t iters;
+};
+
+tpa_status tpa_save_preprocessed(const tpa_graph *g, const char *path)
+{
+    API_BEGIN
+    TPA_REQUIRE(g && path, "tpa_save_preprocessed: NULL argument");
+    if (!g->has_pre) {
+        set_error("tpa_save_preprocessed: tpa_preprocess has not run");
+        return TPA_ESTATE;
+    }
+    std::vector<float> h((size_t)g->n);
+    TPA_CUDA(cudaMemcpy(h.data(), g->r_str.p, (size_t)g->n * sizeof(float), cudaMemcpyDeviceToHost));
+    PreHeader hd;
+    memcpy(hd.magic, "TPASTR01", 8);
+    hd.n = g->n;
+    hd.m = g->m;
+    hd.c = g->c;
+    hd.T = g->T;
+    hd.eps = g->eps;
+    hd.iters = g->pre_iters;
+    FILE *f = fopen(path, "wb");
+    TPA_REQUIRE(f != nullptr, "tpa_save_preprocessed: cannot open %s", path);
+    const bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
+    const bool closed = fclose(f) == 0;
+    TPA_REQUIRE(ok && closed, "tpa_save_preprocessed: write to %s failed", path);
+    API_END
+}
+
+tpa_status tpa_load_preprocessed(tpa_graph *g, const char *path, void *stream)
+{
+    API_BEGIN
+    TPA_REQUIRE(g && path, "tpa_load_preprocessed: NULL argument");
+    FILE *f = fopen(path, "rb");
+    TPA_REQUIRE(f != nullptr, "tpa_load_preprocessed: cannot open %s", path);
+    PreHeader hd;
+    std::vector<float> h;
+    bool ok = fread(&hd, sizeof(hd), 1, f) == 1 && memcmp(hd.magic, "TPASTR01", 8) == 0 && hd.n == g->n &&
+              hd.m == g->m && hd.c > 0 && hd.c < 1 && hd.T >= 1 && hd.T < (1 << 30);
+    if (ok) {
+        h.resize((size_t)g->n);
+        ok = fread(h.data(), sizeof(float), h.size(), f) == h.size();
+    }
+    fclose(f);
+    TPA_REQUIRE(ok, "tpa_load_preprocessed: %s is not preprocessed data for this graph", path);
+    cudaStream_t s = (cudaStream_t)stream;
+    g->r_str.ensure((size_t)g->n * sizeof(float), s);
+    TPA_CUDA(cudaMemcpyAsync(g->r_str.p, h.data(), (size_t)g->n * sizeof(float), cudaMemcpyHostToDevice, s));
+    TPA_CUDA(cudaStreamSynchronize(s));
+    g->c = hd.c;
+    g->T = (int)hd.T;
+    g->eps = hd.eps;
+    g->pre_iters = hd.iters;
+    g->has_pre = true;
+    API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,825 @@
+// Cumulative power iteration (Algorithm 1) on the GPU.
+//
+// One iteration computes x_i = (1-c) A~^T x_{i-1} for k independent columns
+// (node-major X[n][KP], KP = padded k) with a merge-path SpMM over CSR(A~^T)
+// (Merrill and Garland's merge-based decomposition: the path interleaves the
+// n row-end markers with the m nonzeros, and every CTA takes an equal slice
+// of it, so hub rows with huge in-degree cost no load imbalance).
+//
+// spmm_tile_k, tiles of L = NVT * ITEMS path steps, taken round-robin by
+// persistent CTAs:
+//   1. stage the tile's row ends and (col, val) into shared memory with
+//      evict-first loads, so the CSR stream does not push the iterates out
+//      of L2;
+//   2. each virtual thread (G lanes, V columns per lane) finds its own
+//      diagonal by a merge-path search in shared memory, issues the
+//      gathers x[col] for a chunk of steps, then walks the chunk, emitting
+//      finished rows;
+//   3. a segmented scan over the virtual threads' carries finishes rows
+//      that straddle virtual threads; the row straddling the tile's start
+//      is deferred to the fixup kernel, and the tile's last partial row is
+//      written out as the tile carry;
+//   4. the epilogue of Algorithm 1 is fused: y = (1-c) sum, r += y for
+//      columns still running when i >= s_iter, per-column L1 of y in FP64;
+//      or, on the last family iteration of Algorithm 3, the finalize
+//      out = (1+alpha)(r + y) + r~_stranger.
+// fixup_k, warps over tiles: adds the carries of earlier tiles to each
+// deferred row in a fixed order, applies the epilogue, reduces the per-tile
+// L1 partials in a fixed order, and the last block applies the break test
+// ||x_i||_1 < eps per column.  Both kernels run persistent grids with a static
+// tile order, so results are deterministic run to run.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "tpa_internal.cuh"
+
+namespace tpa {
+
+constexpr int KP_MAX = 256;
+constexpr int CTA = 256;
+
+// Control buffer layout (bytes): Ctl header, int32 alive[KP_MAX], int32 iters[KP_MAX], double norm[KP_MAX]
+struct CtlView {
+    Ctl *hdr;
+    int32_t *alive;
+    int32_t *iters;
+    double *norm;
+};
+__host__ __device__ inline CtlView ctl_view(void *base)
+{
+    CtlView v;
+    v.hdr = reinterpret_cast<Ctl *>(base);
+    v.alive = reinterpret_cast<int32_t *>(v.hdr + 1);
+    v.iters = v.alive + KP_MAX;
+    v.norm = reinterpret_cast<double *>(v.iters + KP_MAX);
+    return v;
+}
+constexpr size_t CTL_BYTES = sizeof(Ctl) + 2 * KP_MAX * sizeof(int32_t) + KP_MAX * sizeof(double);
+
+struct Params {
+    // CSR(A~^T)
+    const int64_t *rp;
+    const int32_t *col;
+    const float *val;
+    int64_t n;
+    // merge-path plan
+    const int32_t *tile_x;
+    const int64_t *tile_y;
+    const int32_t *head_row;
+    const int32_t *head_first;
+    int64_t tiles;
+    // iterates [n][KP]
+    const float *x;
+    float *y;
+    // accumulator and finalize
+    float *r;
+    int64_t ldr;
+    float *out;
+    int64_t ldo;
+    const float *r_str;
+    float one_plus_alpha;
+    float decay;
+    int k;
+    int mode;
+    int accumulate;
+    int iter;
+    double eps;
+    // per-tile scratch
+    float *carry;    // [tiles][KP]
+    float *head;     // [tiles][KP]
+    double *tl1;     // [tiles][KP]
+    double *part;    // [fix blocks][KP]
+    void *ctl;
+};
+
+// ------------------------------------------------------------- helpers ---
+template <int V>
+__device__ __forceinline__ void ld_row(const float *p, float (&o)[V])
+{
+    if constexpr (V == 1) {
+        o[0] = __ldg(p);
+    } else if constexpr (V == 2) {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        o[0] = t.x; o[1] = t.y;
+    } else if constexpr (V == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else {
+        static_assert(V == 8, "V");
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+        o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void st_row(float *p, const float (&v)[V])
+{
+    if constexpr (V == 1) {
+        p[0] = v[0];
+    } else if constexpr (V == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    } else if constexpr (V == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+}
+
+// Epilogue of Algorithm 1 for one finished row and V consecutive columns.
+template <int KP, int V>
+__device__ __forceinline__ void epilogue(const Params &p, int64_t row, int col0, const float (&s)[V],
+                                         const int (&alive)[V], double (&l1)[V])
+{
+    float yv[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) yv[j] = p.decay * s[j];
+    if (p.mode == MODE_ACC) {
+        st_row<V>(p.y + row * KP + col0, yv);
+        if (p.accumulate) {
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+                if (col0 + j < p.k && alive[j]) p.r[row * p.ldr + col0 + j] += yv[j];
+        }
+    } else {
+        const float rs = p.r_str[row];
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+            if (col0 + j < p.k) {
+                const float fam = p.r[row * p.ldr + col0 + j] + (alive[j] ? yv[j] : 0.0f);
+                p.out[row * p.ldo + col0 + j] = fmaf(p.one_plus_alpha, fam, rs);
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) l1[j] += alive[j] ? (double)fabsf(yv[j]) : 0.0;
+}
+
+// --------------------------------------------------------- main kernel ---
+template <int G, int V, int ITEMS, int PF>
+struct SpmmSmem {
+    static constexpr int NVT = CTA / G;
+    static constexpr int L = NVT * ITEMS;
+    static constexpr int KP = G * V;
+    int32_t end[L + 1];
+    int32_t col[L];
+    float val[L];
+    int32_t crow[NVT];
+    float carry[NVT][KP];
+    double l1[CTA / 32][KP];
+};
+
+template <int G, int V, int ITEMS, int PF>
+__global__ void __launch_bounds__(CTA) spmm_tile_k(Params p)
+{
+    using Sm = SpmmSmem<G, V, ITEMS, PF>;
+    constexpr int NVT = Sm::NVT, L = Sm::L, KP = Sm::KP;
+    static_assert(ITEMS % PF == 0, "PF");
+    static_assert(L <= (1 << 20), "L");
+    __shared__ Sm S;
+
+    const CtlView cv = ctl_view(p.ctl);
+    if (*(volatile int32_t *)&cv.hdr->done) return;
+
+    const int vt = threadIdx.x / G, g = threadIdx.x % G;
+    const int col0 = g * V;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int alive[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) alive[j] = cv.alive[col0 + j];
+
+    // persistent CTA: static round-robin over tiles (deterministic)
+    for (int64_t t = blockIdx.x; t < p.tiles; t += gridDim.x) {
+        const int32_t x0 = p.tile_x[t], x1 = p.tile_x[t + 1];
+        const int64_t y0 = p.tile_y[t], y1 = p.tile_y[t + 1];
+        const int nrows = x1 - x0, nnz = (int)(y1 - y0);
+        __syncthreads();   // the previous tile is done with shared memory
+
+        for (int i = threadIdx.x; i < nrows; i += CTA) S.end[i] = (int)(__ldcs(p.rp + x0 + i + 1) - y0);
+        if (threadIdx.x == 0) S.end[nrows] = 0x7fffffff;
+        for (int i = threadIdx.x; i < nnz; i += CTA) {
+            S.col[i] = __ldcs(p.col + y0 + i);
+            S.val[i] = __ldcs(p.val + y0 + i);
+        }
+        __syncthreads();
+
+        // merge-path search for this virtual thread's diagonal
+        const int d = min(vt * ITEMS, nrows + nnz);
+        int lo = max(0, d - nnz), hi = min(d, nrows);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (S.end[mid] + mid + 1 <= d) lo = mid + 1; else hi = mid;
+        }
+        int xs = lo, ys = d - lo;
+        const int avail = nrows + nnz - d;
+
+        float acc[V];
+        double l1[V];
+        float first_val[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            acc[j] = 0.0f;
+            l1[j] = 0.0;
+            first_val[j] = 0.0f;
+        }
+        int first_row = -1;
+
+#pragma unroll
+        for (int c0 = 0; c0 < ITEMS; c0 += PF) {
+            float xv[PF][V];
+            float vv[PF];
+            unsigned nzmask = 0;
+            // pass 1: decide each step and issue the gathers
+            {
+                int xa = xs, ya = ys;
+#pragma unroll
+                for (int it = 0; it < PF; ++it) {
+                    if (c0 + it < avail) {
+                        if (ya < S.end[xa]) {
+                            const int c = S.col[ya];
+                            vv[it] = S.val[ya];
+                            ld_row<V>(p.x + (int64_t)c * KP + col0, xv[it]);
+                            nzmask |= 1u << it;
+                            ++ya;
+                        } else {
+                            ++xa;
+                        }
+                    }
+                }
+            }
+            // pass 2: accumulate and emit
+#pragma unroll
+            for (int it = 0; it < PF; ++it) {
+                if (c0 + it < avail) {
+                    if (nzmask & (1u << it)) {
+#pragma unroll
+                        for (int j = 0; j < V; ++j) acc[j] = fmaf(vv[it], xv[it][j], acc[j]);
+                        ++ys;
+                    } else {
+                        if (first_row < 0) {
+                            first_row = xs;
+#pragma unroll
+                            for (int j = 0; j < V; ++j) first_val[j] = acc[j];
+                        } else {
+                            epilogue<KP, V>(p, (int64_t)(x0 + xs), col0, acc, alive, l1);
+                        }
+#pragma unroll
+                        for (int j = 0; j < V; ++j) acc[j] = 0.0f;
+                        ++xs;
+                    }
+                }
+            }
+        }
+
+        // segmented inclusive scan of the virtual threads' carries (key = row)
+        if (g == 0) S.crow[vt] = xs;
+#pragma unroll
+        for (int j = 0; j < V; ++j) S.carry[vt][col0 + j] = acc[j];
+        __syncthreads();
+#pragma unroll 1
+        for (int off = 1; off < NVT; off <<= 1) {
+            float add[V];
+            const bool take = vt >= off && S.crow[vt - off] == S.crow[vt];
+#pragma unroll
+            for (int j = 0; j < V; ++j) add[j] = take ? S.carry[vt - off][col0 + j] : 0.0f;
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < V; ++j) S.carry[vt][col0 + j] += add[j];
+            __syncthreads();
+        }
+
+        if (first_row >= 0) {
+            float tot[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) tot[j] = first_val[j] + (vt > 0 ? S.carry[vt - 1][col0 + j] : 0.0f);
+            if (first_row == 0 && p.head_row[t] >= 0) {
+                st_row<V>(p.head + t * KP + col0, tot);
+            } else {
+                epilogue<KP, V>(p, (int64_t)(x0 + first_row), col0, tot, alive, l1);
+            }
+        }
+        if (vt == NVT - 1) {
+            float cv2[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) cv2[j] = S.carry[vt][col0 + j];
+            st_row<V>(p.carry + t * KP + col0, cv2);
+        }
+
+        // per-column L1 of this tile, fixed reduction order
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            double v = l1[j];
+#pragma unroll
+            for (int o = G; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            l1[j] = v;
+        }
+        if (lane < G) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) S.l1[warp][col0 + j] = l1[j];
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < KP; c += CTA) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < CTA / 32; ++w) sum += S.l1[w][c];
+            p.tl1[t * KP + c] = sum;
+        }
+    }
+}
+
+// --------------------------------------------------------------- fixup ---
+constexpr int FIX_WARPS = 8;
+
+// Persistent grid: each warp takes tiles in a fixed round-robin order, adds the
+// carries of earlier tiles to the tile's deferred row (unrolled, fixed order),
+// applies the epilogue and accumulates the per-tile L1; the last block to
+// finish reduces the block partials in parallel in a fixed order and applies
+// the break test.
+template <int KP>
+__global__ void __launch_bounds__(FIX_WARPS * 32) fixup_k(Params p)
+{
+    constexpr int CW = KP < 32 ? KP : 32;    // columns per lane group
+    constexpr int SUB = 32 / CW;             // lanes sharing one column
+    constexpr int NCH = KP / CW;             // column chunks per lane
+    constexpr int NG = (FIX_WARPS * 32) / KP > 0 ? (FIX_WARPS * 32) / KP : 1;   // groups in the final reduction
+    __shared__ double s_l1[FIX_WARPS][KP];
+    __shared__ double s_red[NG * KP];
+    __shared__ int s_last;
+    const CtlView cv = ctl_view(p.ctl);
+    if (*(volatile int32_t *)&cv.hdr->done) return;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cl = lane % CW, sub = lane / CW;
+    double l1acc[NCH];
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) l1acc[i] = 0.0;
+
+    for (int64_t t = (int64_t)blockIdx.x * FIX_WARPS + warp; t < p.tiles; t += (int64_t)gridDim.x * FIX_WARPS) {
+        const int32_t h = p.head_row[t];
+        const int64_t first = p.head_first[t];
+#pragma unroll
+        for (int i = 0; i < NCH; ++i) {
+            const int c = i * CW + cl;
+            double l1 = sub == 0 ? p.tl1[t * KP + c] : 0.0;
+            if (h >= 0) {
+                float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+                int64_t u = first + sub;
+                for (; u + 3 * SUB < t; u += 4 * SUB) {
+                    s0 += p.carry[u * KP + c];
+                    s1 += p.carry[(u + SUB) * KP + c];
+                    s2 += p.carry[(u + 2 * SUB) * KP + c];
+                    s3 += p.carry[(u + 3 * SUB) * KP + c];
+                }
+                for (; u < t; u += SUB) s0 += p.carry[u * KP + c];
+                float s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+                for (int o = CW; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (sub == 0) {
+                    float tot[1] = {p.head[t * KP + c] + s};
+                    int al[1] = {cv.alive[c]};
+                    double e[1] = {0.0};
+                    epilogue<KP, 1>(p, (int64_t)h, c, tot, al, e);
+                    l1 += e[0];
+                }
+            }
+            l1acc[i] += l1;
+        }
+    }
+    if (sub == 0) {
+#pragma unroll
+        for (int i = 0; i < NCH; ++i) s_l1[warp][i * CW + cl] = l1acc[i];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < KP; c += FIX_WARPS * 32) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < FIX_WARPS; ++w) sum += s_l1[w][c];
+        p.part[(int64_t)blockIdx.x * KP + c] = sum;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&cv.hdr->ticket, 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x < NG * KP) {
+        const int c = threadIdx.x % KP, grp = threadIdx.x / KP;
+        double sum = 0.0;
+        for (unsigned b = grp; b < gridDim.x; b += NG) sum += __ldcg(&p.part[(int64_t)b * KP + c]);
+        s_red[grp * KP + c] = sum;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < KP; c += FIX_WARPS * 32) {
+        double sum = 0.0;
+        for (int grp = 0; grp < NG; ++grp) sum += s_red[grp * KP + c];
+        if (c < p.k && cv.alive[c]) {
+            cv.norm[c] = sum;
+            cv.iters[c] = p.iter;
+            // the break test; the finalize iteration is the last one, so the
+            // break state stays as it was for finalize_if_done_k
+            if (sum < p.eps && p.mode == MODE_ACC) cv.alive[c] = 0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int c = 0; c < p.k && c < KP; ++c) any |= cv.alive[c];
+        cv.hdr->done = any ? 0 : 1;
+        cv.hdr->ticket = 0;
+    }
+}
+
+// ---------------------------------------------------------- init / misc ---
+// x0 = c q per column (one-hot at seeds[j], or c/n everywhere when seeds is null);
+// r = x0 when s_iter == 0, else 0.
+__global__ void init_k(float *x, int KP, int64_t n, const int32_t *seeds, int k, float c_val, float pr_val,
+                       float *r, int64_t ldr, int acc0)
+{
+    const int64_t total = n * KP;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = i / KP;
+        const int j = (int)(i % KP);
+        float x0 = 0.0f;
+        if (j < k) x0 = seeds ? (seeds[j] == v ? c_val : 0.0f) : pr_val;
+        x[i] = x0;
+        if (r && j < k) r[v * ldr + j] = acc0 ? x0 : 0.0f;
+    }
+}
+
+__global__ void ctl_init_k(void *ctl, int k)
+{
+    const CtlView cv = ctl_view(ctl);
+    for (int j = threadIdx.x; j < KP_MAX; j += blockDim.x) {
+        cv.alive[j] = j < k ? 1 : 0;
+        cv.iters[j] = 0;
+        cv.norm[j] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        cv.hdr->done = 0;
+        cv.hdr->ticket = 0;
+        cv.hdr->iter = 0;
+    }
+}
+
+// r_TPA = (1+alpha) r_family + r_str, used when the family has no SpMV (S = 1)
+__global__ void finalize_k(const float *r, int64_t ldr, const float *r_str, float opa, float *out, int64_t ldo,
+                           int64_t n, int k)
+{
+    const int64_t total = n * k;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = i / k;
+        const int j = (int)(i % k);
+        out[v * ldo + j] = fmaf(opa, r[v * ldr + j], r_str[v]);
+    }
+}
+
+// The finalize of Algorithm 3 when every column broke before the last family
+// iteration (the SpMM of that iteration then returned early):
+// r_TPA = (1+alpha) r_family + r_str.
+__global__ void finalize_if_done_k(const void *ctl, const float *r, int64_t ldr, const float *r_str, float opa,
+                                   float *out, int64_t ldo, int64_t n, int k)
+{
+    const CtlView cv = ctl_view(const_cast<void *>(ctl));
+    if (!*(volatile int32_t *)&cv.hdr->done) return;
+    const int64_t total = n * k;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = i / k;
+        const int j = (int)(i % k);
+        out[v * ldo + j] = fmaf(opa, r[v * ldr + j], r_str[v]);
+    }
+}
+
+__global__ void copy_iters_k(const void *ctl, int32_t *out, int k)
+{
+    const CtlView cv = ctl_view(const_cast<void *>(ctl));
+    for (int j = threadIdx.x; j < k; j += blockDim.x) out[j] = cv.iters[j];
+}
+
+// ------------------------------------------------------------- planning ---
+__global__ void plan_tiles_k(const int64_t *rp, int64_t n, int64_t m, int64_t L, int64_t tiles, int32_t *tx, int64_t *ty)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= tiles; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t D = min(t * L, n + m);
+        int64_t lo = max((int64_t)0, D - m), hi = min(D, n);
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (rp[mid + 1] + mid + 1 <= D) lo = mid + 1; else hi = mid;
+        }
+        tx[t] = (int32_t)lo;
+        ty[t] = D - lo;
+    }
+}
+
+__global__ void plan_heads_k(const int64_t *rp, const int32_t *tx, const int64_t *ty, int64_t tiles, int32_t *hr, int32_t *hf)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x0 = tx[t], x1 = tx[t + 1];
+        const int64_t y0 = ty[t];
+        if (x0 < x1 && rp[x0] < y0) {
+            hr[t] = x0;
+            // last tile whose start is at or before the row's first nonzero
+            const int64_t s = rp[x0];
+            int64_t lo = 0, hi = t;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (ty[mid] <= s) lo = mid; else hi = mid - 1;
+            }
+            hf[t] = (int32_t)lo;
+        } else {
+            hr[t] = -1;
+            hf[t] = (int32_t)t;
+        }
+    }
+}
+
+static unsigned grid_1d(int64_t work, int threads)
+{
+    const int64_t b = (work + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+}
+
+const Plan &get_plan(tpa_graph *g, int L, cudaStream_t s)
+{
+    auto it = g->plans_t.find(L);
+    if (it != g->plans_t.end()) return it->second;
+    Plan &P = g->plans_t[L];
+    P.L = L;
+    P.tiles = std::max<int64_t>(1, (g->n + g->m + L - 1) / L);
+    TPA_REQUIRE(P.tiles < INT32_MAX, "merge-path plan: too many tiles");
+    P.tile_x.ensure((size_t)(P.tiles + 1) * sizeof(int32_t), s);
+    P.tile_y.ensure((size_t)(P.tiles + 1) * sizeof(int64_t), s);
+    P.head_row.ensure((size_t)P.tiles * sizeof(int32_t), s);
+    P.head_first.ensure((size_t)P.tiles * sizeof(int32_t), s);
+    plan_tiles_k<<<grid_1d(P.tiles + 1, 256), 256, 0, s>>>(g->rp_t.as<int64_t>(), g->n, g->m, L, P.tiles,
+                                                            P.tile_x.as<int32_t>(), P.tile_y.as<int64_t>());
+    plan_heads_k<<<grid_1d(P.tiles, 256), 256, 0, s>>>(g->rp_t.as<int64_t>(), P.tile_x.as<int32_t>(),
+                                                       P.tile_y.as<int64_t>(), P.tiles, P.head_row.as<int32_t>(),
+                                                       P.head_first.as<int32_t>());
+    note_launch("plan", 2);
+    TPA_CHECK_LAUNCH();
+    return P;
+}
+
+// --------------------------------------------------------- dispatching ---
+struct KCfg {
+    int G, V, ITEMS, PF;
+    int KP() const { return G * V; }
+    int L() const { return (CTA / G) * ITEMS; }
+};
+
+typedef void (*SpmmFn)(Params);
+typedef void (*FixFn)(Params);
+
+static int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        TPA_CUDA(cudaGetDevice(&dev));
+        TPA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return sms;
+}
+
+// Persistent grid: resident CTAs per SM x SMs, capped by the tile count.
+template <int G, int V, int ITEMS, int PF>
+static void launch_spmm(const Params &p, cudaStream_t s)
+{
+    static int per_sm = 0;
+    if (!per_sm) {
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmm_tile_k<G, V, ITEMS, PF>, CTA, 0));
+        per_sm = std::max(per_sm, 1);
+    }
+    const int64_t grid = std::min<int64_t>(p.tiles, (int64_t)per_sm * num_sms());
+    spmm_tile_k<G, V, ITEMS, PF><<<(unsigned)grid, CTA, 0, s>>>(p);
+}
+
+template <int KP>
+static void launch_fix(const Params &p, unsigned blocks, cudaStream_t s)
+{
+    fixup_k<KP><<<blocks, FIX_WARPS * 32, 0, s>>>(p);
+}
+
+struct Variant {
+    KCfg cfg;
+    void (*spmm)(const Params &, cudaStream_t);
+    void (*fix)(const Params &, unsigned, cudaStream_t);
+};
+
+#define TPA_VARIANT(G, V, I, PF) {{G, V, I, PF}, launch_spmm<G, V, I, PF>, launch_fix<G * V>}
+static const Variant kVariants[] = {
+    TPA_VARIANT(1, 1, 8, 8),
+    TPA_VARIANT(1, 1, 6, 6),
+    TPA_VARIANT(1, 1, 12, 12),
+    TPA_VARIANT(1, 2, 8, 8),
+    TPA_VARIANT(1, 4, 8, 8),
+    TPA_VARIANT(2, 2, 8, 8),
+    TPA_VARIANT(2, 4, 16, 8),
+    TPA_VARIANT(8, 1, 16, 16),
+    TPA_VARIANT(4, 4, 16, 8),
+    TPA_VARIANT(8, 4, 16, 8),
+    TPA_VARIANT(32, 1, 16, 16),
+    TPA_VARIANT(16, 4, 16, 8),
+    TPA_VARIANT(32, 4, 32, 8),
+    TPA_VARIANT(32, 8, 32, 4),
+};
+#undef TPA_VARIANT
+
+// Padded width: the smallest power of two >= k (every power of two up to
+// KP_MAX has at least one kernel variant).
+static int kp_for(int k)
+{
+    int kp = 1;
+    while (kp < k) kp <<= 1;
+    return std::max(1, std::min(kp, KP_MAX));
+}
+
+// Default variant per padded width (the first listed with that width).
+static const Variant &pick_variant(int KP)
+{
+    for (const Variant &v : kVariants)
+        if (v.cfg.KP() == KP) return v;
+    set_error("no SpMM kernel variant for padded width %d", KP);
+    throw Fail{TPA_EINVAL};
+}
+
+int variant_count() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
+
+// ------------------------------------------------------------ CPI loop ---
+// Algorithmic bytes of one SpMV/SpMM launch over CSR(A~^T): row pointers
+// (int64), columns and values once, the iterate X[n][KP] read once and, in the
+// accumulate mode, Y[n][KP] written and r[n][k] read and written; in the
+// finalize mode r[n][k] and r~_stranger[n] read and out[n][k] written.
+static double spmm_bytes(int64_t n, int64_t m, int KP, int k, int mode, int accumulate)
+{
+    double b = 8.0 * (double)(n + 1) + 8.0 * (double)m + 4.0 * (double)n * KP;
+    if (mode == MODE_ACC)
+        b += 4.0 * (double)n * KP + (accumulate ? 8.0 * (double)n * k : 0.0);
+    else
+        b += 4.0 * (double)n * k + 4.0 * (double)n + 4.0 * (double)n * k;
+    return b;
+}
+
+static int iteration_bound(double c, double eps)
+{
+    // first i with c (1-c)^i < eps, plus a margin for FP32 rounding of the norm
+    const double b = std::log(eps / c) / std::log(1.0 - c);
+    const double i = std::max(0.0, std::ceil(b));
+    return (int)std::min(1.0e6, i) + 4;
+}
+
+void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t s)
+{
+    const int KP = kp_for(kc);
+    const Variant &var = pick_variant(KP);
+    const Plan &P = get_plan(g, var.cfg.L(), s);
+    const int64_t n = g->n;
+    Workspace &W = g->ws;
+    W.x.ensure((size_t)n * KP * sizeof(float), s);
+    W.y.ensure((size_t)n * KP * sizeof(float), s);
+    W.carry.ensure((size_t)P.tiles * KP * sizeof(float), s);
+    W.head.ensure((size_t)P.tiles * KP * sizeof(float), s);
+    W.tl1.ensure((size_t)P.tiles * KP * sizeof(double), s);
+    const unsigned fix_blocks =
+        (unsigned)std::min<int64_t>((P.tiles + FIX_WARPS - 1) / FIX_WARPS, (int64_t)4 * num_sms());
+    W.fix.ensure((size_t)fix_blocks * KP * sizeof(double), s);
+    W.ctl.ensure(CTL_BYTES, s);
+
+    ctl_init_k<<<1, 256, 0, s>>>(W.ctl.p, kc);
+    note_launch("init", 2);
+    const float c_val = (float)a.c;
+    const float pr_val = (float)(a.c * (1.0 / (double)n));
+    float *r;
+    int64_t ldr;
+    if (a.r_internal) {
+        W.r.ensure((size_t)n * KP * sizeof(float), s);
+        r = W.r.as<float>();
+        ldr = KP;
+    } else {
+        r = a.r + k0;
+        ldr = a.ldr;
+    }
+    init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, a.seeds ? a.seeds + k0 : nullptr, kc, c_val,
+                                                 pr_val, r, ldr, a.s_iter == 0 ? 1 : 0);
+    TPA_CHECK_LAUNCH();
+
+    const int last = a.t_iter >= 0 ? a.t_iter : iteration_bound(a.c, a.eps);
+    if (last == 0) {
+        if (a.tpa_final) {
+            finalize_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(r, ldr, a.r_str, (float)(1.0 + a.alpha), a.out + k0,
+                                                           a.ldo, n, kc);
+            note_launch("finalize");
+        }
+        if (a.iters_out) {
+            copy_iters_k<<<1, 256, 0, s>>>(W.ctl.p, a.iters_out + k0, kc);
+            note_launch("init");
+        }
+        TPA_CHECK_LAUNCH();
+        return;
+    }
+
+    Params p{};
+    p.rp = g->rp_t.as<int64_t>();
+    p.col = g->col_t.as<int32_t>();
+    p.val = g->val_t.as<float>();
+    p.n = n;
+    p.tile_x = P.tile_x.as<int32_t>();
+    p.tile_y = P.tile_y.as<int64_t>();
+    p.head_row = P.head_row.as<int32_t>();
+    p.head_first = P.head_first.as<int32_t>();
+    p.tiles = P.tiles;
+    p.r = r;
+    p.ldr = ldr;
+    p.out = a.out ? a.out + k0 : nullptr;
+    p.ldo = a.ldo;
+    p.r_str = a.r_str;
+    p.one_plus_alpha = (float)(1.0 + a.alpha);
+    p.decay = (float)(1.0 - a.c);
+    p.k = kc;
+    p.eps = a.eps;
+    p.carry = W.carry.as<float>();
+    p.head = W.head.as<float>();
+    p.tl1 = W.tl1.as<double>();
+    p.part = W.fix.as<double>();
+    p.ctl = W.ctl.p;
+
+    float *cur = W.x.as<float>(), *nxt = W.y.as<float>();
+    // Host-side early stop: every CHUNK iterations, read the device done flag
+    // of the chunk before last, so launches never run far past convergence.
+    const int CHUNK = 8;
+    int32_t *hflag = nullptr;
+    if (a.t_iter < 0) {
+        if (!W.hflag) TPA_CUDA(cudaHostAlloc((void **)&W.hflag, 2 * sizeof(int32_t), cudaHostAllocDefault));
+        hflag = W.hflag;
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    try {
+        if (hflag) {
+            hflag[0] = hflag[1] = 0;
+            TPA_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+            TPA_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+        }
+        int chunk = 0;
+        for (int i = 1; i <= last; ++i) {
+            p.x = cur;
+            p.y = nxt;
+            p.iter = i;
+            p.accumulate = i >= a.s_iter ? 1 : 0;
+            p.mode = (a.tpa_final && i == last) ? MODE_FINAL : MODE_ACC;
+            ProfMark pm = prof_begin(s);
+            var.spmm(p, s);
+            prof_end(pm, "spmm", spmm_bytes(n, g->m, KP, kc, p.mode, p.accumulate), s);
+            ProfMark pf = prof_begin(s);
+            var.fix(p, fix_blocks, s);
+            prof_end(pf, "fixup", 0.0, s);
+            note_launch("spmm");
+            note_launch("fixup");
+            if (p.mode == MODE_FINAL) {
+                finalize_if_done_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(W.ctl.p, r, ldr, a.r_str, p.one_plus_alpha,
+                                                                        p.out, p.ldo, n, kc);
+                note_launch("finalize");
+            }
+            TPA_CHECK_LAUNCH();
+            std::swap(cur, nxt);
+            if (hflag && i % CHUNK == 0) {
+                const int slot = chunk & 1;
+                if (chunk >= 2) {
+                    TPA_CUDA(cudaEventSynchronize(ev[slot]));
+                    if (hflag[slot]) break;
+                }
+                const CtlView cv = ctl_view(W.ctl.p);
+                TPA_CUDA(cudaMemcpyAsync(&hflag[slot], &cv.hdr->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                TPA_CUDA(cudaEventRecord(ev[slot], s));
+                ++chunk;
+            }
+        }
+        if (a.iters_out) {
+            copy_iters_k<<<1, 256, 0, s>>>(W.ctl.p, a.iters_out + k0, kc);
+            note_launch("init");
+        }
+        TPA_CHECK_LAUNCH();
+    } catch (...) {
+        if (hflag) cudaStreamSynchronize(s);
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+        throw;
+    }
+    if (hflag) TPA_CUDA(cudaStreamSynchronize(s));
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+}
+
+void run_cpi(tpa_graph *g, const CpiArgs &a, cudaStream_t s)
+{
+    for (int k0 = 0; k0 < a.k; k0 += KP_MAX) {
+        const int kc = std::min(KP_MAX, a.k - k0);
+        run_cpi_chunk(g, a, k0, kc, s);
+    }
+}
+
+}  // namespace tpa

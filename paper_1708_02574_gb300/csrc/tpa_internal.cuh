@@ -1,0 +1,153 @@
+// Internal declarations shared by the libtpa translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+
+#include "../../include/tpa.h"
+
+namespace tpa {
+
+// ---------------------------------------------------------------- errors ---
+void set_error(const char *fmt, ...);
+
+struct Fail {
+    tpa_status st;
+};
+
+#define TPA_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            ::tpa::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            throw ::tpa::Fail{e_ == cudaErrorMemoryAllocation ? TPA_ENOMEM : TPA_ECUDA}; \
+        }                                                                                 \
+    } while (0)
+
+#define TPA_REQUIRE(cond, ...)                 \
+    do {                                       \
+        if (!(cond)) {                         \
+            ::tpa::set_error(__VA_ARGS__);     \
+            throw ::tpa::Fail{TPA_EINVAL};     \
+        }                                      \
+    } while (0)
+
+#define TPA_CHECK_LAUNCH() TPA_CUDA(cudaGetLastError())
+
+// profile.cu: launch accounting and optional event timing
+void note_launch(const char *family, int count = 1);
+struct ProfMark {
+    cudaEvent_t a;
+};
+ProfMark prof_begin(cudaStream_t s);
+void prof_end(const ProfMark &m, const char *family, double bytes, cudaStream_t s);
+
+// --------------------------------------------------------------- memory ---
+// Device buffer owned by the library (cudaMallocAsync on the call's stream).
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    void ensure(size_t b, cudaStream_t s);   // grow-only
+    void release(cudaStream_t s);
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+bool is_device_ptr(const void *p);
+
+// Copy `bytes` from a host or device pointer into device memory (stream-ordered).
+void copy_in(void *dst_dev, const void *src_any, size_t bytes, cudaStream_t s);
+
+// ------------------------------------------------------ merge-path plans ---
+// A tile of the merge path between the row-end offsets of a CSR and the
+// nonzero indices.  Tile t covers path diagonals [t*L, (t+1)*L).
+struct Plan {
+    int L = 0;              // path steps per tile
+    int64_t tiles = 0;
+    DevBuf tile_x;          // int32[tiles+1]  rows fully consumed before the tile
+    DevBuf tile_y;          // int64[tiles+1]  nonzeros consumed before the tile
+    DevBuf head_row;        // int32[tiles]    row whose end falls in the tile but that started before it, or -1
+    DevBuf head_first;      // int32[tiles]    first tile holding a nonzero of that row
+};
+
+// ---------------------------------------------------------------- graph ---
+struct Workspace {
+    DevBuf x, y, r;         // iterates and accumulator
+    DevBuf carry, head, tl1;   // per-tile carries, deferred heads, per-tile L1
+    DevBuf fix;             // fixup partials
+    DevBuf ctl;             // control block (see Ctl)
+    DevBuf seeds;           // int32 seeds
+    DevBuf out;             // device staging for host outputs
+    DevBuf iters;           // int32 per-column iteration counts
+    int32_t *hflag = nullptr;   // pinned host mirror of the done flag (2 slots)
+};
+
+}  // namespace tpa
+
+struct tpa_graph {
+    int64_t n = 0, m = 0;
+    int device = 0;
+    // CSR(A~^T): rows = destinations
+    tpa::DevBuf rp_t, col_t, val_t;
+    // CSR(A~): rows = sources
+    tpa::DevBuf rp_a, col_a, val_a;
+    tpa::DevBuf outdeg;
+    // preprocessing result
+    tpa::DevBuf r_str;
+    bool has_pre = false;
+    double c = 0, eps = 0;
+    int T = 0;
+    int64_t pre_iters = 0;
+    std::map<int, tpa::Plan> plans_t;   // merge-path plans over CSR(A~^T) keyed by L
+    tpa::Workspace ws;
+};
+
+namespace tpa {
+
+// Control block living in device memory, one per CPI run.
+struct Ctl {
+    int32_t done;           // 1 once no column is alive
+    int32_t ticket;         // last-block-done counter for the fixup reduction
+    int32_t iter;           // current iteration index (written by the host-side schedule)
+    int32_t pad;
+};
+// Per-column state follows the Ctl header in the control buffer:
+//   int32 alive[kpad], int32 iters[kpad], double norm[kpad]
+
+// build.cu
+void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t m_in,
+               cudaStream_t s);
+
+// cpi.cu
+const Plan &get_plan(tpa_graph *g, int L, cudaStream_t s);
+
+enum Mode : int {
+    MODE_ACC = 0,     // y written; r += y for alive columns when i >= s_iter
+    MODE_FINAL = 1    // TPA: out = (1+alpha) (r + y) + r_str; y and r not written
+};
+
+struct CpiArgs {
+    // seeds for single-seed columns (device int32[k]); nullptr = PageRank (k = 1)
+    const int32_t *seeds = nullptr;
+    int k = 1;
+    double c = 0.15, eps = 1e-9;
+    int s_iter = 0, t_iter = -1;
+    // output: accumulation target (float32, row stride ldr, columns offset by the
+    // chunk start), or an internal [n][KP] buffer when r_internal is set
+    float *r = nullptr;
+    int64_t ldr = 1;
+    bool r_internal = false;
+    // TPA online: finalize into out with (1+alpha) and r_str on the last iteration
+    bool tpa_final = false;
+    double alpha = 0.0;
+    const float *r_str = nullptr;
+    float *out = nullptr;
+    int64_t ldo = 1;
+    int32_t *iters_out = nullptr;   // device int32[k] or nullptr
+};
+
+void run_cpi(tpa_graph *g, const CpiArgs &a, cudaStream_t s);
+
+}  // namespace tpa

@@ -1,0 +1,233 @@
+"""ctypes binding of libtpa (names follow include/tpa.h without the ``tpa_`` prefix).
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA).  Results are
+returned as CUDA torch tensors allocated on the current device, written on the
+current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+_lib = None
+
+STATUS = {0: "TPA_OK", 1: "TPA_EINVAL", 2: "TPA_ENOMEM", 3: "TPA_ECUDA", 4: "TPA_ESTATE", 5: "TPA_ETIMEOUT"}
+
+
+class TpaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library():
+    """Load libtpa.so (compiling it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or _build.stale():
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "tpa_last_error": (ctypes.c_char_p, []),
+        "tpa_build_graph": (i32, [i64, i64, P, P, P, ctypes.POINTER(P)]),
+        "tpa_free_graph": (None, [P]),
+        "tpa_graph_info": (i32, [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "tpa_get_csr": (i32, [P, i32, P, P, P, P]),
+        "tpa_preprocess": (i32, [P, f64, i32, f64, P]),
+        "tpa_get_stranger": (i32, [P, P, ctypes.POINTER(i64), P]),
+        "tpa_query": (i32, [P, P, i32, i32, P, P]),
+        "tpa_cpi": (i32, [P, P, i32, f64, f64, i32, i32, P, P, P]),
+        "tpa_cpi_exact": (i32, [P, ctypes.c_int32, f64, f64, P, P, P]),
+        "tpa_save_preprocessed": (i32, [P, ctypes.c_char_p]),
+        "tpa_load_preprocessed": (i32, [P, ctypes.c_char_p, P]),
+        "tpa_launch_count": (ctypes.c_uint64, []),
+        "tpa_profile_reset": (i32, [i32]),
+        "tpa_profile_read": (i32, [P, i32, ctypes.POINTER(i32)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise TpaError(st, library().tpa_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(a):
+    """Raw pointer of a contiguous numpy array or torch tensor."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(a.ctypes.data)
+    assert a.is_contiguous()
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def _as_i32(a):
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        return a.to(torch.int32).contiguous()
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class Graph:
+    """Owner of a ``tpa_graph`` handle."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise TpaError(1, "graph was freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            library().tpa_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def n(self) -> int:
+        return graph_info(self)[0]
+
+    @property
+    def m(self) -> int:
+        return graph_info(self)[1]
+
+
+def build_graph(n: int, src, dst) -> Graph:
+    """tpa_build_graph: row-normalised adjacency of the simple graph (Table 1)."""
+    s, d = _as_i32(src), _as_i32(dst)
+    h = ctypes.c_void_p()
+    m = len(s)
+    _check(library().tpa_build_graph(int(n), int(m), _ptr(s), _ptr(d), _stream(), ctypes.byref(h)))
+    return Graph(h)
+
+
+def graph_info(g: Graph):
+    n, m = ctypes.c_int64(), ctypes.c_int64()
+    _check(library().tpa_graph_info(g.handle, ctypes.byref(n), ctypes.byref(m)))
+    return n.value, m.value
+
+
+def get_csr(g: Graph, which: int = 0):
+    """CSR of A~^T (which=0) or A~ (which=1) as CUDA tensors (row_ptr, col, val)."""
+    torch = _torch()
+    n, m = graph_info(g)
+    rp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    col = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+    val = torch.empty(max(m, 1), dtype=torch.float32, device="cuda")
+    _check(library().tpa_get_csr(g.handle, int(which), _ptr(rp), _ptr(col), _ptr(val), _stream()))
+    return rp, col[:m], val[:m]
+
+
+def preprocess(g: Graph, c: float = 0.15, T: int = 10, eps: float = 1e-9) -> None:
+    """tpa_preprocess (Algorithm 2)."""
+    _check(library().tpa_preprocess(g.handle, float(c), int(T), float(eps), _stream()))
+
+
+def get_stranger(g: Graph):
+    torch = _torch()
+    n, _ = graph_info(g)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    it = ctypes.c_int64()
+    _check(library().tpa_get_stranger(g.handle, _ptr(out), ctypes.byref(it), _stream()))
+    return out, it.value
+
+
+def query(g: Graph, seeds, S: int = 5, out=None):
+    """tpa_query (Algorithm 3) for k single-seed queries; returns float32 [n, k]."""
+    torch = _torch()
+    s = _as_i32(seeds)
+    k = len(s)
+    n, _ = graph_info(g)
+    if out is None:
+        out = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    _check(library().tpa_query(g.handle, _ptr(s), int(k), int(S), _ptr(out), _stream()))
+    return out
+
+
+def cpi(g: Graph, seeds, c: float = 0.15, eps: float = 1e-9, s_iter: int = 0, t_iter: int = -1, out=None):
+    """tpa_cpi (Algorithm 1) for k single-seed vectors; returns (float32 [n, k], int32 iters[k])."""
+    torch = _torch()
+    s = _as_i32(seeds)
+    k = len(s)
+    n, _ = graph_info(g)
+    if out is None:
+        out = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    iters = torch.empty(k, dtype=torch.int32, device="cuda")
+    _check(library().tpa_cpi(g.handle, _ptr(s), int(k), float(c), float(eps), int(s_iter), int(t_iter),
+                             _ptr(out), _ptr(iters), _stream()))
+    return out, iters
+
+
+def cpi_exact(g: Graph, seed: int, c: float = 0.15, eps: float = 1e-9):
+    """tpa_cpi_exact: exact RWR by CPI for one seed; returns (float32 [n], iterations)."""
+    torch = _torch()
+    n, _ = graph_info(g)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    it = np.zeros(1, dtype=np.int32)
+    _check(library().tpa_cpi_exact(g.handle, int(seed), float(c), float(eps), _ptr(out), _ptr(it), _stream()))
+    return out, int(it[0])
+
+
+def save_preprocessed(g: Graph, path: str) -> None:
+    _check(library().tpa_save_preprocessed(g.handle, os.fsencode(path)))
+
+
+def load_preprocessed(g: Graph, path: str) -> None:
+    _check(library().tpa_load_preprocessed(g.handle, os.fsencode(path), _stream()))
+
+
+class _KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("alg_bytes", ctypes.c_double)]
+
+
+def launch_count() -> int:
+    """Kernel launches issued by libtpa since it was loaded."""
+    return int(library().tpa_launch_count())
+
+
+def profile_reset(timing: bool = False) -> None:
+    """Clear kernel statistics; with timing, bracket SpMV/SpMM and fixup launches with CUDA events."""
+    _check(library().tpa_profile_reset(1 if timing else 0))
+
+
+def profile_read() -> dict:
+    """Per kernel family: launches, summed event time (ms) and algorithmic bytes."""
+    cap = 64
+    arr = (_KernelStat * cap)()
+    cnt = ctypes.c_int()
+    _check(library().tpa_profile_read(ctypes.cast(arr, ctypes.c_void_p), cap, ctypes.byref(cnt)))
+    return {arr[i].name.decode(): dict(launches=int(arr[i].launches), total_ms=float(arr[i].total_ms),
+                                       alg_bytes=float(arr[i].alg_bytes)) for i in range(min(cnt.value, cap))}

@@ -1,0 +1,201 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars (the benchmark spec): CSR bit-exact; every FP32 score vector within
+L1 <= 1e-5 and max-abs <= 1e-7 of the FP64 oracle, checked per result.
+Graphs: R-MAT scale 14 (16,384 nodes, edge factor 16, a/b/c/d = .57/.19/.19/.05,
+key 1) plus small named graphs; the merge-path tiles there span many tiles and
+end in a ragged tail.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+C, S, T, EPS = 0.15, 5, 10, 1e-9
+L1_TOL, MAX_TOL = 1e-5, 1e-7
+
+
+def tpa():
+    import paper_1708_02574_gb300 as m
+    return m
+
+
+def parity(gpu, ref, tag=""):
+    g = np.asarray(gpu, dtype=np.float64)
+    diff = np.abs(g - ref)
+    l1, mx = float(diff.sum()), float(diff.max()) if diff.size else 0.0
+    assert np.isfinite(g).all(), tag
+    assert l1 <= L1_TOL and mx <= MAX_TOL, f"{tag}: L1 {l1:.3e} max-abs {mx:.3e}"
+    return l1, mx
+
+
+@pytest.fixture(scope="module")
+def rmat14():
+    s, d = synth.rmat_edges(14, 16)
+    n = 1 << 14
+    og = oracle.build_graph(n, s, d)
+    g = tpa().build_graph(n, s, d)
+    rs, it = oracle.preprocess(og, C, T, EPS)
+    tpa().preprocess(g, C, T, EPS)
+    cand = synth.nodes_with_out_edge(n, s, d)
+    return dict(n=n, s=s, d=d, og=og, g=g, rs=rs, it=it, cand=cand)
+
+
+def csr_equal(g, og):
+    t = tpa()
+    for which, (rp, col, val) in ((0, (og.rp_t, og.col_t, og.val_t)), (1, (og.rp_a, og.col_a, og.val_a))):
+        grp, gcol, gval = (a.cpu().numpy() for a in t.get_csr(g, which))
+        assert np.array_equal(grp, rp), which
+        assert np.array_equal(gcol, col), which
+        # RN32(1/outdeg) equals the FP32 rounding of the exact FP64 1/outdeg for outdeg < 2^24
+        assert np.array_equal(gval.view(np.uint32), val.astype(np.float32).view(np.uint32)), which
+
+
+def test_csr_bit_exact_rmat14(rmat14):
+    assert rmat14["g"].m == rmat14["og"].m
+    csr_equal(rmat14["g"], rmat14["og"])
+
+
+@pytest.mark.parametrize("kind,n", [("cycle", 7), ("star", 33), ("random", 300), ("complete", 12),
+                                    ("random_nodead", 1000)])
+def test_csr_bit_exact_small(kind, n):
+    n, s, d = synth.small_graph(kind, n)
+    og = oracle.build_graph(n, s, d)
+    g = tpa().build_graph(n, s, d)
+    assert g.m == og.m
+    csr_equal(g, og)
+
+
+def test_csr_degenerate():
+    t = tpa()
+    g = t.build_graph(1, np.zeros(3, np.int32), np.zeros(3, np.int32))   # only self-loops
+    assert (g.n, g.m) == (1, 0)
+    g = t.build_graph(5, np.zeros(0, np.int32), np.zeros(0, np.int32))   # no edges
+    assert (g.n, g.m) == (5, 0)
+    rp, _, _ = t.get_csr(g, 0)
+    assert rp.cpu().tolist() == [0] * 6
+    t.preprocess(g, C, T, EPS)
+    out = t.query(g, [2, 4], S).cpu().numpy()
+    og = oracle.build_graph(5, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    rs, _ = oracle.preprocess(og, C, T, EPS)
+    for j, sd in enumerate([2, 4]):
+        parity(out[:, j], oracle.query(og, sd, C, S, T, rs, EPS), f"empty graph seed {sd}")
+
+
+def test_preprocess_parity(rmat14):
+    r, it = tpa().get_stranger(rmat14["g"])
+    parity(r.cpu().numpy(), rmat14["rs"], "r_stranger")
+    assert abs(it - rmat14["it"]) <= 1, (it, rmat14["it"])
+
+
+@pytest.mark.parametrize("k", [1, 7, 32, 100, 256, 300])
+def test_query_parity(rmat14, k):
+    cand = rmat14["cand"]
+    seeds = synth.query_seeds(cand, k, key=2)
+    seeds[0] = 0                                   # the biggest hub
+    if k > 2:
+        dead = np.setdiff1d(np.arange(rmat14["n"]), cand)
+        seeds[1] = dead[0]                         # a node without out-edges
+    out = tpa().query(rmat14["g"], seeds, S).cpu().numpy()
+    assert out.shape == (rmat14["n"], k)
+    cols = range(k) if k <= 32 else list(range(8)) + list(range(k - 8, k))
+    for j in cols:
+        ref = oracle.query(rmat14["og"], int(seeds[j]), C, S, T, rmat14["rs"], EPS)
+        parity(out[:, j], ref, f"k={k} col {j} seed {seeds[j]}")
+
+
+def test_query_matches_single_seed_columns(rmat14):
+    """A batched query agrees with single-seed queries column by column (parity tolerance)."""
+    t = tpa()
+    seeds = synth.query_seeds(rmat14["cand"], 7, key=9)
+    batch = t.query(rmat14["g"], seeds, S).cpu().numpy()
+    for j in (0, 3, 6):
+        one = t.query(rmat14["g"], seeds[j:j + 1], S).cpu().numpy()[:, 0]
+        parity(batch[:, j], one.astype(np.float64), f"column {j}")
+
+
+@pytest.mark.parametrize("S_", [1, 2, 10])
+def test_query_edge_S(rmat14, S_):
+    seeds = np.array([0, 5, int(rmat14["cand"][-1])], np.int32)
+    out = tpa().query(rmat14["g"], seeds, S_).cpu().numpy()
+    for j, sd in enumerate(seeds):
+        parity(out[:, j], oracle.query(rmat14["og"], int(sd), C, S_, T, rmat14["rs"], EPS), f"S={S_} seed {sd}")
+
+
+def test_cpi_exact_parity(rmat14):
+    for sd in (0, int(rmat14["cand"][len(rmat14["cand"]) // 2])):
+        out, it = tpa().cpi_exact(rmat14["g"], sd, C, EPS)
+        ref, rit = oracle.cpi_exact(rmat14["og"], sd, C, EPS)
+        parity(out.cpu().numpy(), ref, f"exact CPI seed {sd}")
+        assert abs(it - rit) <= 1
+
+
+def test_cpi_parts_parity(rmat14):
+    """Algorithm 1 with s_iter/t_iter: neighbor part (S..T-1) and stranger part (T..inf)."""
+    seeds = np.array([0, 17, int(rmat14["cand"][3])], np.int32)
+    for s_it, t_it in ((S, T - 1), (T, -1), (0, 0), (3, 3)):
+        out, iters = tpa().cpi(rmat14["g"], seeds, C, EPS, s_it, t_it)
+        out = out.cpu().numpy()
+        for j, sd in enumerate(seeds):
+            q = np.zeros(rmat14["n"])
+            q[sd] = 1.0
+            ref, rit = oracle.cpi(rmat14["og"], q, C, EPS, s_it, None if t_it < 0 else t_it)
+            parity(out[:, j], ref, f"cpi({s_it},{t_it}) seed {sd}")
+            assert abs(int(iters[j]) - rit) <= 1
+
+
+def test_host_buffers_through_c_abi(rmat14):
+    """Host input and output pointers: the library copies in and out itself."""
+    import ctypes
+    t = tpa()
+    lib = t.library()
+    seeds = np.array([0, 11, 99], np.int32)
+    out = np.empty((rmat14["n"], 3), np.float32)
+    st = lib.tpa_query(rmat14["g"].handle, ctypes.c_void_p(seeds.ctypes.data), 3, S,
+                       ctypes.c_void_p(out.ctypes.data), None)
+    assert st == 0, lib.tpa_last_error()
+    dev = t.query(rmat14["g"], seeds, S).cpu().numpy()
+    assert np.array_equal(out, dev)
+
+
+def test_deterministic(rmat14):
+    seeds = synth.query_seeds(rmat14["cand"], 32, key=4)
+    a = tpa().query(rmat14["g"], seeds, S).cpu().numpy()
+    b = tpa().query(rmat14["g"], seeds, S).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_errors(rmat14):
+    t = tpa()
+    with pytest.raises(t.TpaError, match="EINVAL"):
+        t.query(rmat14["g"], [rmat14["n"]], S)
+    with pytest.raises(t.TpaError, match="EINVAL"):
+        t.query(rmat14["g"], [-1], S)
+    with pytest.raises(t.TpaError, match="EINVAL"):
+        t.query(rmat14["g"], [0], T + 1)
+    with pytest.raises(t.TpaError, match="EINVAL"):
+        t.preprocess(rmat14["g"], 1.5, T, EPS)
+    with pytest.raises(t.TpaError, match="EINVAL"):
+        t.build_graph(4, np.array([0, 4], np.int32), np.array([1, 2], np.int32))
+    g2 = t.build_graph(4, np.array([0, 1], np.int32), np.array([1, 2], np.int32))
+    with pytest.raises(t.TpaError, match="ESTATE"):
+        t.query(g2, [0], S)
+
+
+def test_save_load_preprocessed(rmat14, tmp_path):
+    t = tpa()
+    p = str(tmp_path / "str.bin")
+    t.save_preprocessed(rmat14["g"], p)
+    g2 = t.build_graph(rmat14["n"], rmat14["s"], rmat14["d"])
+    t.load_preprocessed(g2, p)
+    a, ia = t.get_stranger(rmat14["g"])
+    b, ib = t.get_stranger(g2)
+    assert ia == ib and np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+    seeds = [0, 3]
+    assert np.array_equal(t.query(g2, seeds, S).cpu().numpy(), t.query(rmat14["g"], seeds, S).cpu().numpy())
+    small = t.build_graph(5, np.array([0, 1], np.int32), np.array([1, 2], np.int32))
+    with pytest.raises(t.TpaError, match="EINVAL"):
+        t.load_preprocessed(small, p)
