@@ -118,6 +118,30 @@ tpa_status tpa_cpi_exact(tpa_graph *g, int32_t seed, double c, double eps, float
 tpa_status tpa_save_preprocessed(const tpa_graph *g, const char *path);
 tpa_status tpa_load_preprocessed(tpa_graph *g, const char *path, void *stream);
 
+/* ---------------------------------------------------- kernel tuning ---
+ * Not part of the paper's method.  Process-wide settings of the SpMV/SpMM
+ * that runs each CPI iteration; an autotuner times the variants on a graph
+ * and keeps the fastest.  Results do not depend on the choice beyond FP32
+ * rounding order. */
+
+/* Number of compiled SpMV/SpMM variants. */
+int tpa_variant_count(void);
+
+/* Shape of variant idx: padded batch width kp (columns per CPI chunk), lanes
+ * per merge-path walker, columns per lane, path steps per walker, threads per
+ * CTA.  TPA_EINVAL for an index out of range. */
+tpa_status tpa_variant_info(int idx, int *kp, int *lanes, int *cols_per_lane, int *items, int *threads);
+
+/* Use variant idx for padded width kp (a power of two <= 256); idx = -1
+ * restores the default.  TPA_EINVAL if the variant has another width. */
+tpa_status tpa_set_variant(int kp, int idx);
+
+/* Seeds per CPI chunk when tpa_query or tpa_cpi get k seeds: chunks of
+ * `width` columns run one after another (a power of two <= 256; default 256).
+ * A narrow chunk keeps its iterates X[n][width] in L2. */
+tpa_status tpa_set_batch_width(int width);
+int tpa_get_batch_width(void);
+
 /* ------------------------------------------------------ measurement ---
  * Not part of the paper's method: launch accounting and kernel timing for
  * benchmarks.  The statistics are process-wide and thread-safe. */

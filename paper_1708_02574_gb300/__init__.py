@@ -27,4 +27,8 @@ from .tpa import (  # noqa: F401
     preprocess,
     query,
     save_preprocessed,
+    set_batch_width,
+    get_batch_width,
+    set_variant,
+    variants,
 )

@@ -14,17 +14,18 @@
 
 namespace tpa {
 
-static thread_local std::string g_err;
+// Fixed per-thread buffer: recording an error never allocates.
+static thread_local char g_err[1024];
 
 void set_error(const char *fmt, ...)
 {
-    char buf[1024];
     va_list ap;
     va_start(ap, fmt);
-    vsnprintf(buf, sizeof(buf), fmt, ap);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
-    g_err = buf;
 }
+
+void clear_error() { g_err[0] = '\0'; }
 
 void DevBuf::ensure(size_t b, cudaStream_t s)
 {
@@ -91,7 +92,7 @@ static std::vector<int32_t> read_seeds(const int32_t *seeds, int k, int64_t n, c
 using namespace tpa;
 
 #define API_BEGIN \
-    g_err.clear(); \
+    clear_error(); \
     try {
 #define API_END                                   \
     }                                             \
@@ -110,7 +111,7 @@ using namespace tpa;
 
 extern "C" {
 
-const char *tpa_last_error(void) { return g_err.c_str(); }
+const char *tpa_last_error(void) { return g_err; }
 
 tpa_status tpa_build_graph(int64_t n, int64_t m_edges, const int32_t *src, const int32_t *dst, void *stream,
                            tpa_graph **out)

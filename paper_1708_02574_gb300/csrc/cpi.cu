@@ -32,6 +32,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <vector>
 
@@ -129,6 +130,25 @@ __device__ __forceinline__ void st_row(float *p, const float (&v)[V])
     } else {
         reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
         reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void ld_row_smem(const float *p, float (&o)[V])
+{
+    if constexpr (V == 1) {
+        o[0] = p[0];
+    } else if constexpr (V == 2) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        o[0] = t.x; o[1] = t.y;
+    } else if constexpr (V == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else {
+        const float4 a = reinterpret_cast<const float4 *>(p)[0];
+        const float4 b = reinterpret_cast<const float4 *>(p)[1];
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+        o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
     }
 }
 
@@ -328,6 +348,172 @@ __global__ void __launch_bounds__(CTA) spmm_tile_k(Params p)
 #pragma unroll
             for (int w = 0; w < CTA / 32; ++w) sum += S.l1[w][c];
             p.tl1[t * KP + c] = sum;
+        }
+    }
+}
+
+// ------------------------------------------------ narrow-batch kernel ---
+// Warp-level merge-path SpMV/SpMM for V <= 8 columns per lane (V = 1: one
+// vector; V = 2..8: the block of iterates X[n][V] of a small batch stays in
+// L2 while the CSR streams once per V seeds).  Every warp owns whole tiles of
+// L = 32 * ITEMS path steps and needs no block-wide barrier:
+//   1. stage the tile's row ends and the products val * X[col][0..V) of its
+//      nonzeros (coalesced, branch-free, ITEMS gathers in flight per lane)
+//      into the warp's shared-memory slice;
+//   2. each lane walks its ITEMS steps, keeping the current row end in a
+//      register, and writes finished row sums to shared memory;
+//   3. a shuffle segmented scan adds the carry of earlier lanes to each
+//      lane's first row and yields the tile carry;
+//   4. the epilogue runs lane-per-row over the tile's rows (coalesced y, r,
+//      out); the tile's first row is deferred to the fixup when it started
+//      in an earlier tile.
+// Vector arrays first: every row of prod/rowsum starts on a V*4-byte boundary
+// (float2/float4 shared-memory accesses), and the slice size is a multiple of
+// 16 bytes so every warp's slice starts aligned too.
+template <int V, int ITEMS>
+struct __align__(16) WarpTile {
+    static constexpr int L = 32 * ITEMS;
+    float prod[L][V];
+    float rowsum[L][V];
+    int32_t end[L + 4];
+};
+
+template <int V, int ITEMS, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, (V <= 2 ? 1536 : 1024) / (WARPS * 32)) spmvw_tile_k(Params p)
+{
+    using WT = WarpTile<V, ITEMS>;
+    static_assert(offsetof(WT, prod) % 16 == 0 && offsetof(WT, rowsum) % 16 == 0, "vector rows must be aligned");
+    static_assert((V * sizeof(float)) % (V == 1 ? 4 : V == 2 ? 8 : 16) == 0, "row width");
+    static_assert(sizeof(WT) % 16 == 0, "warp slices must stay 16-byte aligned");
+    __shared__ WT S_all[WARPS];
+    const CtlView cv = ctl_view(p.ctl);
+    if (*(volatile int32_t *)&cv.hdr->done) return;
+    int alive[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) alive[j] = cv.alive[j];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WT &S = S_all[warp];
+
+    for (int64_t t = (int64_t)blockIdx.x * WARPS + warp; t < p.tiles; t += (int64_t)gridDim.x * WARPS) {
+        const int32_t x0 = p.tile_x[t], x1 = p.tile_x[t + 1];
+        const int64_t y0 = p.tile_y[t], y1 = p.tile_y[t + 1];
+        const int nrows = x1 - x0, nnz = (int)(y1 - y0);
+        const bool defer_first = p.head_row[t] >= 0;
+        __syncwarp();   // the previous tile is done with this warp's slice
+
+        // 1. row ends and products
+        for (int i = lane; i < nrows; i += 32) S.end[i] = (int)(__ldcs(p.rp + x0 + i + 1) - y0);
+        if (lane == 0) S.end[nrows] = 0x7fffffff;
+        {
+            int32_t c[ITEMS];
+            float v[ITEMS];
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const int i = lane + j * 32;
+                c[j] = i < nnz ? __ldcs(p.col + y0 + i) : 0;
+                v[j] = i < nnz ? __ldcs(p.val + y0 + i) : 0.0f;
+            }
+            float xv[ITEMS][V];
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if (lane + j * 32 < nnz) {
+                    ld_row<V>(p.x + (int64_t)c[j] * V, xv[j]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) xv[j][q] = 0.0f;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j)
+                if (lane + j * 32 < nnz) {
+                    float pr[V];
+#pragma unroll
+                    for (int q = 0; q < V; ++q) pr[q] = v[j] * xv[j][q];
+                    st_row<V>(&S.prod[lane + j * 32][0], pr);
+                }
+        }
+        __syncwarp();
+
+        // 2. merge-path walk in shared memory
+        const int d = min(lane * ITEMS, nrows + nnz);
+        int lo = max(0, d - nnz), hi = min(d, nrows);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (S.end[mid] + mid + 1 <= d) lo = mid + 1; else hi = mid;
+        }
+        int xs = lo, ys = d - lo;
+        const int avail = nrows + nnz - d;
+        int row_end = S.end[xs];
+        float acc[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) acc[q] = 0.0f;
+        int first = -1;
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            if (it < avail) {
+                if (ys < row_end) {
+                    float pr[V];
+                    ld_row_smem<V>(&S.prod[ys][0], pr);
+#pragma unroll
+                    for (int q = 0; q < V; ++q) acc[q] += pr[q];
+                    ++ys;
+                } else {
+                    st_row<V>(&S.rowsum[xs][0], acc);
+                    if (first < 0) first = xs;
+#pragma unroll
+                    for (int q = 0; q < V; ++q) acc[q] = 0.0f;
+                    ++xs;
+                    row_end = S.end[xs];
+                }
+            }
+        }
+
+        // 3. segmented inclusive scan of (row, partial) over the lanes
+        const int key = xs;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int k2 = __shfl_up_sync(0xffffffffu, key, off);
+            const bool take = lane >= off && k2 == key;
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const float v2 = __shfl_up_sync(0xffffffffu, acc[q], off);
+                if (take) acc[q] += v2;
+            }
+        }
+        float prev[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) prev[q] = __shfl_up_sync(0xffffffffu, acc[q], 1);
+        __syncwarp();   // rowsum writes of the walk are visible
+        if (first >= 0 && lane > 0) {
+#pragma unroll
+            for (int q = 0; q < V; ++q) S.rowsum[first][q] += prev[q];
+        }
+        if (lane == 31) st_row<V>(p.carry + t * V, acc);
+        __syncwarp();
+
+        // 4. coalesced epilogue, lane per row
+        double l1[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) l1[q] = 0.0;
+        for (int i = lane; i < nrows; i += 32) {
+            float sum[V];
+            ld_row_smem<V>(&S.rowsum[i][0], sum);
+            if (i == 0 && defer_first) {
+                st_row<V>(p.head + t * V, sum);
+                continue;
+            }
+            epilogue<V, V>(p, (int64_t)(x0 + i), 0, sum, alive, l1);
+        }
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            double a = l1[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            l1[q] = a;
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < V; ++q) p.tl1[t * V + q] = l1[q];
         }
     }
 }
@@ -568,8 +754,9 @@ const Plan &get_plan(tpa_graph *g, int L, cudaStream_t s)
 // --------------------------------------------------------- dispatching ---
 struct KCfg {
     int G, V, ITEMS, PF;
+    int NT;   // threads per CTA
     int KP() const { return G * V; }
-    int L() const { return (CTA / G) * ITEMS; }
+    int L() const { return (NT / G) * ITEMS; }
 };
 
 typedef void (*SpmmFn)(Params);
@@ -599,6 +786,18 @@ static void launch_spmm(const Params &p, cudaStream_t s)
     spmm_tile_k<G, V, ITEMS, PF><<<(unsigned)grid, CTA, 0, s>>>(p);
 }
 
+template <int V, int ITEMS, int WARPS>
+static void launch_spmvw(const Params &p, cudaStream_t s)
+{
+    static int per_sm = 0;
+    if (!per_sm) {
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmvw_tile_k<V, ITEMS, WARPS>, WARPS * 32, 0));
+        per_sm = std::max(per_sm, 1);
+    }
+    const int64_t grid = std::min<int64_t>((p.tiles + WARPS - 1) / WARPS, (int64_t)per_sm * num_sms());
+    spmvw_tile_k<V, ITEMS, WARPS><<<(unsigned)grid, WARPS * 32, 0, s>>>(p);
+}
+
 template <int KP>
 static void launch_fix(const Params &p, unsigned blocks, cudaStream_t s)
 {
@@ -611,11 +810,18 @@ struct Variant {
     void (*fix)(const Params &, unsigned, cudaStream_t);
 };
 
-#define TPA_VARIANT(G, V, I, PF) {{G, V, I, PF}, launch_spmm<G, V, I, PF>, launch_fix<G * V>}
+#define TPA_VARIANT(G, V, I, PF) {{G, V, I, PF, CTA}, launch_spmm<G, V, I, PF>, launch_fix<G * V>}
+#define TPA_VARIANTW(V, I, W) {{1, V, I, I, 32}, launch_spmvw<V, I, W>, launch_fix<V>}
 static const Variant kVariants[] = {
+    TPA_VARIANTW(1, 8, 8),
+    TPA_VARIANTW(1, 6, 8),
+    TPA_VARIANTW(1, 12, 8),
+    TPA_VARIANTW(2, 8, 8),
+    TPA_VARIANTW(4, 8, 4),
+    TPA_VARIANTW(4, 4, 8),
+    TPA_VARIANTW(8, 4, 4),
+    TPA_VARIANTW(8, 2, 8),
     TPA_VARIANT(1, 1, 8, 8),
-    TPA_VARIANT(1, 1, 6, 6),
-    TPA_VARIANT(1, 1, 12, 12),
     TPA_VARIANT(1, 2, 8, 8),
     TPA_VARIANT(1, 4, 8, 8),
     TPA_VARIANT(2, 2, 8, 8),
@@ -629,6 +835,7 @@ static const Variant kVariants[] = {
     TPA_VARIANT(32, 8, 32, 4),
 };
 #undef TPA_VARIANT
+#undef TPA_VARIANTW
 
 // Padded width: the smallest power of two >= k (every power of two up to
 // KP_MAX has at least one kernel variant).
@@ -639,16 +846,22 @@ static int kp_for(int k)
     return std::max(1, std::min(kp, KP_MAX));
 }
 
-// Default variant per padded width (the first listed with that width).
+constexpr int NUM_VARIANTS = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+// Variant chosen per padded width (index into kVariants, -1 = default).
+static int g_forced[KP_MAX + 1];
+static bool g_forced_init = false;
+// Seeds per CPI chunk in batched calls (a power of two <= KP_MAX).
+static int g_chunk = KP_MAX;
+
+// The forced variant for a padded width, else the first listed with that width.
 static const Variant &pick_variant(int KP)
 {
+    if (g_forced_init && KP <= KP_MAX && g_forced[KP] >= 0) return kVariants[g_forced[KP]];
     for (const Variant &v : kVariants)
         if (v.cfg.KP() == KP) return v;
     set_error("no SpMM kernel variant for padded width %d", KP);
     throw Fail{TPA_EINVAL};
 }
-
-int variant_count() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
 
 // ------------------------------------------------------------ CPI loop ---
 // Algorithmic bytes of one SpMV/SpMM launch over CSR(A~^T): row pointers
@@ -816,10 +1029,67 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
 
 void run_cpi(tpa_graph *g, const CpiArgs &a, cudaStream_t s)
 {
-    for (int k0 = 0; k0 < a.k; k0 += KP_MAX) {
-        const int kc = std::min(KP_MAX, a.k - k0);
+    for (int k0 = 0; k0 < a.k; k0 += g_chunk) {
+        const int kc = std::min(g_chunk, a.k - k0);
         run_cpi_chunk(g, a, k0, kc, s);
     }
 }
+
+}  // namespace tpa
+
+using namespace tpa;
+
+extern "C" {
+
+int tpa_variant_count(void) { return NUM_VARIANTS; }
+
+tpa_status tpa_variant_info(int idx, int *kp, int *lanes, int *cols_per_lane, int *items, int *threads)
+{
+    if (idx < 0 || idx >= NUM_VARIANTS) {
+        set_error("tpa_variant_info: index %d outside [0, %d)", idx, NUM_VARIANTS);
+        return TPA_EINVAL;
+    }
+    const KCfg &c = kVariants[idx].cfg;
+    if (kp) *kp = c.KP();
+    if (lanes) *lanes = c.G;
+    if (cols_per_lane) *cols_per_lane = c.V;
+    if (items) *items = c.ITEMS;
+    if (threads) *threads = c.NT;
+    return TPA_OK;
+}
+
+tpa_status tpa_set_variant(int kp, int idx)
+{
+    if (kp < 1 || kp > KP_MAX || (kp & (kp - 1))) {
+        set_error("tpa_set_variant: width %d is not a power of two in [1, %d]", kp, KP_MAX);
+        return TPA_EINVAL;
+    }
+    if (idx >= NUM_VARIANTS || (idx >= 0 && kVariants[idx].cfg.KP() != kp)) {
+        set_error("tpa_set_variant: variant %d does not have width %d", idx, kp);
+        return TPA_EINVAL;
+    }
+    if (!g_forced_init) {
+        for (int i = 0; i <= KP_MAX; ++i) g_forced[i] = -1;
+        g_forced_init = true;
+    }
+    g_forced[kp] = idx < 0 ? -1 : idx;
+    return TPA_OK;
+}
+
+tpa_status tpa_set_batch_width(int width)
+{
+    if (width < 1 || width > KP_MAX || (width & (width - 1))) {
+        set_error("tpa_set_batch_width: %d is not a power of two in [1, %d]", width, KP_MAX);
+        return TPA_EINVAL;
+    }
+    g_chunk = width;
+    return TPA_OK;
+}
+
+int tpa_get_batch_width(void) { return g_chunk; }
+
+}  // extern "C"
+
+namespace tpa {
 
 }  // namespace tpa

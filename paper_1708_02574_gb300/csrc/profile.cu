@@ -57,6 +57,8 @@ void note_launch(const char *family, int count)
     g_stats[family].launches += count;
 }
 
+void note_launch_count(int count) { g_launches += (uint64_t)count; }
+
 ProfMark prof_begin(cudaStream_t s)
 {
     ProfMark m{nullptr};

@@ -13,6 +13,7 @@ namespace tpa {
 
 // ---------------------------------------------------------------- errors ---
 void set_error(const char *fmt, ...);
+void clear_error();
 
 struct Fail {
     tpa_status st;
@@ -39,6 +40,7 @@ struct Fail {
 
 // profile.cu: launch accounting and optional event timing
 void note_launch(const char *family, int count = 1);
+void note_launch_count(int count);   // counter only; never allocates
 struct ProfMark {
     cudaEvent_t a;
 };

@@ -48,6 +48,12 @@ def library():
         "tpa_save_preprocessed": (i32, [P, ctypes.c_char_p]),
         "tpa_load_preprocessed": (i32, [P, ctypes.c_char_p, P]),
         "tpa_launch_count": (ctypes.c_uint64, []),
+        "tpa_variant_count": (i32, []),
+        "tpa_variant_info": (i32, [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                   ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "tpa_set_variant": (i32, [i32, i32]),
+        "tpa_set_batch_width": (i32, [i32]),
+        "tpa_get_batch_width": (i32, []),
         "tpa_profile_reset": (i32, [i32]),
         "tpa_profile_read": (i32, [P, i32, ctypes.POINTER(i32)]),
     }
@@ -231,3 +237,27 @@ def profile_read() -> dict:
     _check(library().tpa_profile_read(ctypes.cast(arr, ctypes.c_void_p), cap, ctypes.byref(cnt)))
     return {arr[i].name.decode(): dict(launches=int(arr[i].launches), total_ms=float(arr[i].total_ms),
                                        alg_bytes=float(arr[i].alg_bytes)) for i in range(min(cnt.value, cap))}
+
+
+def variants() -> list[dict]:
+    """Compiled SpMV/SpMM variants: padded width, lanes per walker, columns per lane, steps, threads."""
+    lib = library()
+    out = []
+    for i in range(lib.tpa_variant_count()):
+        v = [ctypes.c_int() for _ in range(5)]
+        _check(lib.tpa_variant_info(i, *[ctypes.byref(x) for x in v]))
+        out.append(dict(index=i, kp=v[0].value, lanes=v[1].value, cols_per_lane=v[2].value, items=v[3].value,
+                        threads=v[4].value))
+    return out
+
+
+def set_variant(kp: int, idx: int) -> None:
+    _check(library().tpa_set_variant(int(kp), int(idx)))
+
+
+def set_batch_width(width: int) -> None:
+    _check(library().tpa_set_batch_width(int(width)))
+
+
+def get_batch_width() -> int:
+    return int(library().tpa_get_batch_width())
