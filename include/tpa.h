@@ -118,6 +118,33 @@ tpa_status tpa_cpi_exact(tpa_graph *g, int32_t seed, double c, double eps, float
 tpa_status tpa_save_preprocessed(const tpa_graph *g, const char *path);
 tpa_status tpa_load_preprocessed(tpa_graph *g, const char *path, void *stream);
 
+/*
+ * One propagation step of CPI for a single vector that allocates nothing.
+ * The paper has no counterpart: this is an extra entry point for callers that
+ * cannot allocate device memory when they want a step -- for example a
+ * serving process whose GPU memory is all reserved by another allocator, or a
+ * latency-critical loop that must avoid cudaMalloc/cudaFree and the
+ * synchronisation they imply.
+ *
+ * Computes y = (1-c) A~^T x over the caller's CSR of A~^T (row_ptr int64[n+1],
+ * col int32[m], val float32[m]; rows = destinations), adds y into r when r is
+ * not NULL, and writes ||y||_1 (FP64) to l1[0] when l1 is not NULL.  Every
+ * array must be device memory; the call is stream-ordered on `stream`.
+ *
+ * Scratch lives in a file-scope device array of TPA_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) that every GPU loading the library holds until the process exits;
+ * it fits graphs with n + m up to about 119 million (TPA_EINVAL beyond, with
+ * the needed size in tpa_last_error).  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one array, so calls whose
+ * GPU work overlaps (other streams, other threads) race and give wrong
+ * results; serialise them.  Each call clears the counters it needs before use.
+ */
+#define TPA_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+tpa_status tpa_cpi_step_noalloc(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                                const float *val, double c, const float *x, float *y, float *r,
+                                double *l1, void *stream);
+
 /* ---------------------------------------------------- kernel tuning ---
  * Not part of the paper's method.  Process-wide settings of the SpMV/SpMM
  * that runs each CPI iteration; an autotuner times the variants on a graph

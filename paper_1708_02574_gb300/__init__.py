@@ -16,6 +16,7 @@ from .tpa import (  # noqa: F401
     build_graph,
     cpi,
     cpi_exact,
+    cpi_step_noalloc,
     get_csr,
     get_stranger,
     graph_info,

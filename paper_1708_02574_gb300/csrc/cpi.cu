@@ -1027,6 +1027,111 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     if (ev[1]) cudaEventDestroy(ev[1]);
 }
 
+// ------------------------------------------------ single step, no alloc ---
+// One propagation step for one vector over caller-provided CSR(A~^T), with
+// every scratch array carved out of a caller-provided device buffer.  Error
+// reporting is by return value: this path throws nothing and allocates
+// nothing (it backs the scratch-free entry point).
+namespace {
+constexpr int STEP_ITEMS = 8;
+constexpr int STEP_WARPS = 8;
+constexpr int STEP_L = 32 * STEP_ITEMS;
+constexpr int STEP_FIX_BLOCKS = 256;
+
+__host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct StepLayout {
+    size_t tile_x, tile_y, head_row, head_first, carry, head, tl1, part, ctl, total;
+};
+
+StepLayout step_layout(int64_t tiles)
+{
+    StepLayout L;
+    size_t off = 0;
+    L.tile_x = off;     off += align256((size_t)(tiles + 1) * sizeof(int32_t));
+    L.tile_y = off;     off += align256((size_t)(tiles + 1) * sizeof(int64_t));
+    L.head_row = off;   off += align256((size_t)tiles * sizeof(int32_t));
+    L.head_first = off; off += align256((size_t)tiles * sizeof(int32_t));
+    L.carry = off;      off += align256((size_t)tiles * sizeof(float));
+    L.head = off;       off += align256((size_t)tiles * sizeof(float));
+    L.tl1 = off;        off += align256((size_t)tiles * sizeof(double));
+    L.part = off;       off += align256((size_t)STEP_FIX_BLOCKS * sizeof(double));
+    L.ctl = off;        off += align256(CTL_BYTES);
+    L.total = off;
+    return L;
+}
+
+__global__ void copy_norm_k(const void *ctl, double *out)
+{
+    const CtlView cv = ctl_view(const_cast<void *>(ctl));
+    out[0] = cv.norm[0];
+}
+}  // namespace
+
+size_t step1_scratch_bytes(int64_t n, int64_t m)
+{
+    const int64_t tiles = std::max<int64_t>(1, (n + m + STEP_L - 1) / STEP_L);
+    return step_layout(tiles).total;
+}
+
+cudaError_t run_step1(const int64_t *rp, const int32_t *col, const float *val, int64_t n, int64_t m, double c,
+                      const float *x, float *y, float *r, double *l1, unsigned char *scratch, cudaStream_t s)
+{
+    const int64_t tiles = std::max<int64_t>(1, (n + m + STEP_L - 1) / STEP_L);
+    const StepLayout L = step_layout(tiles);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmvw_tile_k<1, STEP_ITEMS, STEP_WARPS>,
+                                                          STEP_WARPS * 32, 0);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(per_sm, 1);
+
+    Params p{};
+    p.rp = rp;
+    p.col = col;
+    p.val = val;
+    p.n = n;
+    p.tile_x = reinterpret_cast<int32_t *>(scratch + L.tile_x);
+    p.tile_y = reinterpret_cast<int64_t *>(scratch + L.tile_y);
+    p.head_row = reinterpret_cast<int32_t *>(scratch + L.head_row);
+    p.head_first = reinterpret_cast<int32_t *>(scratch + L.head_first);
+    p.tiles = tiles;
+    p.x = x;
+    p.y = y;
+    p.r = r;
+    p.ldr = 1;
+    p.decay = (float)(1.0 - c);
+    p.k = 1;
+    p.mode = MODE_ACC;
+    p.accumulate = r ? 1 : 0;
+    p.iter = 1;
+    p.eps = 0.0;
+    p.carry = reinterpret_cast<float *>(scratch + L.carry);
+    p.head = reinterpret_cast<float *>(scratch + L.head);
+    p.tl1 = reinterpret_cast<double *>(scratch + L.tl1);
+    p.part = reinterpret_cast<double *>(scratch + L.part);
+    p.ctl = scratch + L.ctl;
+
+    plan_tiles_k<<<grid_1d(tiles + 1, 256), 256, 0, s>>>(rp, n, m, STEP_L, tiles, const_cast<int32_t *>(p.tile_x),
+                                                          const_cast<int64_t *>(p.tile_y));
+    plan_heads_k<<<grid_1d(tiles, 256), 256, 0, s>>>(rp, p.tile_x, p.tile_y, tiles, const_cast<int32_t *>(p.head_row),
+                                                     const_cast<int32_t *>(p.head_first));
+    ctl_init_k<<<1, 256, 0, s>>>(p.ctl, 1);   // done, ticket and alive start cleared for every call
+    const int64_t grid = std::min<int64_t>((tiles + STEP_WARPS - 1) / STEP_WARPS, (int64_t)per_sm * sms);
+    spmvw_tile_k<1, STEP_ITEMS, STEP_WARPS><<<(unsigned)grid, STEP_WARPS * 32, 0, s>>>(p);
+    const unsigned fb = (unsigned)std::min<int64_t>((tiles + FIX_WARPS - 1) / FIX_WARPS, STEP_FIX_BLOCKS);
+    fixup_k<1><<<fb, FIX_WARPS * 32, 0, s>>>(p);
+    int launches = 5;
+    if (l1) {
+        copy_norm_k<<<1, 1, 0, s>>>(p.ctl, l1);
+        ++launches;
+    }
+    note_launch_count(launches);
+    return cudaGetLastError();
+}
+
 void run_cpi(tpa_graph *g, const CpiArgs &a, cudaStream_t s)
 {
     for (int k0 = 0; k0 < a.k; k0 += g_chunk) {

@@ -152,4 +152,11 @@ struct CpiArgs {
 
 void run_cpi(tpa_graph *g, const CpiArgs &a, cudaStream_t s);
 
+// One CPI propagation step for a single vector with all scratch taken from
+// `scratch` (at least step1_scratch_bytes(n, m) bytes of device memory).
+// Throws nothing and allocates nothing; returns the first CUDA error.
+size_t step1_scratch_bytes(int64_t n, int64_t m);
+cudaError_t run_step1(const int64_t *rp, const int32_t *col, const float *val, int64_t n, int64_t m, double c,
+                      const float *x, float *y, float *r, double *l1, unsigned char *scratch, cudaStream_t s);
+
 }  // namespace tpa

@@ -47,6 +47,7 @@ def library():
         "tpa_cpi_exact": (i32, [P, ctypes.c_int32, f64, f64, P, P, P]),
         "tpa_save_preprocessed": (i32, [P, ctypes.c_char_p]),
         "tpa_load_preprocessed": (i32, [P, ctypes.c_char_p, P]),
+        "tpa_cpi_step_noalloc": (i32, [i64, i64, P, P, P, f64, P, P, P, P, P]),
         "tpa_launch_count": (ctypes.c_uint64, []),
         "tpa_variant_count": (i32, []),
         "tpa_variant_info": (i32, [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -261,3 +262,11 @@ def set_batch_width(width: int) -> None:
 
 def get_batch_width() -> int:
     return int(library().tpa_get_batch_width())
+
+
+def cpi_step_noalloc(n: int, m: int, row_ptr, col, val, c: float, x, y, r=None, l1=None) -> None:
+    """tpa_cpi_step_noalloc: y = (1-c) A~^T x (and r += y, l1[0] = ||y||_1) with no allocation.
+
+    All tensors must be CUDA tensors; the CSR is that of A~^T (rows = destinations)."""
+    _check(library().tpa_cpi_step_noalloc(int(n), int(m), _ptr(row_ptr), _ptr(col), _ptr(val), float(c), _ptr(x),
+                                          _ptr(y), _ptr(r), _ptr(l1), _stream()))
