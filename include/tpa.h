@@ -169,6 +169,12 @@ tpa_status tpa_set_variant(int kp, int idx);
 tpa_status tpa_set_batch_width(int width);
 int tpa_get_batch_width(void);
 
+/* Direction choice in tpa_query (default on): for chunks of up to 8 seeds,
+ * each with at most 256 out-edges, and S >= 4, the sparse iterates x1 and x2
+ * are pushed along CSR(A~) instead of pulled over all of A~^T; results differ
+ * only by FP32 rounding order.  enable = 0 pulls every iteration. */
+tpa_status tpa_set_push(int enable);
+
 /* ------------------------------------------------------ measurement ---
  * Not part of the paper's method: launch accounting and kernel timing for
  * benchmarks.  The statistics are process-wide and thread-safe. */

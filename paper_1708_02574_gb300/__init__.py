@@ -29,6 +29,7 @@ from .tpa import (  # noqa: F401
     query,
     save_preprocessed,
     set_batch_width,
+    set_push,
     get_batch_width,
     set_variant,
     variants,

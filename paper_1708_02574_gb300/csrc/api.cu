@@ -289,6 +289,8 @@ tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *ou
     a.r_str = g->r_str.as<float>();
     a.out = dout;
     a.ldo = k;
+    std::vector<int32_t> od = seed_outdegrees(g, a.seeds, k, s);
+    a.seed_outdeg = od.data();
     run_cpi(g, a, s);
     if (host_out) {
         TPA_CUDA(cudaMemcpyAsync(out, dout, (size_t)g->n * k * sizeof(float), cudaMemcpyDeviceToHost, s));

@@ -46,9 +46,12 @@ constexpr int CTA = 256;
 // Control buffer layout (bytes): Ctl header, int32 alive[KP_MAX], int32 iters[KP_MAX], double norm[KP_MAX]
 struct CtlView {
     Ctl *hdr;
-    int32_t *alive;
-    int32_t *iters;
-    double *norm;
+    int32_t *alive;   // column still running (its iterate is accumulated)
+    int32_t *iters;   // last iteration computed per column
+    int32_t *own;     // push path: x2 belongs to r (the column passed the test after x1)
+    int32_t *pad;
+    double *norm;     // last ||x_i||_1 per column
+    double *norm1;    // push path: ||x1||_1 per column
 };
 __host__ __device__ inline CtlView ctl_view(void *base)
 {
@@ -56,10 +59,13 @@ __host__ __device__ inline CtlView ctl_view(void *base)
     v.hdr = reinterpret_cast<Ctl *>(base);
     v.alive = reinterpret_cast<int32_t *>(v.hdr + 1);
     v.iters = v.alive + KP_MAX;
-    v.norm = reinterpret_cast<double *>(v.iters + KP_MAX);
+    v.own = v.iters + KP_MAX;
+    v.pad = v.own + KP_MAX;
+    v.norm = reinterpret_cast<double *>(v.pad + KP_MAX);
+    v.norm1 = v.norm + KP_MAX;
     return v;
 }
-constexpr size_t CTL_BYTES = sizeof(Ctl) + 2 * KP_MAX * sizeof(int32_t) + KP_MAX * sizeof(double);
+constexpr size_t CTL_BYTES = sizeof(Ctl) + 4 * KP_MAX * sizeof(int32_t) + 2 * KP_MAX * sizeof(double);
 
 struct Params {
     // CSR(A~^T)
@@ -92,9 +98,13 @@ struct Params {
     // per-tile scratch
     float *carry;    // [tiles][KP]
     float *head;     // [tiles][KP]
-    double *tl1;     // [tiles][KP]
+    float *tl1;      // [tiles][KP] per-tile L1 partials (FP32; FP64 only across blocks)
     double *part;    // [fix blocks][KP]
     void *ctl;
+    // push path: the first pulled iteration also adds its input x2 to r for
+    // the columns flagged in own
+    int own_add;
+    const int32_t *own;
 };
 
 // ------------------------------------------------------------- helpers ---
@@ -152,10 +162,43 @@ __device__ __forceinline__ void ld_row_smem(const float *p, float (&o)[V])
     }
 }
 
+// Plain (read-write path) vector load of V floats.
+template <int V>
+__device__ __forceinline__ void ld_row_rw(const float *p, float (&o)[V])
+{
+    if constexpr (V == 1) {
+        o[0] = p[0];
+    } else if constexpr (V == 2) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        o[0] = t.x; o[1] = t.y;
+    } else if constexpr (V == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else {
+        const float4 a = reinterpret_cast<const float4 *>(p)[0];
+        const float4 b = reinterpret_cast<const float4 *>(p)[1];
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+        o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+    }
+}
+
+// Asynchronous global -> shared copies (cp.async, no register staging).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+
+// Copy one row of V floats of the iterate into its swizzled shared-memory slot.
+template <int V>
+__device__ __forceinline__ void cp_async_row(float *base, int elem, const float *src);
+
 // Epilogue of Algorithm 1 for one finished row and V consecutive columns.
 template <int KP, int V>
 __device__ __forceinline__ void epilogue(const Params &p, int64_t row, int col0, const float (&s)[V],
-                                         const int (&alive)[V], double (&l1)[V])
+                                         const int (&alive)[V], float (&l1)[V])
 {
     float yv[V];
 #pragma unroll
@@ -163,21 +206,45 @@ __device__ __forceinline__ void epilogue(const Params &p, int64_t row, int col0,
     if (p.mode == MODE_ACC) {
         st_row<V>(p.y + row * KP + col0, yv);
         if (p.accumulate) {
+            if (p.ldr == KP && V > 1) {
+                // whole padded row contiguous: vector read-modify-write
+                float rv[V], xo[V];
+                ld_row_rw<V>(p.r + row * KP + col0, rv);
+                if (p.own_add) ld_row_rw<V>(p.x + row * KP + col0, xo);
 #pragma unroll
-            for (int j = 0; j < V; ++j)
-                if (col0 + j < p.k && alive[j]) p.r[row * p.ldr + col0 + j] += yv[j];
+                for (int j = 0; j < V; ++j) {
+                    if (col0 + j < p.k) {
+                        if (p.own_add && p.own[col0 + j]) rv[j] += xo[j];
+                        if (alive[j]) rv[j] += yv[j];
+                    }
+                }
+                st_row<V>(p.r + row * KP + col0, rv);
+            } else {
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    const bool own = p.own_add && p.own[col0 + j];
+                    if (col0 + j < p.k && (alive[j] || own)) {
+                        float rv = p.r[row * p.ldr + col0 + j];
+                        if (own) rv += p.x[row * KP + col0 + j];
+                        if (alive[j]) rv += yv[j];
+                        p.r[row * p.ldr + col0 + j] = rv;
+                    }
+                }
+            }
         }
     } else {
         const float rs = p.r_str[row];
 #pragma unroll
         for (int j = 0; j < V; ++j)
             if (col0 + j < p.k) {
-                const float fam = p.r[row * p.ldr + col0 + j] + (alive[j] ? yv[j] : 0.0f);
+                float fam = p.r[row * p.ldr + col0 + j];
+                if (p.own_add && p.own[col0 + j]) fam += p.x[row * KP + col0 + j];
+                if (alive[j]) fam += yv[j];
                 p.out[row * p.ldo + col0 + j] = fmaf(p.one_plus_alpha, fam, rs);
             }
     }
 #pragma unroll
-    for (int j = 0; j < V; ++j) l1[j] += alive[j] ? (double)fabsf(yv[j]) : 0.0;
+    for (int j = 0; j < V; ++j) l1[j] += alive[j] ? fabsf(yv[j]) : 0.0f;
 }
 
 // --------------------------------------------------------- main kernel ---
@@ -191,7 +258,7 @@ struct SpmmSmem {
     float val[L];
     int32_t crow[NVT];
     float carry[NVT][KP];
-    double l1[CTA / 32][KP];
+    float l1[CTA / 32][KP];
 };
 
 template <int G, int V, int ITEMS, int PF>
@@ -239,12 +306,12 @@ __global__ void __launch_bounds__(CTA) spmm_tile_k(Params p)
         const int avail = nrows + nnz - d;
 
         float acc[V];
-        double l1[V];
+        float l1[V];
         float first_val[V];
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             acc[j] = 0.0f;
-            l1[j] = 0.0;
+            l1[j] = 0.0f;
             first_val[j] = 0.0f;
         }
         int first_row = -1;
@@ -333,7 +400,7 @@ __global__ void __launch_bounds__(CTA) spmm_tile_k(Params p)
         // per-column L1 of this tile, fixed reduction order
 #pragma unroll
         for (int j = 0; j < V; ++j) {
-            double v = l1[j];
+            float v = l1[j];
 #pragma unroll
             for (int o = G; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             l1[j] = v;
@@ -344,7 +411,7 @@ __global__ void __launch_bounds__(CTA) spmm_tile_k(Params p)
         }
         __syncthreads();
         for (int c = threadIdx.x; c < KP; c += CTA) {
-            double sum = 0.0;
+            float sum = 0.0f;
 #pragma unroll
             for (int w = 0; w < CTA / 32; ++w) sum += S.l1[w][c];
             p.tl1[t * KP + c] = sum;
@@ -367,24 +434,88 @@ __global__ void __launch_bounds__(CTA) spmm_tile_k(Params p)
 //   4. the epilogue runs lane-per-row over the tile's rows (coalesced y, r,
 //      out); the tile's first row is deferred to the fixup when it started
 //      in an earlier tile.
+// Shared-memory rows of V floats, stored as chunks of CB bytes (16 for V >= 4,
+// else 4V) whose position inside each 128-byte bank row is XOR-swizzled by the
+// row number.  Lanes of a merge-path walk read elements about ITEMS apart,
+// which without the swizzle lands every lane in the same banks.
+template <int V>
+struct Swz {
+    static constexpr int CB = V >= 4 ? 16 : 4 * V;   // chunk bytes
+    static constexpr int CPE = (4 * V) / CB;          // chunks per element (1 or 2)
+    static constexpr int R = 128 / CB;                // chunks per 128-byte bank row
+    static constexpr int CF = CB / 4;                 // floats per chunk
+    __device__ __forceinline__ static int slot(int elem, int h)
+    {
+        const int c = elem * CPE + h;
+        return (c & ~(R - 1)) | ((c ^ (c / R)) & (R - 1));
+    }
+};
+
+template <int V>
+__device__ __forceinline__ void lds_row(const float *base, int elem, float (&o)[V])
+{
+    using Z = Swz<V>;
+#pragma unroll
+    for (int h = 0; h < Z::CPE; ++h) {
+        const float *p = base + Z::slot(elem, h) * Z::CF;
+        if constexpr (Z::CF == 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(p);
+            o[4 * h] = t.x; o[4 * h + 1] = t.y; o[4 * h + 2] = t.z; o[4 * h + 3] = t.w;
+        } else if constexpr (Z::CF == 2) {
+            const float2 t = *reinterpret_cast<const float2 *>(p);
+            o[0] = t.x; o[1] = t.y;
+        } else {
+            o[0] = p[0];
+        }
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void sts_row(float *base, int elem, const float (&v)[V])
+{
+    using Z = Swz<V>;
+#pragma unroll
+    for (int h = 0; h < Z::CPE; ++h) {
+        float *p = base + Z::slot(elem, h) * Z::CF;
+        if constexpr (Z::CF == 4) {
+            *reinterpret_cast<float4 *>(p) = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+        } else if constexpr (Z::CF == 2) {
+            *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+        } else {
+            p[0] = v[0];
+        }
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void cp_async_row(float *base, int elem, const float *src)
+{
+    using Z = Swz<V>;
+#pragma unroll
+    for (int h = 0; h < Z::CPE; ++h) cp_async<Z::CB>(base + Z::slot(elem, h) * Z::CF, src + h * Z::CF);
+}
+
 // Vector arrays first: every row of prod/rowsum starts on a V*4-byte boundary
 // (float2/float4 shared-memory accesses), and the slice size is a multiple of
 // 16 bytes so every warp's slice starts aligned too.
 template <int V, int ITEMS>
 struct __align__(16) WarpTile {
     static constexpr int L = 32 * ITEMS;
-    float prod[L][V];
-    float rowsum[L][V];
+    float prod[L * V];     // gathered rows X[col], swizzled (see Swz)
+    float rowsum[L * V];   // finished row sums, swizzled
+    float val[L];          // A~ values of the tile, swizzled as V = 1 rows
     int32_t end[L + 4];
 };
 
 template <int V, int ITEMS, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, (V <= 2 ? 1536 : 1024) / (WARPS * 32)) spmvw_tile_k(Params p)
+__global__ void __launch_bounds__(WARPS * 32, (V == 1 ? 1536 : V == 2 ? 1280 : V == 4 ? 1024 : 768) / (WARPS * 32))
+spmvw_tile_k(Params p)
 {
     using WT = WarpTile<V, ITEMS>;
     static_assert(offsetof(WT, prod) % 16 == 0 && offsetof(WT, rowsum) % 16 == 0, "vector rows must be aligned");
     static_assert((V * sizeof(float)) % (V == 1 ? 4 : V == 2 ? 8 : 16) == 0, "row width");
     static_assert(sizeof(WT) % 16 == 0, "warp slices must stay 16-byte aligned");
+    static_assert(sizeof(WT) * WARPS <= 48 * 1024, "static shared memory is limited to 48 KB per block");
     __shared__ WT S_all[WARPS];
     const CtlView cv = ctl_view(p.ctl);
     if (*(volatile int32_t *)&cv.hdr->done) return;
@@ -413,24 +544,14 @@ __global__ void __launch_bounds__(WARPS * 32, (V <= 2 ? 1536 : 1024) / (WARPS * 
                 c[j] = i < nnz ? __ldcs(p.col + y0 + i) : 0;
                 v[j] = i < nnz ? __ldcs(p.val + y0 + i) : 0.0f;
             }
-            float xv[ITEMS][V];
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                if (lane + j * 32 < nnz) {
-                    ld_row<V>(p.x + (int64_t)c[j] * V, xv[j]);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < V; ++q) xv[j][q] = 0.0f;
-                }
-            }
+            // gathers go straight to shared memory, all in flight at once
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j)
-                if (lane + j * 32 < nnz) {
-                    float pr[V];
+                if (lane + j * 32 < nnz) cp_async_row<V>(S.prod, lane + j * 32, p.x + (int64_t)c[j] * V);
 #pragma unroll
-                    for (int q = 0; q < V; ++q) pr[q] = v[j] * xv[j][q];
-                    st_row<V>(&S.prod[lane + j * 32][0], pr);
-                }
+            for (int j = 0; j < ITEMS; ++j)
+                if (lane + j * 32 < nnz) S.val[Swz<1>::slot(lane + j * 32, 0)] = v[j];
+            cp_async_wait_all();
         }
         __syncwarp();
 
@@ -452,13 +573,14 @@ __global__ void __launch_bounds__(WARPS * 32, (V <= 2 ? 1536 : 1024) / (WARPS * 
         for (int it = 0; it < ITEMS; ++it) {
             if (it < avail) {
                 if (ys < row_end) {
-                    float pr[V];
-                    ld_row_smem<V>(&S.prod[ys][0], pr);
+                    float xr[V];
+                    lds_row<V>(S.prod, ys, xr);
+                    const float vv = S.val[Swz<1>::slot(ys, 0)];
 #pragma unroll
-                    for (int q = 0; q < V; ++q) acc[q] += pr[q];
+                    for (int q = 0; q < V; ++q) acc[q] = fmaf(vv, xr[q], acc[q]);
                     ++ys;
                 } else {
-                    st_row<V>(&S.rowsum[xs][0], acc);
+                    sts_row<V>(S.rowsum, xs, acc);
                     if (first < 0) first = xs;
 #pragma unroll
                     for (int q = 0; q < V; ++q) acc[q] = 0.0f;
@@ -485,19 +607,22 @@ __global__ void __launch_bounds__(WARPS * 32, (V <= 2 ? 1536 : 1024) / (WARPS * 
         for (int q = 0; q < V; ++q) prev[q] = __shfl_up_sync(0xffffffffu, acc[q], 1);
         __syncwarp();   // rowsum writes of the walk are visible
         if (first >= 0 && lane > 0) {
+            float cur[V];
+            lds_row<V>(S.rowsum, first, cur);
 #pragma unroll
-            for (int q = 0; q < V; ++q) S.rowsum[first][q] += prev[q];
+            for (int q = 0; q < V; ++q) cur[q] += prev[q];
+            sts_row<V>(S.rowsum, first, cur);
         }
         if (lane == 31) st_row<V>(p.carry + t * V, acc);
         __syncwarp();
 
         // 4. coalesced epilogue, lane per row
-        double l1[V];
+        float l1[V];
 #pragma unroll
-        for (int q = 0; q < V; ++q) l1[q] = 0.0;
+        for (int q = 0; q < V; ++q) l1[q] = 0.0f;
         for (int i = lane; i < nrows; i += 32) {
             float sum[V];
-            ld_row_smem<V>(&S.rowsum[i][0], sum);
+            lds_row<V>(S.rowsum, i, sum);
             if (i == 0 && defer_first) {
                 st_row<V>(p.head + t * V, sum);
                 continue;
@@ -506,7 +631,7 @@ __global__ void __launch_bounds__(WARPS * 32, (V <= 2 ? 1536 : 1024) / (WARPS * 
         }
 #pragma unroll
         for (int q = 0; q < V; ++q) {
-            double a = l1[q];
+            float a = l1[q];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
             l1[q] = a;
@@ -533,7 +658,7 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) fixup_k(Params p)
     constexpr int SUB = 32 / CW;             // lanes sharing one column
     constexpr int NCH = KP / CW;             // column chunks per lane
     constexpr int NG = (FIX_WARPS * 32) / KP > 0 ? (FIX_WARPS * 32) / KP : 1;   // groups in the final reduction
-    __shared__ double s_l1[FIX_WARPS][KP];
+    __shared__ float s_l1[FIX_WARPS][KP];
     __shared__ double s_red[NG * KP];
     __shared__ int s_last;
     const CtlView cv = ctl_view(p.ctl);
@@ -541,9 +666,9 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) fixup_k(Params p)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cl = lane % CW, sub = lane / CW;
-    double l1acc[NCH];
+    float l1acc[NCH];
 #pragma unroll
-    for (int i = 0; i < NCH; ++i) l1acc[i] = 0.0;
+    for (int i = 0; i < NCH; ++i) l1acc[i] = 0.0f;
 
     for (int64_t t = (int64_t)blockIdx.x * FIX_WARPS + warp; t < p.tiles; t += (int64_t)gridDim.x * FIX_WARPS) {
         const int32_t h = p.head_row[t];
@@ -551,7 +676,7 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) fixup_k(Params p)
 #pragma unroll
         for (int i = 0; i < NCH; ++i) {
             const int c = i * CW + cl;
-            double l1 = sub == 0 ? p.tl1[t * KP + c] : 0.0;
+            float l1 = sub == 0 ? p.tl1[t * KP + c] : 0.0f;
             if (h >= 0) {
                 float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
                 int64_t u = first + sub;
@@ -568,7 +693,7 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) fixup_k(Params p)
                 if (sub == 0) {
                     float tot[1] = {p.head[t * KP + c] + s};
                     int al[1] = {cv.alive[c]};
-                    double e[1] = {0.0};
+                    float e[1] = {0.0f};
                     epilogue<KP, 1>(p, (int64_t)h, c, tot, al, e);
                     l1 += e[0];
                 }
@@ -582,10 +707,10 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) fixup_k(Params p)
     }
     __syncthreads();
     for (int c = threadIdx.x; c < KP; c += FIX_WARPS * 32) {
-        double sum = 0.0;
+        float sum = 0.0f;
 #pragma unroll
         for (int w = 0; w < FIX_WARPS; ++w) sum += s_l1[w][c];
-        p.part[(int64_t)blockIdx.x * KP + c] = sum;
+        p.part[(int64_t)blockIdx.x * KP + c] = (double)sum;
     }
     __threadfence();
     __syncthreads();
@@ -620,6 +745,121 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) fixup_k(Params p)
     }
 }
 
+// Fixup for narrow widths (KP <= 8): one thread per tile, so the dependent
+// loads of many tiles are in flight at once.  A deferred row whose carries
+// span at most FIX_SHORT earlier tiles is summed by its thread in tile order;
+// longer spans (rows of hubs) are summed by the whole warp in a fixed
+// lane-strided order.  The last block reduces the block partials of the L1
+// norm in a fixed order and applies the break test.
+constexpr int FIX_SHORT = 32;
+
+template <int V>
+__global__ void __launch_bounds__(256) fixup_small_k(Params p)
+{
+    constexpr int NG = 256 / V;
+    __shared__ float s_red[8][V];
+    __shared__ double s_fin[NG * V];
+    __shared__ int s_last;
+    const CtlView cv = ctl_view(p.ctl);
+    if (*(volatile int32_t *)&cv.hdr->done) return;
+    int alive[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) alive[q] = cv.alive[q];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const bool mine = t < p.tiles;
+    const int32_t h = mine ? p.head_row[t] : -1;
+    const int64_t first = mine ? (int64_t)p.head_first[t] : 0;
+    float l1[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) l1[q] = mine ? p.tl1[t * V + q] : 0.0f;
+    const bool longspan = h >= 0 && t - first > FIX_SHORT;
+    if (h >= 0 && !longspan) {
+        float sum[V];
+        ld_row<V>(p.head + t * V, sum);
+        for (int64_t u = first; u < t; ++u) {
+            float c[V];
+            ld_row<V>(p.carry + u * V, c);
+#pragma unroll
+            for (int q = 0; q < V; ++q) sum[q] += c[q];
+        }
+        epilogue<V, V>(p, (int64_t)h, 0, sum, alive, l1);
+    }
+    unsigned lm = __ballot_sync(0xffffffffu, longspan);
+    while (lm) {
+        const int src = __ffs(lm) - 1;
+        lm &= lm - 1;
+        const int64_t tt = __shfl_sync(0xffffffffu, t, src);
+        const int64_t ff = __shfl_sync(0xffffffffu, first, src);
+        float part[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) part[q] = 0.0f;
+        for (int64_t u = ff + lane; u < tt; u += 32) {
+            float c[V];
+            ld_row<V>(p.carry + u * V, c);
+#pragma unroll
+            for (int q = 0; q < V; ++q) part[q] += c[q];
+        }
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part[q] += __shfl_xor_sync(0xffffffffu, part[q], o);
+        }
+        if (lane == src) {
+            float sum[V];
+            ld_row<V>(p.head + t * V, sum);
+#pragma unroll
+            for (int q = 0; q < V; ++q) sum[q] += part[q];
+            epilogue<V, V>(p, (int64_t)h, 0, sum, alive, l1);
+        }
+    }
+    // block partial of the L1 norm, fixed order
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+        float a = l1[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) s_red[warp][q] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < V) {
+        float a = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) a += s_red[w][threadIdx.x];
+        p.part[(int64_t)blockIdx.x * V + threadIdx.x] = (double)a;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&cv.hdr->ticket, 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    {
+        const int c = threadIdx.x % V, grp = threadIdx.x / V;
+        double a = 0.0;
+        for (unsigned b = grp; b < gridDim.x; b += NG) a += __ldcg(&p.part[(int64_t)b * V + c]);
+        s_fin[grp * V + c] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < V) {
+        const int c = threadIdx.x;
+        double a = 0.0;
+        for (int grp = 0; grp < NG; ++grp) a += s_fin[grp * V + c];
+        if (c < p.k && cv.alive[c]) {
+            cv.norm[c] = a;
+            cv.iters[c] = p.iter;
+            if (a < p.eps && p.mode == MODE_ACC) cv.alive[c] = 0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int c = 0; c < p.k && c < V; ++c) any |= cv.alive[c];
+        cv.hdr->done = any ? 0 : 1;
+        cv.hdr->ticket = 0;
+    }
+}
+
 // ---------------------------------------------------------- init / misc ---
 // x0 = c q per column (one-hot at seeds[j], or c/n everywhere when seeds is null);
 // r = x0 when s_iter == 0, else 0.
@@ -643,7 +883,9 @@ __global__ void ctl_init_k(void *ctl, int k)
     for (int j = threadIdx.x; j < KP_MAX; j += blockDim.x) {
         cv.alive[j] = j < k ? 1 : 0;
         cv.iters[j] = 0;
+        cv.own[j] = 0;
         cv.norm[j] = 0.0;
+        cv.norm1[j] = 0.0;
     }
     if (threadIdx.x == 0) {
         cv.hdr->done = 0;
@@ -684,6 +926,127 @@ __global__ void copy_iters_k(const void *ctl, int32_t *out, int k)
 {
     const CtlView cv = ctl_view(const_cast<void *>(ctl));
     for (int j = threadIdx.x; j < k; j += blockDim.x) out[j] = cv.iters[j];
+}
+
+// ---------------------------------------------------------- push path ---
+// The first family iterates of a query are sparse: x1 lives on the
+// out-neighbours of the seed and x2 on their out-neighbours (about 0.2% of the
+// edges are touched), while a pull iteration streams the whole CSR.  So for
+// light seeds x1 and x2 are pushed along CSR(A~) and only iterations 3.. are
+// pulled:
+//   x1[u] = (1-c) (A~_su c)                 for u in out(s)
+//   x2[v] = (1-c) sum_u A~_uv x1[u]
+// x2 is accumulated in 64-bit fixed point (scale 2^63; every term is
+// non-negative and the total mass is below 1), so the integer atomics make the
+// sum independent of their order: the result is deterministic and rounded to
+// FP32 once.  r starts as x0 + x1; x2 is added to r by the first pulled
+// iteration (Params::own_add).
+constexpr float FX_SCALE_F = 9223372036854775808.0f;      // 2^63, exact in FP32
+constexpr float FX_INV_F = 1.0842021724855044e-19f;       // 2^-63, exact in FP32
+
+__global__ void push_x2_k(const int64_t *rp_a, const int32_t *col_a, const float *val_a, const int32_t *seeds,
+                          int KP, float c_f, float decay, unsigned long long *U, float *R, void *ctl)
+{
+    const CtlView cv = ctl_view(ctl);
+    const int j = blockIdx.y;
+    const int32_t s = seeds[j];
+    const int64_t e0 = rp_a[s], e1 = rp_a[s + 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        R[(int64_t)s * KP + j] = c_f;                                   // x0
+        float nrm = 0.0f;
+        for (int64_t e = e0; e < e1; ++e) {
+            const float x1u = decay * (val_a[e] * c_f);                 // x1, as the pull computes it
+            R[(int64_t)col_a[e] * KP + j] = x1u;
+            nrm += x1u;
+        }
+        cv.norm1[j] = (double)nrm;
+    }
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = e0; e < e1; ++e) {
+        const int32_t u = col_a[e];
+        const float x1u = decay * (val_a[e] * c_f);
+        const int64_t f0 = rp_a[u], f1 = rp_a[u + 1];
+        for (int64_t f = f0 + gt; f < f1; f += gs) {
+            const float q = val_a[f] * x1u;
+            atomicAdd(&U[(int64_t)col_a[f] * KP + j], __float2ull_rn(q * FX_SCALE_F));
+        }
+    }
+}
+
+// X = x2 in FP32 (padding columns zero), U cleared for the next chunk,
+// ||x2||_1 per column; the last block applies the break tests after x1 and x2.
+template <int KP>
+__global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, float *X, int64_t n, int kc, float decay,
+                                                    double eps, double *part, void *ctl)
+{
+    __shared__ float s_red[8][KP];
+    __shared__ double s_fin[256];
+    __shared__ int s_last;
+    const CtlView cv = ctl_view(ctl);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t v = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    float nrm[KP];
+#pragma unroll
+    for (int j = 0; j < KP; ++j) nrm[j] = 0.0f;
+    if (v < n) {
+#pragma unroll
+        for (int j = 0; j < KP; ++j) {
+            float x = 0.0f;
+            if (j < kc) {
+                const unsigned long long a = U[v * KP + j];
+                if (a) {
+                    U[v * KP + j] = 0ull;
+                    x = decay * (__ull2float_rn(a) * FX_INV_F);
+                }
+            }
+            X[v * KP + j] = x;
+            nrm[j] = x;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+        float a = nrm[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) s_red[warp][j] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < KP) {
+        float a = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) a += s_red[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * KP + threadIdx.x] = (double)a;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&cv.hdr->ticket, 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    constexpr int NG = 256 / KP;
+    {
+        const int c = threadIdx.x % KP, grp = threadIdx.x / KP;
+        double a = 0.0;
+        for (unsigned b = grp; b < gridDim.x; b += NG) a += __ldcg(&part[(int64_t)b * KP + c]);
+        s_fin[grp * KP + c] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < KP) {
+        const int c = threadIdx.x;
+        double a = 0.0;
+        for (int grp = 0; grp < NG; ++grp) a += s_fin[grp * KP + c];
+        if (c < kc) {
+            const bool a1 = cv.norm1[c] >= eps;          // Algorithm 1 breaks after x1 when ||x1|| < eps
+            const bool a2 = a1 && a >= eps;              // ... or after x2
+            cv.own[c] = a1 ? 1 : 0;
+            cv.alive[c] = a2 ? 1 : 0;
+            cv.iters[c] = a1 ? 2 : 1;
+            cv.norm[c] = a1 ? a : cv.norm1[c];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) cv.hdr->ticket = 0;   // done stays 0: iteration 3 adds x2 to r
 }
 
 // ------------------------------------------------------------- planning ---
@@ -801,7 +1164,19 @@ static void launch_spmvw(const Params &p, cudaStream_t s)
 template <int KP>
 static void launch_fix(const Params &p, unsigned blocks, cudaStream_t s)
 {
-    fixup_k<KP><<<blocks, FIX_WARPS * 32, 0, s>>>(p);
+    if constexpr (KP <= 8) {
+        (void)blocks;
+        fixup_small_k<KP><<<(unsigned)((p.tiles + 255) / 256), 256, 0, s>>>(p);
+    } else {
+        fixup_k<KP><<<blocks, FIX_WARPS * 32, 0, s>>>(p);
+    }
+}
+
+// Blocks of the fixup grid (the L1 partial buffer holds one row per block).
+static unsigned fix_grid(int KP, int64_t tiles)
+{
+    if (KP <= 8) return (unsigned)((tiles + 255) / 256);
+    return (unsigned)std::min<int64_t>((tiles + FIX_WARPS - 1) / FIX_WARPS, (int64_t)4 * num_sms());
 }
 
 struct Variant {
@@ -815,11 +1190,14 @@ struct Variant {
 static const Variant kVariants[] = {
     TPA_VARIANTW(1, 8, 8),
     TPA_VARIANTW(1, 6, 8),
-    TPA_VARIANTW(1, 12, 8),
-    TPA_VARIANTW(2, 8, 8),
+    TPA_VARIANTW(1, 7, 8),
+    TPA_VARIANTW(2, 8, 4),
+    TPA_VARIANTW(2, 6, 8),
+    TPA_VARIANTW(4, 6, 4),
     TPA_VARIANTW(4, 8, 4),
     TPA_VARIANTW(4, 4, 8),
     TPA_VARIANTW(8, 4, 4),
+    TPA_VARIANTW(8, 6, 2),
     TPA_VARIANTW(8, 2, 8),
     TPA_VARIANT(1, 1, 8, 8),
     TPA_VARIANT(1, 2, 8, 8),
@@ -852,6 +1230,21 @@ static int g_forced[KP_MAX + 1];
 static bool g_forced_init = false;
 // Seeds per CPI chunk in batched calls (a power of two <= KP_MAX).
 static int g_chunk = KP_MAX;
+// Push path for the first two family iterations of a query (on by default).
+static bool g_push = true;
+constexpr int PUSH_MAX_OUTDEG = 256;   // seeds with more out-edges keep the pull path
+constexpr int PUSH_BLOCKS = 16;        // blocks per column in push_x2_k
+
+static void launch_convert(int KP, unsigned blocks, unsigned long long *U, float *X, int64_t n, int kc, float decay,
+                           double eps, double *part, void *ctl, cudaStream_t s)
+{
+    switch (KP) {
+    case 1: convert_x2_k<1><<<blocks, 256, 0, s>>>(U, X, n, kc, decay, eps, part, ctl); break;
+    case 2: convert_x2_k<2><<<blocks, 256, 0, s>>>(U, X, n, kc, decay, eps, part, ctl); break;
+    case 4: convert_x2_k<4><<<blocks, 256, 0, s>>>(U, X, n, kc, decay, eps, part, ctl); break;
+    default: convert_x2_k<8><<<blocks, 256, 0, s>>>(U, X, n, kc, decay, eps, part, ctl); break;
+    }
+}
 
 // The forced variant for a padded width, else the first listed with that width.
 static const Variant &pick_variant(int KP)
@@ -878,6 +1271,16 @@ static double spmm_bytes(int64_t n, int64_t m, int KP, int k, int mode, int accu
     return b;
 }
 
+// Statistics family of the SpMV/SpMM launches of one padded width.
+static const char *spmm_family(int KP)
+{
+    static const char *names[] = {"spmm_kp1", "spmm_kp2", "spmm_kp4", "spmm_kp8", "spmm_kp16",
+                                  "spmm_kp32", "spmm_kp64", "spmm_kp128", "spmm_kp256"};
+    int i = 0;
+    while ((1 << i) < KP && i < 8) ++i;
+    return names[i];
+}
+
 static int iteration_bound(double c, double eps)
 {
     // first i with c (1-c)^i < eps, plus a margin for FP32 rounding of the norm
@@ -897,9 +1300,8 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     W.y.ensure((size_t)n * KP * sizeof(float), s);
     W.carry.ensure((size_t)P.tiles * KP * sizeof(float), s);
     W.head.ensure((size_t)P.tiles * KP * sizeof(float), s);
-    W.tl1.ensure((size_t)P.tiles * KP * sizeof(double), s);
-    const unsigned fix_blocks =
-        (unsigned)std::min<int64_t>((P.tiles + FIX_WARPS - 1) / FIX_WARPS, (int64_t)4 * num_sms());
+    W.tl1.ensure((size_t)P.tiles * KP * sizeof(float), s);
+    const unsigned fix_blocks = fix_grid(KP, P.tiles);
     W.fix.ensure((size_t)fix_blocks * KP * sizeof(double), s);
     W.ctl.ensure(CTL_BYTES, s);
 
@@ -917,11 +1319,33 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
         r = a.r + k0;
         ldr = a.ldr;
     }
-    init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, a.seeds ? a.seeds + k0 : nullptr, kc, c_val,
-                                                 pr_val, r, ldr, a.s_iter == 0 ? 1 : 0);
-    TPA_CHECK_LAUNCH();
-
     const int last = a.t_iter >= 0 ? a.t_iter : iteration_bound(a.c, a.eps);
+    // Push path for the first two family iterations (light seeds, narrow chunks).
+    bool push = g_push && a.tpa_final && a.seeds && a.seed_outdeg && last >= 3 && KP <= 8 && a.r_internal;
+    for (int j = 0; push && j < kc; ++j) push = a.seed_outdeg[k0 + j] <= PUSH_MAX_OUTDEG;
+    if (push) {
+        const unsigned cblocks = (unsigned)((n + 255) / 256);
+        W.fix.ensure((size_t)std::max<unsigned>(fix_blocks, cblocks) * KP * sizeof(double), s);
+        if (!W.u.p || W.u.bytes < (size_t)n * KP * sizeof(unsigned long long) || !W.u_clean) {
+            W.u.ensure((size_t)n * KP * sizeof(unsigned long long), s);
+            TPA_CUDA(cudaMemsetAsync(W.u.p, 0, W.u.bytes, s));
+        }
+        W.u_clean = false;
+        TPA_CUDA(cudaMemsetAsync(r, 0, (size_t)n * KP * sizeof(float), s));
+        const float decay_f = (float)(1.0 - a.c);
+        push_x2_k<<<dim3(PUSH_BLOCKS, kc), 256, 0, s>>>(g->rp_a.as<int64_t>(), g->col_a.as<int32_t>(),
+                                                        g->val_a.as<float>(), a.seeds + k0, KP, c_val, decay_f,
+                                                        W.u.as<unsigned long long>(), r, W.ctl.p);
+        launch_convert(KP, cblocks, W.u.as<unsigned long long>(), W.x.as<float>(), n, kc, decay_f, a.eps,
+                       W.fix.as<double>(), W.ctl.p, s);
+        note_launch("push", 2);
+        TPA_CHECK_LAUNCH();
+        W.u_clean = true;
+    } else {
+        init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, a.seeds ? a.seeds + k0 : nullptr, kc,
+                                                     c_val, pr_val, r, ldr, a.s_iter == 0 ? 1 : 0);
+        TPA_CHECK_LAUNCH();
+    }
     if (last == 0) {
         if (a.tpa_final) {
             finalize_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(r, ldr, a.r_str, (float)(1.0 + a.alpha), a.out + k0,
@@ -957,9 +1381,10 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     p.eps = a.eps;
     p.carry = W.carry.as<float>();
     p.head = W.head.as<float>();
-    p.tl1 = W.tl1.as<double>();
+    p.tl1 = W.tl1.as<float>();
     p.part = W.fix.as<double>();
     p.ctl = W.ctl.p;
+    p.own = ctl_view(W.ctl.p).own;
 
     float *cur = W.x.as<float>(), *nxt = W.y.as<float>();
     // Host-side early stop: every CHUNK iterations, read the device done flag
@@ -978,19 +1403,20 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
             TPA_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
         }
         int chunk = 0;
-        for (int i = 1; i <= last; ++i) {
+        for (int i = push ? 3 : 1; i <= last; ++i) {
             p.x = cur;
             p.y = nxt;
             p.iter = i;
+            p.own_add = (push && i == 3) ? 1 : 0;
             p.accumulate = i >= a.s_iter ? 1 : 0;
             p.mode = (a.tpa_final && i == last) ? MODE_FINAL : MODE_ACC;
             ProfMark pm = prof_begin(s);
             var.spmm(p, s);
-            prof_end(pm, "spmm", spmm_bytes(n, g->m, KP, kc, p.mode, p.accumulate), s);
+            prof_end(pm, spmm_family(KP), spmm_bytes(n, g->m, KP, kc, p.mode, p.accumulate), s);
             ProfMark pf = prof_begin(s);
             var.fix(p, fix_blocks, s);
             prof_end(pf, "fixup", 0.0, s);
-            note_launch("spmm");
+            note_launch(spmm_family(KP));
             note_launch("fixup");
             if (p.mode == MODE_FINAL) {
                 finalize_if_done_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(W.ctl.p, r, ldr, a.r_str, p.one_plus_alpha,
@@ -1054,7 +1480,7 @@ StepLayout step_layout(int64_t tiles)
     L.head_first = off; off += align256((size_t)tiles * sizeof(int32_t));
     L.carry = off;      off += align256((size_t)tiles * sizeof(float));
     L.head = off;       off += align256((size_t)tiles * sizeof(float));
-    L.tl1 = off;        off += align256((size_t)tiles * sizeof(double));
+    L.tl1 = off;        off += align256((size_t)tiles * sizeof(float));
     L.part = off;       off += align256((size_t)STEP_FIX_BLOCKS * sizeof(double));
     L.ctl = off;        off += align256(CTL_BYTES);
     L.total = off;
@@ -1110,7 +1536,7 @@ cudaError_t run_step1(const int64_t *rp, const int32_t *col, const float *val, i
     p.eps = 0.0;
     p.carry = reinterpret_cast<float *>(scratch + L.carry);
     p.head = reinterpret_cast<float *>(scratch + L.head);
-    p.tl1 = reinterpret_cast<double *>(scratch + L.tl1);
+    p.tl1 = reinterpret_cast<float *>(scratch + L.tl1);
     p.part = reinterpret_cast<double *>(scratch + L.part);
     p.ctl = scratch + L.ctl;
 
@@ -1130,6 +1556,26 @@ cudaError_t run_step1(const int64_t *rp, const int32_t *col, const float *val, i
     }
     note_launch_count(launches);
     return cudaGetLastError();
+}
+
+__global__ void gather_outdeg_k(const int32_t *outdeg, const int32_t *seeds, int k, int32_t *out)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) out[j] = outdeg[seeds[j]];
+}
+
+std::vector<int32_t> seed_outdegrees(tpa_graph *g, const int32_t *d_seeds, int k, cudaStream_t s)
+{
+    std::vector<int32_t> h((size_t)k);
+    DevBuf tmp;
+    tmp.ensure((size_t)k * sizeof(int32_t), s);
+    gather_outdeg_k<<<(unsigned)std::min(1024, (k + 255) / 256), 256, 0, s>>>(g->outdeg.as<int32_t>(), d_seeds, k,
+                                                                            tmp.as<int32_t>());
+    note_launch("init");
+    TPA_CHECK_LAUNCH();
+    TPA_CUDA(cudaMemcpyAsync(h.data(), tmp.p, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TPA_CUDA(cudaStreamSynchronize(s));
+    tmp.release(s);
+    return h;
 }
 
 void run_cpi(tpa_graph *g, const CpiArgs &a, cudaStream_t s)
@@ -1192,6 +1638,12 @@ tpa_status tpa_set_batch_width(int width)
 }
 
 int tpa_get_batch_width(void) { return g_chunk; }
+
+tpa_status tpa_set_push(int enable)
+{
+    g_push = enable != 0;
+    return TPA_OK;
+}
 
 }  // extern "C"
 

@@ -6,6 +6,7 @@
 
 #include <map>
 #include <string>
+#include <vector>
 
 #include "../../include/tpa.h"
 
@@ -83,6 +84,8 @@ struct Workspace {
     DevBuf seeds;           // int32 seeds
     DevBuf out;             // device staging for host outputs
     DevBuf iters;           // int32 per-column iteration counts
+    DevBuf u;               // push path: 64-bit fixed-point accumulator [n][KP]
+    bool u_clean = false;   // u is known to be all zero
     int32_t *hflag = nullptr;   // pinned host mirror of the done flag (2 slots)
 };
 
@@ -148,7 +151,11 @@ struct CpiArgs {
     float *out = nullptr;
     int64_t ldo = 1;
     int32_t *iters_out = nullptr;   // device int32[k] or nullptr
+    const int32_t *seed_outdeg = nullptr;   // host int32[k]: out-degrees of the seeds (enables the push path)
 };
+
+// Out-degrees of k device-resident seeds, copied to the host.
+std::vector<int32_t> seed_outdegrees(tpa_graph *g, const int32_t *d_seeds, int k, cudaStream_t s);
 
 void run_cpi(tpa_graph *g, const CpiArgs &a, cudaStream_t s);
 

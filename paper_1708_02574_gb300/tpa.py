@@ -55,6 +55,7 @@ def library():
         "tpa_set_variant": (i32, [i32, i32]),
         "tpa_set_batch_width": (i32, [i32]),
         "tpa_get_batch_width": (i32, []),
+        "tpa_set_push": (i32, [i32]),
         "tpa_profile_reset": (i32, [i32]),
         "tpa_profile_read": (i32, [P, i32, ctypes.POINTER(i32)]),
     }
@@ -270,3 +271,8 @@ def cpi_step_noalloc(n: int, m: int, row_ptr, col, val, c: float, x, y, r=None, 
     All tensors must be CUDA tensors; the CSR is that of A~^T (rows = destinations)."""
     _check(library().tpa_cpi_step_noalloc(int(n), int(m), _ptr(row_ptr), _ptr(col), _ptr(val), float(c), _ptr(x),
                                           _ptr(y), _ptr(r), _ptr(l1), _stream()))
+
+
+def set_push(enable: bool) -> None:
+    """Push the sparse first family iterates of a query (default) or pull every iteration."""
+    _check(library().tpa_set_push(1 if enable else 0))

@@ -199,3 +199,41 @@ def test_save_load_preprocessed(rmat14, tmp_path):
     small = t.build_graph(5, np.array([0, 1], np.int32), np.array([1, 2], np.int32))
     with pytest.raises(t.TpaError, match="EINVAL"):
         t.load_preprocessed(small, p)
+
+
+@pytest.fixture
+def narrow_batches():
+    t = tpa()
+    t.set_batch_width(8)
+    yield
+    t.set_batch_width(256)
+    t.set_push(True)
+
+
+@pytest.mark.parametrize("k,S_", [(1, 5), (3, 4), (8, 5), (8, 10), (13, 6)])
+def test_query_push_path(rmat14, narrow_batches, k, S_):
+    """Light seeds in chunks of <= 8: x1 and x2 are pushed along CSR(A~); parity with the oracle."""
+    n = rmat14["n"]
+    og = rmat14["og"]
+    light = rmat14["cand"][(og.outdeg[rmat14["cand"]] <= 256)]
+    seeds = synth.query_seeds(light, k, key=20 + k)
+    if k >= 3:
+        dead = np.setdiff1d(np.arange(n), rmat14["cand"])
+        seeds[1] = dead[3]                         # no out-edges: the column stops after x1
+    out = tpa().query(rmat14["g"], seeds, S_).cpu().numpy()
+    for j in range(k):
+        ref = oracle.query(og, int(seeds[j]), C, S_, T, rmat14["rs"], EPS)
+        parity(out[:, j], ref, f"push k={k} S={S_} col {j} seed {seeds[j]}")
+    t = tpa()
+    t.set_push(False)
+    pulled = t.query(rmat14["g"], seeds, S_).cpu().numpy()
+    for j in range(k):
+        parity(out[:, j], pulled[:, j].astype(np.float64), f"push vs pull col {j}")
+
+
+def test_query_push_deterministic(rmat14, narrow_batches):
+    light = rmat14["cand"][(rmat14["og"].outdeg[rmat14["cand"]] <= 256)]
+    seeds = synth.query_seeds(light, 8, key=31)
+    a = tpa().query(rmat14["g"], seeds, S).cpu().numpy()
+    b = tpa().query(rmat14["g"], seeds, S).cpu().numpy()
+    assert np.array_equal(a, b)
