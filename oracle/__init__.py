@@ -67,14 +67,12 @@ def _load():
 
 def _bind_adjoint(lib):
     P, i64, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    lib.orc_adj_set_fault.argtypes = [ctypes.c_int]
+    lib.orc_adj_set_fault.restype = None
     lib.orc_weighted_csr.restype = ctypes.c_int
     lib.orc_weighted_csr.argtypes = [i64, P, P, P, P, i64, P, P, P]
-    lib.orc_tpa_loss.restype = f64
-    lib.orc_tpa_loss.argtypes = [i64, P, P, P, i64, P, P, P, P, f64, f64, i64, i64, i64,
-                                 P, P, P, P]
     lib.orc_adjoint_grad.restype = f64
-    lib.orc_adjoint_grad.argtypes = [i64, P, P, P, i64, P, P, P, P, f64, f64, i64, i64, i64,
-                                     P, P, P, P, P]
+    lib.orc_adjoint_grad.argtypes = [i64, i64, P, P, P, P, P, f64, i64, i64, i64, i64, P, P, P, P, P, P, P]
 
 
 def _p(a):
@@ -166,3 +164,49 @@ def cpi_exact(g: Graph, seed: int, c: float, eps: float = 1e-9):
     if it < 0:
         raise ValueError("orc_cpi_exact")
     return out, int(it)
+
+
+# ------------------------------------------------------------- adjoint ---
+def set_adjoint_fault(k: int) -> None:
+    """Plant mistake k in the adjoint oracle (0 = none).  For pin-strength tests only."""
+    _load().orc_adj_set_fault(int(k))
+
+
+def edge_weights(theta: np.ndarray, feat: np.ndarray) -> np.ndarray:
+    """w_e = exp(theta . f_e) in FP64 (feat rows in CSR(A~) edge order)."""
+    return np.exp(np.asarray(feat, dtype=np.float64) @ np.asarray(theta, dtype=np.float64))
+
+
+def weighted_vals(g: Graph, w: np.ndarray):
+    """(val_a, val_t, pos_t): A~ = w / rowsum in both CSR orders; pos_t maps CSR(A~) -> CSR(A~^T) positions."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    va = np.empty(max(g.m, 1))
+    vt = np.empty(max(g.m, 1))
+    pt = np.empty(max(g.m, 1), dtype=np.int64)
+    rc = _load().orc_weighted_csr(g.n, _p(g.rp_a), _p(g.col_a), _p(w), _p(g.rp_t), g.m, _p(va), _p(vt), _p(pt))
+    if rc != 0:
+        raise MemoryError("orc_weighted_csr")
+    return va[:g.m], vt[:g.m], pt[:g.m]
+
+
+def loss_grad(g: Graph, w: np.ndarray, seeds, pos, neg, c: float, S: int, T: int, K: int, want_grad: bool = True):
+    """Link-prediction loss on TPA scores and dL/dw (CSR(A~) order), FP64.
+
+    Returns (loss, grad_w or None, r_pairs [ntrip, 2] = (r[pos], r[neg]), r_stranger)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    s = np.ascontiguousarray(seeds, dtype=np.int32)
+    p = np.ascontiguousarray(pos, dtype=np.int32)
+    q = np.ascontiguousarray(neg, dtype=np.int32)
+    gw = np.empty(max(g.m, 1)) if want_grad else None
+    rr = np.empty(2 * len(s))
+    rs = np.empty(g.n)
+    loss = _load().orc_adjoint_grad(g.n, g.m, _p(g.rp_a), _p(g.col_a), _p(g.rp_t), _p(g.col_t), _p(w), c, S, T, K,
+                                    len(s), _p(s), _p(p), _p(q), _p(gw), _p(rr), _p(rs), None)
+    if not np.isfinite(loss):
+        raise ValueError("orc_adjoint_grad rejected its arguments")
+    return loss, (gw[:g.m] if want_grad else None), rr.reshape(-1, 2), rs
+
+
+def theta_grad(feat: np.ndarray, w: np.ndarray, grad_w: np.ndarray) -> np.ndarray:
+    """dL/dtheta = sum_e dL/dw_e * w_e * f_e (w = exp(theta . f))."""
+    return (np.asarray(grad_w, dtype=np.float64) * np.asarray(w, dtype=np.float64)) @ np.asarray(feat, dtype=np.float64)
