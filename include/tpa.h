@@ -145,6 +145,39 @@ tpa_status tpa_cpi_step_noalloc(int64_t n, int64_t m, const int64_t *row_ptr, co
                                 const float *val, double c, const float *x, float *y, float *r,
                                 double *l1, void *stream);
 
+/* ------------------------------------------------------ differentiation ---
+ * Not part of the paper's method: gradients of a link-prediction loss on TPA
+ * scores with respect to positive edge weights (supervised random walks).
+ * With weights w, A~_uv = w_uv / sum_v' w_uv'. */
+
+/* Use weights w (float32[m], device or host, in CSR(A~) edge order as
+ * returned by tpa_get_csr(g, 1, ...)).  Recomputes A~ in both CSR orders;
+ * the previous preprocessing result is dropped (TPA_ESTATE until
+ * tpa_preprocess runs again). */
+tpa_status tpa_set_edge_weights(tpa_graph *g, const float *w, void *stream);
+
+/* w_e = exp(theta . f_e) for m edges with d <= 16 features (feat row-major
+ * [m][d]); all arrays device memory. */
+tpa_status tpa_edge_weights(const float *feat, const float *theta, int d, int64_t m, float *w, void *stream);
+
+/*
+ * L = sum over ntrip triples (s, p, q) of softplus(r[q] - r[p]), where
+ * r = (1+alpha) r_family(s) + r~_stranger follows Algorithms 2-3 on the
+ * current weights with the stranger chain run for exactly K >= T iterations
+ * (take K from tpa_get_stranger after tpa_preprocess on the same weights so
+ * the loss matches the served scores).  Writes L to *loss (host) and
+ * dL/dw (float32[m], CSR(A~) order, device or host) to grad_w, computed by the
+ * adjoint recursions l_i = (1+alpha) g + P^T l_{i+1} (family, S-1 steps) and
+ * m_i = [i >= T] G + P^T m_{i+1} (stranger, K steps) with P^T = (1-c) A~ and
+ * the row-normalisation Jacobian.  Unweighted graphs use unit weights.
+ */
+tpa_status tpa_loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const int32_t *neg, int ntrip,
+                         double c, int S, int T, int K, double *loss, float *grad_w, void *stream);
+
+/* dL/dtheta_j = sum_e grad_w_e w_e f_ej (FP64 out[d]); device arrays. */
+tpa_status tpa_theta_grad(const float *feat, const float *w, const float *grad_w, int d, int64_t m,
+                          double *grad_theta, void *stream);
+
 /* ---------------------------------------------------- kernel tuning ---
  * Not part of the paper's method.  Process-wide settings of the SpMV/SpMM
  * that runs each CPI iteration; an autotuner times the variants on a graph

@@ -17,6 +17,10 @@ from .tpa import (  # noqa: F401
     cpi,
     cpi_exact,
     cpi_step_noalloc,
+    edge_weights,
+    loss_grad,
+    set_edge_weights,
+    theta_grad,
     get_csr,
     get_stranger,
     graph_info,
@@ -34,3 +38,4 @@ from .tpa import (  # noqa: F401
     set_variant,
     variants,
 )
+from .autograd import TPALinkLoss  # noqa: F401,E402

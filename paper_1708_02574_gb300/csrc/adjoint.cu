@@ -1,0 +1,365 @@
+// Gradient of a link-prediction loss on TPA scores with respect to edge
+// weights (supervised random walks); not part of the paper's method.
+//
+// A~_uv = w_uv / d_u (d_u = sum_v w_uv), P = (1-c) A~^T.  For triples
+// (s, p, q): r = (1+alpha) r_family(s) + r~_stranger (Algorithms 2-3 with the
+// stranger chain run for a fixed K iterations), L = sum softplus(r[q] - r[p]).
+// With g = dL/dr (two nonzeros per triple):
+//   family   l_{S-1} = (1+alpha) g, l_i = (1+alpha) g + P^T l_{i+1}
+//   stranger m_K = G, m_i = [i >= T] G + P^T m_{i+1}, G = sum over triples of g
+//   dL/dA~_uv = (1-c) (sum_i l_i[v] x_{i-1}[u] + sum_i m_i[v] x'_{i-1}[u])
+//   dL/dw_uv  = (dL/dA~_uv - sum_v' dL/dA~_uv' A~_uv') / d_u
+// P x runs the merge-path SpMV over CSR(A~^T); P^T y the same kernel over
+// CSR(A~) (rows = sources), i.e. the non-transposed A~.  The edge gradient is
+// an SDDMM over CSR(A~) edges.  Every reduction has a fixed order; the
+// stranger seed G is accumulated in 64-bit fixed point.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "tpa_internal.cuh"
+
+namespace tpa {
+namespace {
+
+constexpr int KB = 8;                                  // triples per family batch
+constexpr double G_SCALE = 1099511627776.0;            // 2^40, fixed point of G
+
+unsigned grid_for(int64_t work, int threads = 256)
+{
+    const int64_t b = (work + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+}
+
+__global__ void weights_k(const float *feat, const float *theta, int d, int64_t m, float *w)
+{
+    extern __shared__ float s_theta[];
+    for (int j = threadIdx.x; j < d; j += blockDim.x) s_theta[j] = theta[j];
+    __syncthreads();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        float z = 0.0f;
+        for (int j = 0; j < d; ++j) z = fmaf(s_theta[j], feat[e * d + j], z);
+        w[e] = expf(z);
+    }
+}
+
+// Warp per source row: d_u in FP64 (lane-strided, fixed shuffle tree), then
+// A~ = w / d_u in both CSR orders.
+__global__ void normalise_k(const int64_t *rp_a, const float *w, const uint32_t *perm, int64_t n, float *val_a,
+                            float *val_t, double *inv_d)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const int64_t e0 = rp_a[u], e1 = rp_a[u + 1];
+        double sum = 0.0;
+        for (int64_t e = e0 + lane; e < e1; e += 32) sum += (double)w[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        const double inv = sum > 0.0 ? 1.0 / sum : 0.0;
+        if (lane == 0) inv_d[u] = inv;
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const float v = (float)((double)w[e] * inv);
+            val_a[e] = v;
+            val_t[perm[e]] = v;
+        }
+    }
+}
+
+__global__ void row_ids_k(const int64_t *rp_a, int64_t n, int32_t *row)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps)
+        for (int64_t e = rp_a[u] + lane; e < rp_a[u + 1]; e += 32) row[e] = (int32_t)u;
+}
+
+__global__ void fill_k(float *x, int64_t len, float v)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
+}
+
+// r~_stranger = sum_{i=T}^{K} x'_i, summed in iteration order
+__global__ void stranger_sum_k(const float *xs, int64_t n, int T, int K, float *rs)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int i = T; i <= K; ++i) s += xs[(int64_t)i * n + v];
+        rs[v] = s;
+    }
+}
+
+// F_0 = c e_s for the batch's columns (padding columns stay zero)
+__global__ void family_init_k(float *F0, const int32_t *seeds, int kb, float c)
+{
+    const int j = threadIdx.x;
+    if (j < kb) F0[(int64_t)seeds[j] * KB + j] = c;
+}
+
+// Scores at (p, q), loss and sigma per triple; G (stranger seed) in fixed point.
+__global__ void pair_k(const float *F, int64_t n, int S, const int32_t *pos, const int32_t *neg, int kb, float opa,
+                       const float *rs, double *loss, double *sg, unsigned long long *gacc)
+{
+    const int j = threadIdx.x;
+    if (j >= kb) return;
+    const int32_t p = pos[j], q = neg[j];
+    float fp = 0.0f, fq = 0.0f;
+    for (int i = 0; i < S; ++i) {
+        fp += F[((int64_t)i * n + p) * KB + j];
+        fq += F[((int64_t)i * n + q) * KB + j];
+    }
+    const double rp = (double)fmaf(opa, fp, rs[p]);
+    const double rq = (double)fmaf(opa, fq, rs[q]);
+    const double z = rq - rp;
+    loss[j] = z > 0 ? z + log1p(exp(-z)) : log1p(exp(z));
+    const double s = 1.0 / (1.0 + exp(-z));
+    sg[j] = s;
+    const long long fx = __double2ll_rn(s * G_SCALE);
+    atomicAdd(&gacc[q], (unsigned long long)fx);
+    atomicAdd(&gacc[p], (unsigned long long)(-fx));
+}
+
+// lam[q][j] += (1+alpha) sg_j, lam[p][j] -= (1+alpha) sg_j  (one thread per column)
+__global__ void scatter_g_k(float *lam, const int32_t *pos, const int32_t *neg, const double *sg, int kb, float opa)
+{
+    const int j = threadIdx.x;
+    if (j >= kb) return;
+    const float a = (float)((double)opa * sg[j]);
+    lam[(int64_t)neg[j] * KB + j] += a;
+    lam[(int64_t)pos[j] * KB + j] -= a;
+}
+
+// sum of the per-triple losses in triple order
+__global__ void loss_sum_k(const double *loss, int ntrip, double *out)
+{
+    double s = 0.0;
+    for (int t = 0; t < ntrip; ++t) s += loss[t];
+    out[0] = s;
+}
+
+__global__ void gacc_to_float_k(const unsigned long long *gacc, int64_t n, float *G)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        G[v] = (float)((double)(long long)gacc[v] / G_SCALE);
+}
+
+__global__ void axpy_k(float *y, const float *x, int64_t n)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) y[v] += x[v];
+}
+
+// GE[e] += coef * sum_j lam[v][j] * X[u][j] over CSR(A~) edges (u = row, v = col)
+template <int W>
+__global__ void sddmm_k(const int32_t *row, const int32_t *col, int64_t m, const float *lam, const float *X, int kc,
+                        float coef, float *GE)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = row[e], v = col[e];
+        float dot = 0.0f;
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+            if (j < kc) dot = fmaf(__ldg(lam + v * W + j), __ldg(X + u * W + j), dot);
+        GE[e] += coef * dot;
+    }
+}
+
+// dL/dw_e = (GE_e - sum_{e' in row} GE_e' A~_e') / d_u  (warp per row, fixed order)
+__global__ void jacobian_k(const int64_t *rp_a, const float *GE, const float *val_a, const double *inv_d, int64_t n,
+                           float *grad_w)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const int64_t e0 = rp_a[u], e1 = rp_a[u + 1];
+        float s = 0.0f;
+        for (int64_t e = e0 + lane; e < e1; e += 32) s = fmaf(GE[e], val_a[e], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const float inv = (float)inv_d[u];
+        for (int64_t e = e0 + lane; e < e1; e += 32) grad_w[e] = (GE[e] - s) * inv;
+    }
+}
+
+// dL/dtheta_j = sum_e grad_w_e w_e f_ej: block partials (FP32), then the last
+// block sums them in FP64 in block order.
+__global__ void theta_grad_k(const float *feat, const float *w, const float *gw, int d, int64_t m, double *part,
+                             unsigned *ticket, double *out)
+{
+    extern __shared__ float s_acc[];   // [blockDim.x / 32][d]
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float acc[16];
+    for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const float a = gw[e] * w[e];
+        for (int j = 0; j < d; ++j) acc[j] = fmaf(a, feat[e * d + j], acc[j]);
+    }
+    for (int j = 0; j < d; ++j) {
+        float v = acc[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_acc[warp * d + j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < d) {
+        float v = 0.0f;
+        for (int i = 0; i < nw; ++i) v += s_acc[i * d + threadIdx.x];
+        part[(int64_t)blockIdx.x * d + threadIdx.x] = (double)v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x < d) {
+        double v = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&part[(int64_t)b * d + threadIdx.x]);
+        out[threadIdx.x] = v;
+    }
+    if (threadIdx.x == 0) *ticket = 0;
+}
+
+double alpha_of(double c, int S, int T)
+{
+    const double a = std::pow(1.0 - c, (double)S), b = std::pow(1.0 - c, (double)T);
+    return (a - b) / (1.0 - a);
+}
+
+}  // namespace
+
+void ensure_row_ids(tpa_graph *g, cudaStream_t s)
+{
+    if (g->row_a.p) return;
+    g->row_a.ensure((size_t)std::max<int64_t>(g->m, 1) * sizeof(int32_t), s);
+    row_ids_k<<<grid_for(g->n * 32), 256, 0, s>>>(g->rp_a.as<int64_t>(), g->n, g->row_a.as<int32_t>());
+    note_launch("adjoint");
+    TPA_CHECK_LAUNCH();
+}
+
+void set_edge_weights(tpa_graph *g, const float *w_any, cudaStream_t s, bool drop_preprocessing)
+{
+    const int64_t m = g->m, n = g->n;
+    g->w_a.ensure((size_t)std::max<int64_t>(m, 1) * sizeof(float), s);
+    g->inv_d.ensure((size_t)n * sizeof(double), s);
+    if (m) copy_in(g->w_a.p, w_any, (size_t)m * sizeof(float), s);
+    normalise_k<<<grid_for(n * 32), 256, 0, s>>>(g->rp_a.as<int64_t>(), g->w_a.as<float>(), g->perm_a2t.as<uint32_t>(),
+                                                n, g->val_a.as<float>(), g->val_t.as<float>(), g->inv_d.as<double>());
+    note_launch("adjoint");
+    TPA_CHECK_LAUNCH();
+    g->weighted = true;
+    if (drop_preprocessing) g->has_pre = false;   // the stranger vector belongs to the old weights
+}
+
+void weights_from_features(const float *feat, const float *theta, int d, int64_t m, float *w, cudaStream_t s)
+{
+    weights_k<<<grid_for(m), 256, (size_t)d * sizeof(float), s>>>(feat, theta, d, m, w);
+    note_launch("adjoint");
+    TPA_CHECK_LAUNCH();
+}
+
+void theta_grad(const float *feat, const float *w, const float *gw, int d, int64_t m, double *out, cudaStream_t s)
+{
+    const unsigned blocks = std::min<unsigned>(grid_for(m), 1024);
+    DevBuf part, tick;
+    part.ensure((size_t)blocks * d * sizeof(double), s);
+    tick.ensure(sizeof(unsigned), s);
+    TPA_CUDA(cudaMemsetAsync(tick.p, 0, sizeof(unsigned), s));
+    theta_grad_k<<<blocks, 256, (size_t)8 * d * sizeof(float), s>>>(feat, w, gw, d, m, part.as<double>(),
+                                                                   tick.as<unsigned>(), out);
+    note_launch("adjoint");
+    TPA_CHECK_LAUNCH();
+    part.release(s);
+    tick.release(s);
+}
+
+// Loss and dL/dw (device float[m], CSR(A~) order).  seeds/pos/neg are device arrays.
+double loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const int32_t *neg, int ntrip, double c,
+                 int S, int T, int K, float *grad_w, cudaStream_t s)
+{
+    const int64_t n = g->n, m = g->m;
+    const float decay = (float)(1.0 - c);
+    const float opa = (float)(1.0 + alpha_of(c, S, T));
+    ensure_row_ids(g, s);
+    DevBuf xs, rs, F, lamA, lamB, GE, loss, sg, gacc, Gs;
+    xs.ensure((size_t)(K + 1) * n * sizeof(float), s);
+    rs.ensure((size_t)n * sizeof(float), s);
+    F.ensure((size_t)S * n * KB * sizeof(float), s);
+    lamA.ensure((size_t)n * KB * sizeof(float), s);
+    lamB.ensure((size_t)n * KB * sizeof(float), s);
+    GE.ensure((size_t)std::max<int64_t>(m, 1) * sizeof(float), s);
+    loss.ensure((size_t)ntrip * sizeof(double), s);
+    sg.ensure((size_t)ntrip * sizeof(double), s);
+    gacc.ensure((size_t)n * sizeof(unsigned long long), s);
+    Gs.ensure((size_t)n * sizeof(float), s);
+    TPA_CUDA(cudaMemsetAsync(GE.p, 0, GE.bytes, s));
+    TPA_CUDA(cudaMemsetAsync(gacc.p, 0, gacc.bytes, s));
+    float *X = xs.as<float>();
+
+    // stranger chain, K fixed
+    fill_k<<<grid_for(n), 256, 0, s>>>(X, n, (float)(c * (1.0 / (double)n)));
+    for (int i = 1; i <= K; ++i) spmv_apply(g, 0, X + (int64_t)(i - 1) * n, X + (int64_t)i * n, 1, decay, s);
+    stranger_sum_k<<<grid_for(n), 256, 0, s>>>(X, n, T, K, rs.as<float>());
+    note_launch("adjoint", 2);
+    TPA_CHECK_LAUNCH();
+
+    // family chains in batches of KB triples: forward, scores, backward
+    float *Fp = F.as<float>();
+    for (int t0 = 0; t0 < ntrip; t0 += KB) {
+        const int kb = std::min(KB, ntrip - t0);
+        TPA_CUDA(cudaMemsetAsync(Fp, 0, (size_t)n * KB * sizeof(float), s));
+        family_init_k<<<1, 32, 0, s>>>(Fp, seeds + t0, kb, (float)c);
+        // always KB columns: the buffers are laid out [n][KB] and padding columns are zero
+        for (int i = 1; i < S; ++i) spmv_apply(g, 0, Fp + (int64_t)(i - 1) * n * KB, Fp + (int64_t)i * n * KB, KB, decay, s);
+        pair_k<<<1, 32, 0, s>>>(Fp, n, S, pos + t0, neg + t0, kb, opa, rs.as<float>(), loss.as<double>() + t0,
+                                sg.as<double>() + t0, gacc.as<unsigned long long>());
+        float *lam = lamA.as<float>(), *nxt = lamB.as<float>();
+        TPA_CUDA(cudaMemsetAsync(lam, 0, (size_t)n * KB * sizeof(float), s));
+        scatter_g_k<<<1, 32, 0, s>>>(lam, pos + t0, neg + t0, sg.as<double>() + t0, kb, opa);
+        for (int i = S - 1; i >= 1; --i) {
+            sddmm_k<KB><<<grid_for(m), 256, 0, s>>>(g->row_a.as<int32_t>(), g->col_a.as<int32_t>(), m, lam,
+                                                    Fp + (int64_t)(i - 1) * n * KB, kb, decay, GE.as<float>());
+            if (i > 1) {
+                spmv_apply(g, 1, lam, nxt, KB, decay, s);
+                std::swap(lam, nxt);
+                scatter_g_k<<<1, 32, 0, s>>>(lam, pos + t0, neg + t0, sg.as<double>() + t0, kb, opa);
+            }
+        }
+        note_launch("adjoint", 3 + 2 * (S - 1));
+        TPA_CHECK_LAUNCH();
+    }
+
+    // stranger backward: m_K = G, m_i = [i >= T] G + P^T m_{i+1}
+    gacc_to_float_k<<<grid_for(n), 256, 0, s>>>(gacc.as<unsigned long long>(), n, Gs.as<float>());
+    float *mu = lamA.as<float>(), *mn = lamB.as<float>();   // [n] vectors now
+    TPA_CUDA(cudaMemcpyAsync(mu, Gs.p, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    for (int i = K; i >= 1; --i) {
+        sddmm_k<1><<<grid_for(m), 256, 0, s>>>(g->row_a.as<int32_t>(), g->col_a.as<int32_t>(), m, mu,
+                                               X + (int64_t)(i - 1) * n, 1, decay, GE.as<float>());
+        if (i > 1) {
+            spmv_apply(g, 1, mu, mn, 1, decay, s);
+            std::swap(mu, mn);
+            if (i - 1 >= T) axpy_k<<<grid_for(n), 256, 0, s>>>(mu, Gs.as<float>(), n);
+        }
+    }
+    note_launch("adjoint", 1 + 2 * K);
+    jacobian_k<<<grid_for(n * 32), 256, 0, s>>>(g->rp_a.as<int64_t>(), GE.as<float>(), g->val_a.as<float>(),
+                                               g->inv_d.as<double>(), n, grad_w);
+    note_launch("adjoint");
+    TPA_CHECK_LAUNCH();
+
+    loss_sum_k<<<1, 1, 0, s>>>(loss.as<double>(), ntrip, sg.as<double>());
+    note_launch("adjoint");
+    TPA_CHECK_LAUNCH();
+    double L = 0.0;
+    TPA_CUDA(cudaMemcpyAsync(&L, sg.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TPA_CUDA(cudaStreamSynchronize(s));
+    xs.release(s); rs.release(s); F.release(s); lamA.release(s); lamB.release(s); GE.release(s);
+    loss.release(s); sg.release(s); gacc.release(s); Gs.release(s);
+    return L;
+}
+
+}  // namespace tpa

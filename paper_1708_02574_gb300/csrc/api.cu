@@ -156,15 +156,17 @@ void tpa_free_graph(tpa_graph *g)
     cudaStream_t s = 0;
     cudaDeviceSynchronize();
     DevBuf *bufs[] = {&g->rp_t, &g->col_t, &g->val_t, &g->rp_a, &g->col_a, &g->val_a, &g->outdeg, &g->r_str,
+                      &g->perm_a2t, &g->w_a, &g->inv_d, &g->row_a, &g->ws.u, &g->ws.touched,
                       &g->ws.x, &g->ws.y, &g->ws.r, &g->ws.carry, &g->ws.head, &g->ws.tl1, &g->ws.fix,
                       &g->ws.ctl, &g->ws.seeds, &g->ws.out, &g->ws.iters};
     for (DevBuf *b : bufs) b->release(s);
-    for (auto &kv : g->plans_t) {
-        kv.second.tile_x.release(s);
-        kv.second.tile_y.release(s);
-        kv.second.head_row.release(s);
-        kv.second.head_first.release(s);
-    }
+    for (auto *plans : {&g->plans_t, &g->plans_a})
+        for (auto &kv : *plans) {
+            kv.second.tile_x.release(s);
+            kv.second.tile_y.release(s);
+            kv.second.head_row.release(s);
+            kv.second.head_first.release(s);
+        }
     if (g->ws.hflag) cudaFreeHost(g->ws.hflag);
     cudaStreamSynchronize(s);
     delete g;
@@ -345,6 +347,80 @@ tpa_status tpa_cpi(tpa_graph *g, const int32_t *seeds, int k, double c, double e
 tpa_status tpa_cpi_exact(tpa_graph *g, int32_t seed, double c, double eps, float *out, int32_t *iters, void *stream)
 {
     return tpa_cpi(g, &seed, 1, c, eps, 0, -1, out, iters, stream);
+}
+
+tpa_status tpa_set_edge_weights(tpa_graph *g, const float *w, void *stream)
+{
+    API_BEGIN
+    TPA_REQUIRE(g != nullptr && (w != nullptr || g->m == 0), "tpa_set_edge_weights: NULL argument");
+    set_edge_weights(g, w, (cudaStream_t)stream);
+    if (!is_device_ptr(w)) TPA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    API_END
+}
+
+tpa_status tpa_edge_weights(const float *feat, const float *theta, int d, int64_t m, float *w, void *stream)
+{
+    API_BEGIN
+    TPA_REQUIRE(d >= 1 && d <= 16 && m >= 0, "tpa_edge_weights: d = %d outside [1, 16] or m < 0", d);
+    TPA_REQUIRE(m == 0 || (is_device_ptr(feat) && is_device_ptr(theta) && is_device_ptr(w)),
+                "tpa_edge_weights: feat, theta and w must be device memory");
+    if (m) weights_from_features(feat, theta, d, m, w, (cudaStream_t)stream);
+    API_END
+}
+
+tpa_status tpa_loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const int32_t *neg, int ntrip,
+                         double c, int S, int T, int K, double *loss, float *grad_w, void *stream)
+{
+    API_BEGIN
+    TPA_REQUIRE(g && seeds && pos && neg && loss && grad_w, "tpa_loss_grad: NULL argument");
+    TPA_REQUIRE(ntrip >= 1, "tpa_loss_grad: ntrip = %d < 1", ntrip);
+    TPA_REQUIRE(c > 0.0 && c < 1.0, "tpa_loss_grad: c = %g outside (0, 1)", c);
+    TPA_REQUIRE(S >= 1 && S <= T && T <= K && K <= 100000, "tpa_loss_grad: need 1 <= S <= T <= K");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!g->weighted) {
+        // unit weights reproduce the unweighted A~ and give the inverse degrees
+        DevBuf ones;
+        ones.ensure((size_t)std::max<int64_t>(g->m, 1) * sizeof(float), s);
+        std::vector<float> h((size_t)std::max<int64_t>(g->m, 1), 1.0f);
+        TPA_CUDA(cudaMemcpyAsync(ones.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        set_edge_weights(g, ones.as<float>(), s, false);   // RN32(1/d) either way: preprocessing stays valid
+        TPA_CUDA(cudaStreamSynchronize(s));
+        ones.release(s);
+    }
+    std::vector<int32_t> hs = read_seeds(seeds, ntrip, g->n, s), hp = read_seeds(pos, ntrip, g->n, s),
+                         hq = read_seeds(neg, ntrip, g->n, s);
+    DevBuf trip;
+    trip.ensure((size_t)3 * ntrip * sizeof(int32_t), s);
+    TPA_CUDA(cudaMemcpyAsync(trip.as<int32_t>(), hs.data(), (size_t)ntrip * 4, cudaMemcpyHostToDevice, s));
+    TPA_CUDA(cudaMemcpyAsync(trip.as<int32_t>() + ntrip, hp.data(), (size_t)ntrip * 4, cudaMemcpyHostToDevice, s));
+    TPA_CUDA(cudaMemcpyAsync(trip.as<int32_t>() + 2 * ntrip, hq.data(), (size_t)ntrip * 4, cudaMemcpyHostToDevice, s));
+    const bool host_out = !is_device_ptr(grad_w);
+    DevBuf gw;
+    float *dgw = grad_w;
+    if (host_out) {
+        gw.ensure((size_t)std::max<int64_t>(g->m, 1) * sizeof(float), s);
+        dgw = gw.as<float>();
+    }
+    *loss = loss_grad(g, trip.as<int32_t>(), trip.as<int32_t>() + ntrip, trip.as<int32_t>() + 2 * ntrip, ntrip, c, S,
+                      T, K, dgw, s);
+    if (host_out && g->m) {
+        TPA_CUDA(cudaMemcpyAsync(grad_w, dgw, (size_t)g->m * sizeof(float), cudaMemcpyDeviceToHost, s));
+        TPA_CUDA(cudaStreamSynchronize(s));
+    }
+    trip.release(s);
+    gw.release(s);
+    API_END
+}
+
+tpa_status tpa_theta_grad(const float *feat, const float *w, const float *grad_w, int d, int64_t m,
+                          double *grad_theta, void *stream)
+{
+    API_BEGIN
+    TPA_REQUIRE(d >= 1 && d <= 16 && m >= 1, "tpa_theta_grad: d = %d outside [1, 16] or m < 1", d);
+    TPA_REQUIRE(is_device_ptr(feat) && is_device_ptr(w) && is_device_ptr(grad_w) && is_device_ptr(grad_theta),
+                "tpa_theta_grad: every array must be device memory");
+    theta_grad(feat, w, grad_w, d, m, grad_theta, (cudaStream_t)stream);
+    API_END
 }
 
 struct PreHeader {

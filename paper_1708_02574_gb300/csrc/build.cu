@@ -468,6 +468,12 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
         note_launch("build", 2);
     }
     TPA_CHECK_LAUNCH();
+    // keep the payload of the source sort: for each CSR(A~) edge, its index in CSR(A~^T)
+    DevBuf &perm = cur2 ? ib : ia;
+    g->perm_a2t.release(s);
+    g->perm_a2t = perm;
+    perm.p = nullptr;
+    perm.bytes = 0;
     TPA_CUDA(cudaStreamSynchronize(s));
     ka.release(s); kb.release(s); hist.release(s); tmp.release(s); ia.release(s); ib.release(s); cnt.release(s);
 }

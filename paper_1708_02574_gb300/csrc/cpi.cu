@@ -501,9 +501,12 @@ __device__ __forceinline__ void cp_async_row(float *base, int elem, const float 
 template <int V, int ITEMS>
 struct __align__(16) WarpTile {
     static constexpr int L = 32 * ITEMS;
-    float prod[L * V];     // gathered rows X[col], swizzled (see Swz)
-    float rowsum[L * V];   // finished row sums, swizzled
-    float val[L];          // A~ values of the tile, swizzled as V = 1 rows
+    // V <= 2: prod holds the products val * X[col]; V >= 4: prod holds the
+    // gathered rows X[col] (copied by cp.async) and val the A~ values
+    static constexpr bool ASYNC = V >= 4;
+    float prod[L * V];               // swizzled (see Swz)
+    float rowsum[L * V];             // finished row sums, swizzled
+    float val[ASYNC ? L : 4];        // swizzled as V = 1 rows
     int32_t end[L + 4];
 };
 
@@ -544,14 +547,36 @@ spmvw_tile_k(Params p)
                 c[j] = i < nnz ? __ldcs(p.col + y0 + i) : 0;
                 v[j] = i < nnz ? __ldcs(p.val + y0 + i) : 0.0f;
             }
-            // gathers go straight to shared memory, all in flight at once
+            if constexpr (WT::ASYNC) {
+                // wide rows: gathers go straight to shared memory, all in flight at once
 #pragma unroll
-            for (int j = 0; j < ITEMS; ++j)
-                if (lane + j * 32 < nnz) cp_async_row<V>(S.prod, lane + j * 32, p.x + (int64_t)c[j] * V);
+                for (int j = 0; j < ITEMS; ++j)
+                    if (lane + j * 32 < nnz) cp_async_row<V>(S.prod, lane + j * 32, p.x + (int64_t)c[j] * V);
 #pragma unroll
-            for (int j = 0; j < ITEMS; ++j)
-                if (lane + j * 32 < nnz) S.val[Swz<1>::slot(lane + j * 32, 0)] = v[j];
-            cp_async_wait_all();
+                for (int j = 0; j < ITEMS; ++j)
+                    if (lane + j * 32 < nnz) S.val[Swz<1>::slot(lane + j * 32, 0)] = v[j];
+                cp_async_wait_all();
+            } else {
+                // narrow rows: gather into registers, stage the products
+                float xv[ITEMS][V];
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j) {
+                    if (lane + j * 32 < nnz) {
+                        ld_row<V>(p.x + (int64_t)c[j] * V, xv[j]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < V; ++q) xv[j][q] = 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j)
+                    if (lane + j * 32 < nnz) {
+                        float pr[V];
+#pragma unroll
+                        for (int q = 0; q < V; ++q) pr[q] = v[j] * xv[j][q];
+                        sts_row<V>(S.prod, lane + j * 32, pr);
+                    }
+            }
         }
         __syncwarp();
 
@@ -575,9 +600,14 @@ spmvw_tile_k(Params p)
                 if (ys < row_end) {
                     float xr[V];
                     lds_row<V>(S.prod, ys, xr);
-                    const float vv = S.val[Swz<1>::slot(ys, 0)];
+                    if constexpr (WT::ASYNC) {
+                        const float vv = S.val[Swz<1>::slot(ys, 0)];
 #pragma unroll
-                    for (int q = 0; q < V; ++q) acc[q] = fmaf(vv, xr[q], acc[q]);
+                        for (int q = 0; q < V; ++q) acc[q] = fmaf(vv, xr[q], acc[q]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < V; ++q) acc[q] += xr[q];
+                    }
                     ++ys;
                 } else {
                     sts_row<V>(S.rowsum, xs, acc);
@@ -639,6 +669,161 @@ spmvw_tile_k(Params p)
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < V; ++q) p.tl1[t * V + q] = l1[q];
+        }
+    }
+}
+
+// --------------------------------------------------- group-walker kernel ---
+// Warp-level merge path where each walker is a group of G lanes and each lane
+// owns V consecutive columns of a batch of KP = G*V seeds: for a nonzero the
+// group gathers one contiguous row X[col][0..KP) (G*V*4 bytes, one or a few
+// sectors), so a gathered byte is a useful byte.  Only the tile's row ends,
+// columns and values are staged in shared memory (coalesced), which keeps
+// tiles long and occupancy high.  Per warp tile of L = (32/G) * ITEMS steps:
+//   1. stage row ends, col, val;
+//   2. each walker finds its diagonal, then walks ITEMS steps in chunks of
+//      PF: first it decides the steps and issues the PF gathers, then it
+//      accumulates and emits finished rows (epilogue fused, coalesced within
+//      the group);
+//   3. a shuffle segmented scan over the walkers resolves carries; the
+//      tile's first row is deferred to the fixup when it started earlier.
+template <int G, int V, int ITEMS>
+struct GroupTile {
+    static constexpr int NW = 32 / G;
+    static constexpr int L = NW * ITEMS;
+    int32_t col[L];
+    float val[L];
+    int32_t end[L + 4];
+};
+
+template <int G, int V, int ITEMS, int PF, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) spmvg_tile_k(Params p)
+{
+    using GT = GroupTile<G, V, ITEMS>;
+    constexpr int NW = GT::NW, KP = G * V;
+    static_assert(ITEMS % PF == 0, "PF");
+    static_assert(sizeof(GT) * WARPS <= 48 * 1024, "static shared memory is limited to 48 KB per block");
+    __shared__ GT S_all[WARPS];
+    const CtlView cv = ctl_view(p.ctl);
+    if (*(volatile int32_t *)&cv.hdr->done) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int w = lane / G, gl = lane % G, col0 = gl * V;
+    int alive[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) alive[j] = cv.alive[col0 + j];
+    GT &S = S_all[warp];
+
+    for (int64_t t = (int64_t)blockIdx.x * WARPS + warp; t < p.tiles; t += (int64_t)gridDim.x * WARPS) {
+        const int32_t x0 = p.tile_x[t], x1 = p.tile_x[t + 1];
+        const int64_t y0 = p.tile_y[t], y1 = p.tile_y[t + 1];
+        const int nrows = x1 - x0, nnz = (int)(y1 - y0);
+        const bool defer_first = p.head_row[t] >= 0;
+        __syncwarp();
+        for (int i = lane; i < nrows; i += 32) S.end[i] = (int)(__ldcs(p.rp + x0 + i + 1) - y0);
+        if (lane == 0) S.end[nrows] = 0x7fffffff;
+        for (int i = lane; i < nnz; i += 32) {
+            S.col[i] = __ldcs(p.col + y0 + i);
+            S.val[i] = __ldcs(p.val + y0 + i);
+        }
+        __syncwarp();
+
+        const int d = min(w * ITEMS, nrows + nnz);
+        int lo = max(0, d - nnz), hi = min(d, nrows);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (S.end[mid] + mid + 1 <= d) lo = mid + 1; else hi = mid;
+        }
+        int xs = lo, ys = d - lo;
+        const int avail = nrows + nnz - d;
+        float acc[V], first_val[V];
+        float l1[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            acc[j] = 0.0f;
+            first_val[j] = 0.0f;
+            l1[j] = 0.0f;
+        }
+        int first_row = -1;
+#pragma unroll
+        for (int c0 = 0; c0 < ITEMS; c0 += PF) {
+            float xv[PF][V];
+            float vv[PF];
+            unsigned nzmask = 0;
+            {
+                int xa = xs, ya = ys;
+#pragma unroll
+                for (int it = 0; it < PF; ++it) {
+                    if (c0 + it < avail) {
+                        if (ya < S.end[xa]) {
+                            vv[it] = S.val[ya];
+                            ld_row<V>(p.x + (int64_t)S.col[ya] * KP + col0, xv[it]);
+                            nzmask |= 1u << it;
+                            ++ya;
+                        } else {
+                            ++xa;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int it = 0; it < PF; ++it) {
+                if (c0 + it < avail) {
+                    if (nzmask & (1u << it)) {
+#pragma unroll
+                        for (int j = 0; j < V; ++j) acc[j] = fmaf(vv[it], xv[it][j], acc[j]);
+                        ++ys;
+                    } else {
+                        if (first_row < 0) {
+                            first_row = xs;
+#pragma unroll
+                            for (int j = 0; j < V; ++j) first_val[j] = acc[j];
+                        } else {
+                            epilogue<KP, V>(p, (int64_t)(x0 + xs), col0, acc, alive, l1);
+                        }
+#pragma unroll
+                        for (int j = 0; j < V; ++j) acc[j] = 0.0f;
+                        ++xs;
+                    }
+                }
+            }
+        }
+
+        // segmented inclusive scan of the walkers' carries (key = row)
+        const int key = xs;
+#pragma unroll
+        for (int off = 1; off < NW; off <<= 1) {
+            const int k2 = __shfl_up_sync(0xffffffffu, key, off * G);
+            const bool take = w >= off && k2 == key;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const float v2 = __shfl_up_sync(0xffffffffu, acc[j], off * G);
+                if (take) acc[j] += v2;
+            }
+        }
+        float prev[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) prev[j] = __shfl_up_sync(0xffffffffu, acc[j], G);
+        if (first_row >= 0) {
+            float tot[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) tot[j] = first_val[j] + (w > 0 ? prev[j] : 0.0f);
+            if (first_row == 0 && defer_first) {
+                st_row<V>(p.head + t * KP + col0, tot);
+            } else {
+                epilogue<KP, V>(p, (int64_t)(x0 + first_row), col0, tot, alive, l1);
+            }
+        }
+        if (w == NW - 1) st_row<V>(p.carry + t * KP + col0, acc);
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            float a = l1[j];
+#pragma unroll
+            for (int o = G; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            l1[j] = a;
+        }
+        if (lane < G) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) p.tl1[t * KP + col0 + j] = l1[j];
         }
     }
 }
@@ -945,7 +1130,8 @@ constexpr float FX_SCALE_F = 9223372036854775808.0f;      // 2^63, exact in FP32
 constexpr float FX_INV_F = 1.0842021724855044e-19f;       // 2^-63, exact in FP32
 
 __global__ void push_x2_k(const int64_t *rp_a, const int32_t *col_a, const float *val_a, const int32_t *seeds,
-                          int KP, float c_f, float decay, unsigned long long *U, float *R, void *ctl)
+                          int KP, float c_f, float decay, unsigned long long *U, uint32_t *touched, float *R,
+                          void *ctl)
 {
     const CtlView cv = ctl_view(ctl);
     const int j = blockIdx.y;
@@ -969,16 +1155,21 @@ __global__ void push_x2_k(const int64_t *rp_a, const int32_t *col_a, const float
         const int64_t f0 = rp_a[u], f1 = rp_a[u + 1];
         for (int64_t f = f0 + gt; f < f1; f += gs) {
             const float q = val_a[f] * x1u;
-            atomicAdd(&U[(int64_t)col_a[f] * KP + j], __float2ull_rn(q * FX_SCALE_F));
+            const int32_t v = col_a[f];
+            atomicAdd(&U[(int64_t)v * KP + j], __float2ull_rn(q * FX_SCALE_F));
+            const uint32_t bit = 1u << (v & 31);
+            if (!(touched[v >> 5] & bit)) atomicOr(&touched[v >> 5], bit);   // rows the conversion must read
         }
     }
 }
 
-// X = x2 in FP32 (padding columns zero), U cleared for the next chunk,
-// ||x2||_1 per column; the last block applies the break tests after x1 and x2.
+// X = x2 in FP32 (padding columns zero); only rows marked in `touched` read U,
+// and U and the marks are cleared for the next chunk; ||x2||_1 per column; the
+// last block applies the break tests after x1 and x2.  A warp covers 32
+// consecutive rows, i.e. one mark word.
 template <int KP>
-__global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, float *X, int64_t n, int kc, float decay,
-                                                    double eps, double *part, void *ctl)
+__global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, uint32_t *touched, float *X, int64_t n,
+                                                    int kc, float decay, double eps, double *part, void *ctl)
 {
     __shared__ float s_red[8][KP];
     __shared__ double s_fin[256];
@@ -989,11 +1180,13 @@ __global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, float
     float nrm[KP];
 #pragma unroll
     for (int j = 0; j < KP; ++j) nrm[j] = 0.0f;
+    const uint32_t word = v < n ? touched[v >> 5] : 0u;
     if (v < n) {
+        const bool hit = (word >> (v & 31)) & 1u;
 #pragma unroll
         for (int j = 0; j < KP; ++j) {
             float x = 0.0f;
-            if (j < kc) {
+            if (hit && j < kc) {
                 const unsigned long long a = U[v * KP + j];
                 if (a) {
                     U[v * KP + j] = 0ull;
@@ -1004,6 +1197,8 @@ __global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, float
             nrm[j] = x;
         }
     }
+    __syncwarp();
+    if (lane == 0 && v < n && word) touched[v >> 5] = 0u;
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
         float a = nrm[j];
@@ -1092,11 +1287,13 @@ static unsigned grid_1d(int64_t work, int threads)
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
 }
 
-const Plan &get_plan(tpa_graph *g, int L, cudaStream_t s)
+const Plan &get_plan(tpa_graph *g, int L, cudaStream_t s, int which)
 {
-    auto it = g->plans_t.find(L);
-    if (it != g->plans_t.end()) return it->second;
-    Plan &P = g->plans_t[L];
+    std::map<int, Plan> &plans = which ? g->plans_a : g->plans_t;
+    const int64_t *rp = which ? g->rp_a.as<int64_t>() : g->rp_t.as<int64_t>();
+    auto it = plans.find(L);
+    if (it != plans.end()) return it->second;
+    Plan &P = plans[L];
     P.L = L;
     P.tiles = std::max<int64_t>(1, (g->n + g->m + L - 1) / L);
     TPA_REQUIRE(P.tiles < INT32_MAX, "merge-path plan: too many tiles");
@@ -1104,9 +1301,9 @@ const Plan &get_plan(tpa_graph *g, int L, cudaStream_t s)
     P.tile_y.ensure((size_t)(P.tiles + 1) * sizeof(int64_t), s);
     P.head_row.ensure((size_t)P.tiles * sizeof(int32_t), s);
     P.head_first.ensure((size_t)P.tiles * sizeof(int32_t), s);
-    plan_tiles_k<<<grid_1d(P.tiles + 1, 256), 256, 0, s>>>(g->rp_t.as<int64_t>(), g->n, g->m, L, P.tiles,
+    plan_tiles_k<<<grid_1d(P.tiles + 1, 256), 256, 0, s>>>(rp, g->n, g->m, L, P.tiles,
                                                             P.tile_x.as<int32_t>(), P.tile_y.as<int64_t>());
-    plan_heads_k<<<grid_1d(P.tiles, 256), 256, 0, s>>>(g->rp_t.as<int64_t>(), P.tile_x.as<int32_t>(),
+    plan_heads_k<<<grid_1d(P.tiles, 256), 256, 0, s>>>(rp, P.tile_x.as<int32_t>(),
                                                        P.tile_y.as<int64_t>(), P.tiles, P.head_row.as<int32_t>(),
                                                        P.head_first.as<int32_t>());
     note_launch("plan", 2);
@@ -1161,6 +1358,19 @@ static void launch_spmvw(const Params &p, cudaStream_t s)
     spmvw_tile_k<V, ITEMS, WARPS><<<(unsigned)grid, WARPS * 32, 0, s>>>(p);
 }
 
+template <int G, int V, int ITEMS, int PF, int WARPS>
+static void launch_spmvg(const Params &p, cudaStream_t s)
+{
+    static int per_sm = 0;
+    if (!per_sm) {
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmvg_tile_k<G, V, ITEMS, PF, WARPS>,
+                                                               WARPS * 32, 0));
+        per_sm = std::max(per_sm, 1);
+    }
+    const int64_t grid = std::min<int64_t>((p.tiles + WARPS - 1) / WARPS, (int64_t)per_sm * num_sms());
+    spmvg_tile_k<G, V, ITEMS, PF, WARPS><<<(unsigned)grid, WARPS * 32, 0, s>>>(p);
+}
+
 template <int KP>
 static void launch_fix(const Params &p, unsigned blocks, cudaStream_t s)
 {
@@ -1187,6 +1397,7 @@ struct Variant {
 
 #define TPA_VARIANT(G, V, I, PF) {{G, V, I, PF, CTA}, launch_spmm<G, V, I, PF>, launch_fix<G * V>}
 #define TPA_VARIANTW(V, I, W) {{1, V, I, I, 32}, launch_spmvw<V, I, W>, launch_fix<V>}
+#define TPA_VARIANTG(G, V, I, PF) {{G, V, I, PF, 32}, launch_spmvg<G, V, I, PF, 8>, launch_fix<G * V>}
 static const Variant kVariants[] = {
     TPA_VARIANTW(1, 8, 8),
     TPA_VARIANTW(1, 6, 8),
@@ -1199,6 +1410,16 @@ static const Variant kVariants[] = {
     TPA_VARIANTW(8, 4, 4),
     TPA_VARIANTW(8, 6, 2),
     TPA_VARIANTW(8, 2, 8),
+    TPA_VARIANTG(8, 1, 32, 16),
+    TPA_VARIANTG(8, 1, 16, 16),
+    TPA_VARIANTG(4, 2, 32, 16),
+    TPA_VARIANTG(2, 4, 16, 8),
+    TPA_VARIANTG(4, 1, 32, 16),
+    TPA_VARIANTG(2, 2, 16, 16),
+    TPA_VARIANTG(16, 1, 32, 16),
+    TPA_VARIANTG(8, 2, 32, 16),
+    TPA_VARIANTG(8, 4, 32, 8),
+    TPA_VARIANTG(32, 1, 32, 16),
     TPA_VARIANT(1, 1, 8, 8),
     TPA_VARIANT(1, 2, 8, 8),
     TPA_VARIANT(1, 4, 8, 8),
@@ -1214,10 +1435,11 @@ static const Variant kVariants[] = {
 };
 #undef TPA_VARIANT
 #undef TPA_VARIANTW
+#undef TPA_VARIANTG
 
 // Padded width: the smallest power of two >= k (every power of two up to
 // KP_MAX has at least one kernel variant).
-static int kp_for(int k)
+int kp_for(int k)
 {
     int kp = 1;
     while (kp < k) kp <<= 1;
@@ -1235,14 +1457,14 @@ static bool g_push = true;
 constexpr int PUSH_MAX_OUTDEG = 256;   // seeds with more out-edges keep the pull path
 constexpr int PUSH_BLOCKS = 16;        // blocks per column in push_x2_k
 
-static void launch_convert(int KP, unsigned blocks, unsigned long long *U, float *X, int64_t n, int kc, float decay,
-                           double eps, double *part, void *ctl, cudaStream_t s)
+static void launch_convert(int KP, unsigned blocks, unsigned long long *U, uint32_t *touched, float *X, int64_t n,
+                           int kc, float decay, double eps, double *part, void *ctl, cudaStream_t s)
 {
     switch (KP) {
-    case 1: convert_x2_k<1><<<blocks, 256, 0, s>>>(U, X, n, kc, decay, eps, part, ctl); break;
-    case 2: convert_x2_k<2><<<blocks, 256, 0, s>>>(U, X, n, kc, decay, eps, part, ctl); break;
-    case 4: convert_x2_k<4><<<blocks, 256, 0, s>>>(U, X, n, kc, decay, eps, part, ctl); break;
-    default: convert_x2_k<8><<<blocks, 256, 0, s>>>(U, X, n, kc, decay, eps, part, ctl); break;
+    case 1: convert_x2_k<1><<<blocks, 256, 0, s>>>(U, touched, X, n, kc, decay, eps, part, ctl); break;
+    case 2: convert_x2_k<2><<<blocks, 256, 0, s>>>(U, touched, X, n, kc, decay, eps, part, ctl); break;
+    case 4: convert_x2_k<4><<<blocks, 256, 0, s>>>(U, touched, X, n, kc, decay, eps, part, ctl); break;
+    default: convert_x2_k<8><<<blocks, 256, 0, s>>>(U, touched, X, n, kc, decay, eps, part, ctl); break;
     }
 }
 
@@ -1328,15 +1550,19 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
         W.fix.ensure((size_t)std::max<unsigned>(fix_blocks, cblocks) * KP * sizeof(double), s);
         if (!W.u.p || W.u.bytes < (size_t)n * KP * sizeof(unsigned long long) || !W.u_clean) {
             W.u.ensure((size_t)n * KP * sizeof(unsigned long long), s);
+            W.touched.ensure((size_t)((n + 31) / 32) * sizeof(uint32_t), s);
             TPA_CUDA(cudaMemsetAsync(W.u.p, 0, W.u.bytes, s));
+            TPA_CUDA(cudaMemsetAsync(W.touched.p, 0, W.touched.bytes, s));
         }
         W.u_clean = false;
         TPA_CUDA(cudaMemsetAsync(r, 0, (size_t)n * KP * sizeof(float), s));
         const float decay_f = (float)(1.0 - a.c);
         push_x2_k<<<dim3(PUSH_BLOCKS, kc), 256, 0, s>>>(g->rp_a.as<int64_t>(), g->col_a.as<int32_t>(),
                                                         g->val_a.as<float>(), a.seeds + k0, KP, c_val, decay_f,
-                                                        W.u.as<unsigned long long>(), r, W.ctl.p);
-        launch_convert(KP, cblocks, W.u.as<unsigned long long>(), W.x.as<float>(), n, kc, decay_f, a.eps,
+                                                        W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), r,
+                                                        W.ctl.p);
+        launch_convert(KP, cblocks, W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), W.x.as<float>(), n, kc,
+                       decay_f, a.eps,
                        W.fix.as<double>(), W.ctl.p, s);
         note_launch("push", 2);
         TPA_CHECK_LAUNCH();
@@ -1576,6 +1802,54 @@ std::vector<int32_t> seed_outdegrees(tpa_graph *g, const int32_t *d_seeds, int k
     TPA_CUDA(cudaStreamSynchronize(s));
     tmp.release(s);
     return h;
+}
+
+void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float decay, cudaStream_t s)
+{
+    TPA_REQUIRE(kc >= 1 && kc <= 8, "spmv_apply: %d columns (at most 8)", kc);
+    const int KP = kp_for(kc);
+    const Variant &var = pick_variant(KP);
+    const Plan &P = get_plan(g, var.cfg.L(), s, which);
+    Workspace &W = g->ws;
+    W.carry.ensure((size_t)P.tiles * KP * sizeof(float), s);
+    W.head.ensure((size_t)P.tiles * KP * sizeof(float), s);
+    W.tl1.ensure((size_t)P.tiles * KP * sizeof(float), s);
+    const unsigned fix_blocks = fix_grid(KP, P.tiles);
+    W.fix.ensure((size_t)fix_blocks * KP * sizeof(double), s);
+    W.ctl.ensure(CTL_BYTES, s);
+    ctl_init_k<<<1, 256, 0, s>>>(W.ctl.p, kc);
+    Params p{};
+    p.rp = which ? g->rp_a.as<int64_t>() : g->rp_t.as<int64_t>();
+    p.col = which ? g->col_a.as<int32_t>() : g->col_t.as<int32_t>();
+    p.val = which ? g->val_a.as<float>() : g->val_t.as<float>();
+    p.n = g->n;
+    p.tile_x = P.tile_x.as<int32_t>();
+    p.tile_y = P.tile_y.as<int64_t>();
+    p.head_row = P.head_row.as<int32_t>();
+    p.head_first = P.head_first.as<int32_t>();
+    p.tiles = P.tiles;
+    p.x = x;
+    p.y = y;
+    p.decay = decay;
+    p.k = kc;
+    p.mode = MODE_ACC;
+    p.accumulate = 0;
+    p.iter = 1;
+    p.eps = 0.0;   // no break test: every column stays alive
+    p.carry = W.carry.as<float>();
+    p.head = W.head.as<float>();
+    p.tl1 = W.tl1.as<float>();
+    p.part = W.fix.as<double>();
+    p.ctl = W.ctl.p;
+    p.own = ctl_view(W.ctl.p).own;
+    ProfMark pm = prof_begin(s);
+    var.spmm(p, s);
+    prof_end(pm, spmm_family(KP), spmm_bytes(g->n, g->m, KP, kc, MODE_ACC, 0), s);
+    var.fix(p, fix_blocks, s);
+    note_launch("init");
+    note_launch(spmm_family(KP));
+    note_launch("fixup");
+    TPA_CHECK_LAUNCH();
 }
 
 void run_cpi(tpa_graph *g, const CpiArgs &a, cudaStream_t s)

@@ -85,6 +85,7 @@ struct Workspace {
     DevBuf out;             // device staging for host outputs
     DevBuf iters;           // int32 per-column iteration counts
     DevBuf u;               // push path: 64-bit fixed-point accumulator [n][KP]
+    DevBuf touched;         // push path: one bit per row reached by the push
     bool u_clean = false;   // u is known to be all zero
     int32_t *hflag = nullptr;   // pinned host mirror of the done flag (2 slots)
 };
@@ -99,6 +100,12 @@ struct tpa_graph {
     // CSR(A~): rows = sources
     tpa::DevBuf rp_a, col_a, val_a;
     tpa::DevBuf outdeg;
+    tpa::DevBuf perm_a2t;   // uint32[m]: position in CSR(A~^T) of each CSR(A~) edge
+    // weighted graphs (tpa_set_edge_weights)
+    tpa::DevBuf w_a;        // float[m] edge weights, CSR(A~) order
+    tpa::DevBuf inv_d;      // double[n] 1 / weighted out-degree
+    tpa::DevBuf row_a;      // int32[m] source of each CSR(A~) edge (made on first use)
+    bool weighted = false;
     // preprocessing result
     tpa::DevBuf r_str;
     bool has_pre = false;
@@ -106,6 +113,7 @@ struct tpa_graph {
     int T = 0;
     int64_t pre_iters = 0;
     std::map<int, tpa::Plan> plans_t;   // merge-path plans over CSR(A~^T) keyed by L
+    std::map<int, tpa::Plan> plans_a;   // merge-path plans over CSR(A~) keyed by L
     tpa::Workspace ws;
 };
 
@@ -126,7 +134,13 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
                cudaStream_t s);
 
 // cpi.cu
-const Plan &get_plan(tpa_graph *g, int L, cudaStream_t s);
+const Plan &get_plan(tpa_graph *g, int L, cudaStream_t s, int which = 0);   // which: 0 = A~^T, 1 = A~
+
+// One SpMV/SpMM step y = decay * M x for kc <= 8 columns (x, y node-major
+// [n][kp_for(kc)], padding columns of x zero) with M = A~^T (which = 0) or
+// M = A~ (which = 1).
+int kp_for(int k);
+void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float decay, cudaStream_t s);
 
 enum Mode : int {
     MODE_ACC = 0,     // y written; r += y for alive columns when i >= s_iter
@@ -153,6 +167,13 @@ struct CpiArgs {
     int32_t *iters_out = nullptr;   // device int32[k] or nullptr
     const int32_t *seed_outdeg = nullptr;   // host int32[k]: out-degrees of the seeds (enables the push path)
 };
+
+// adjoint.cu
+void set_edge_weights(tpa_graph *g, const float *w_any, cudaStream_t s, bool drop_preprocessing = true);
+void weights_from_features(const float *feat, const float *theta, int d, int64_t m, float *w, cudaStream_t s);
+void theta_grad(const float *feat, const float *w, const float *gw, int d, int64_t m, double *out, cudaStream_t s);
+double loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const int32_t *neg, int ntrip, double c,
+                 int S, int T, int K, float *grad_w, cudaStream_t s);
 
 // Out-degrees of k device-resident seeds, copied to the host.
 std::vector<int32_t> seed_outdegrees(tpa_graph *g, const int32_t *d_seeds, int k, cudaStream_t s);

@@ -48,6 +48,10 @@ def library():
         "tpa_save_preprocessed": (i32, [P, ctypes.c_char_p]),
         "tpa_load_preprocessed": (i32, [P, ctypes.c_char_p, P]),
         "tpa_cpi_step_noalloc": (i32, [i64, i64, P, P, P, f64, P, P, P, P, P]),
+        "tpa_set_edge_weights": (i32, [P, P, P]),
+        "tpa_edge_weights": (i32, [P, P, i32, i64, P, P]),
+        "tpa_loss_grad": (i32, [P, P, P, P, i32, f64, i32, i32, i32, ctypes.POINTER(f64), P, P]),
+        "tpa_theta_grad": (i32, [P, P, P, i32, i64, P, P]),
         "tpa_launch_count": (ctypes.c_uint64, []),
         "tpa_variant_count": (i32, []),
         "tpa_variant_info": (i32, [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -276,3 +280,44 @@ def cpi_step_noalloc(n: int, m: int, row_ptr, col, val, c: float, x, y, r=None, 
 def set_push(enable: bool) -> None:
     """Push the sparse first family iterates of a query (default) or pull every iteration."""
     _check(library().tpa_set_push(1 if enable else 0))
+
+
+# ------------------------------------------------------------- gradients ---
+def set_edge_weights(g: Graph, w) -> None:
+    """tpa_set_edge_weights: A~ = w / rowsum (w in CSR(A~) edge order)."""
+    w = w.contiguous() if not isinstance(w, np.ndarray) else np.ascontiguousarray(w, dtype=np.float32)
+    _check(library().tpa_set_edge_weights(g.handle, _ptr(w), _stream()))
+
+
+def edge_weights(feat, theta):
+    """tpa_edge_weights: w_e = exp(theta . f_e) for CUDA tensors feat [m, d] and theta [d]."""
+    torch = _torch()
+    feat = feat.contiguous().to(torch.float32)
+    theta = theta.contiguous().to(torch.float32)
+    m, d = feat.shape
+    w = torch.empty(m, dtype=torch.float32, device=feat.device)
+    _check(library().tpa_edge_weights(_ptr(feat), _ptr(theta), int(d), int(m), _ptr(w), _stream()))
+    return w
+
+
+def loss_grad(g: Graph, seeds, pos, neg, c: float = 0.15, S: int = 5, T: int = 10, K: int = 100):
+    """tpa_loss_grad: (loss, dL/dw as a CUDA float32 tensor in CSR(A~) order)."""
+    torch = _torch()
+    s, p, q = _as_i32(seeds), _as_i32(pos), _as_i32(neg)
+    n, m = graph_info(g)
+    gw = torch.empty(max(m, 1), dtype=torch.float32, device="cuda")
+    loss = ctypes.c_double()
+    _check(library().tpa_loss_grad(g.handle, _ptr(s), _ptr(p), _ptr(q), int(len(s)), float(c), int(S), int(T),
+                                   int(K), ctypes.byref(loss), _ptr(gw), _stream()))
+    return loss.value, gw[:m]
+
+
+def theta_grad(feat, w, grad_w):
+    """tpa_theta_grad: dL/dtheta (CUDA float64 tensor [d])."""
+    torch = _torch()
+    feat = feat.contiguous().to(torch.float32)
+    m, d = feat.shape
+    out = torch.empty(d, dtype=torch.float64, device=feat.device)
+    _check(library().tpa_theta_grad(_ptr(feat), _ptr(w.contiguous()), _ptr(grad_w.contiguous()), int(d), int(m),
+                                    _ptr(out), _stream()))
+    return out
