@@ -192,15 +192,27 @@ int tpa_variant_count(void);
  * CTA.  TPA_EINVAL for an index out of range. */
 tpa_status tpa_variant_info(int idx, int *kp, int *lanes, int *cols_per_lane, int *items, int *threads);
 
+/* Static name of variant idx (kernel family and template shape, e.g.
+ * "pipe<2,4,16,8,4>"); NULL for an index out of range.  Owned by the
+ * library, valid for the life of the process. */
+const char *tpa_variant_name(int idx);
+
 /* Use variant idx for padded width kp (a power of two <= 256); idx = -1
  * restores the default.  TPA_EINVAL if the variant has another width. */
 tpa_status tpa_set_variant(int kp, int idx);
 
-/* Seeds per CPI chunk when tpa_query or tpa_cpi get k seeds: chunks of
- * `width` columns run one after another (a power of two <= 256; default 256).
- * A narrow chunk keeps its iterates X[n][width] in L2. */
+/* Seeds per chunk when tpa_query gets k seeds: chunks of `width` columns run
+ * one after another (a power of two <= 256; 0 restores the default, 8).  In a
+ * chunk of at most 8 light seeds x1 and x2 are pushed; a narrow chunk keeps its
+ * iterates X[n][width] near L2 size.  TPA_EINVAL for another value.  The
+ * getter returns the width in effect. */
 tpa_status tpa_set_batch_width(int width);
 int tpa_get_batch_width(void);
+
+/* The same for tpa_cpi and the many-iteration runs behind it (default 128:
+ * every streamed nonzero serves more seeds). */
+tpa_status tpa_set_cpi_batch_width(int width);
+int tpa_get_cpi_batch_width(void);
 
 /* Direction choice in tpa_query (default on): for chunks of up to 8 seeds,
  * each with at most 256 out-edges, and S >= 4, the sparse iterates x1 and x2

@@ -33,6 +33,8 @@ from .tpa import (  # noqa: F401
     query,
     save_preprocessed,
     set_batch_width,
+    set_cpi_batch_width,
+    get_cpi_batch_width,
     set_push,
     get_batch_width,
     set_variant,

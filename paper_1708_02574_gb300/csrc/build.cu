@@ -420,12 +420,15 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
 
     // 4. allocate the graph arrays
     const size_t mb = (size_t)std::max<int64_t>(m, 1);
+    const size_t mp = (size_t)(m + CSR_PAD);
     g->rp_t.ensure((size_t)(n + 1) * sizeof(int64_t), s);
-    g->col_t.ensure(mb * sizeof(int32_t), s);
-    g->val_t.ensure(mb * sizeof(float), s);
+    g->col_t.ensure(mp * sizeof(int32_t), s);
+    g->val_t.ensure(mp * sizeof(float), s);
     g->rp_a.ensure((size_t)(n + 1) * sizeof(int64_t), s);
-    g->col_a.ensure(mb * sizeof(int32_t), s);
-    g->val_a.ensure(mb * sizeof(float), s);
+    g->col_a.ensure(mp * sizeof(int32_t), s);
+    g->val_a.ensure(mp * sizeof(float), s);
+    for (DevBuf *b : {&g->col_t, &g->val_t, &g->col_a, &g->val_a})
+        TPA_CUDA(cudaMemsetAsync(static_cast<char *>(b->p) + (size_t)m * 4, 0, (size_t)CSR_PAD * 4, s));
     g->outdeg.ensure((size_t)n * sizeof(int32_t), s);
     cnt.ensure((size_t)n * sizeof(int32_t), s);
 

@@ -48,7 +48,7 @@ struct CtlView {
     Ctl *hdr;
     int32_t *alive;   // column still running (its iterate is accumulated)
     int32_t *iters;   // last iteration computed per column
-    int32_t *own;     // push path: x2 belongs to r (the column passed the test after x1)
+    int32_t *own;     // reserved
     int32_t *pad;
     double *norm;     // last ||x_i||_1 per column
     double *norm1;    // push path: ||x1||_1 per column
@@ -101,10 +101,6 @@ struct Params {
     float *tl1;      // [tiles][KP] per-tile L1 partials (FP32; FP64 only across blocks)
     double *part;    // [fix blocks][KP]
     void *ctl;
-    // push path: the first pulled iteration also adds its input x2 to r for
-    // the columns flagged in own
-    int own_add;
-    const int32_t *own;
 };
 
 // ------------------------------------------------------------- helpers ---
@@ -208,28 +204,16 @@ __device__ __forceinline__ void epilogue(const Params &p, int64_t row, int col0,
         if (p.accumulate) {
             if (p.ldr == KP && V > 1) {
                 // whole padded row contiguous: vector read-modify-write
-                float rv[V], xo[V];
+                float rv[V];
                 ld_row_rw<V>(p.r + row * KP + col0, rv);
-                if (p.own_add) ld_row_rw<V>(p.x + row * KP + col0, xo);
 #pragma unroll
-                for (int j = 0; j < V; ++j) {
-                    if (col0 + j < p.k) {
-                        if (p.own_add && p.own[col0 + j]) rv[j] += xo[j];
-                        if (alive[j]) rv[j] += yv[j];
-                    }
-                }
+                for (int j = 0; j < V; ++j)
+                    if (col0 + j < p.k && alive[j]) rv[j] += yv[j];
                 st_row<V>(p.r + row * KP + col0, rv);
             } else {
 #pragma unroll
-                for (int j = 0; j < V; ++j) {
-                    const bool own = p.own_add && p.own[col0 + j];
-                    if (col0 + j < p.k && (alive[j] || own)) {
-                        float rv = p.r[row * p.ldr + col0 + j];
-                        if (own) rv += p.x[row * KP + col0 + j];
-                        if (alive[j]) rv += yv[j];
-                        p.r[row * p.ldr + col0 + j] = rv;
-                    }
-                }
+                for (int j = 0; j < V; ++j)
+                    if (col0 + j < p.k && alive[j]) p.r[row * p.ldr + col0 + j] += yv[j];
             }
         }
     } else {
@@ -238,7 +222,6 @@ __device__ __forceinline__ void epilogue(const Params &p, int64_t row, int col0,
         for (int j = 0; j < V; ++j)
             if (col0 + j < p.k) {
                 float fam = p.r[row * p.ldr + col0 + j];
-                if (p.own_add && p.own[col0 + j]) fam += p.x[row * KP + col0 + j];
                 if (alive[j]) fam += yv[j];
                 p.out[row * p.ldo + col0 + j] = fmaf(p.one_plus_alpha, fam, rs);
             }
@@ -828,6 +811,315 @@ __global__ void __launch_bounds__(WARPS * 32) spmvg_tile_k(Params p)
     }
 }
 
+// ------------------------------------------ pipelined group-walker kernel ---
+// The group walker above, reorganised so that no walker waits on memory other
+// than its own prefetched gathers:
+//  - the CSR slice of a warp's next tile (row ends, columns, values) is copied
+//    by cp.async into the second of two shared-memory buffers while the
+//    walkers work on the current tile, and the bounds of the tile after that
+//    are loaded into registers, so a tile's own loads are never on its
+//    critical path;
+//  - columns and values are staged with 16-byte copies (4-byte copies cost
+//    as many L1 wavefronts as the gathers themselves);
+//  - the epilogue reads nothing: y is stored and r gets y by a vector atomic
+//    add.  Each element of r receives exactly one add per launch, so the sum
+//    equals the read-modify-write and is deterministic.  In the final family
+//    iteration a preceding pass has set out = (1+alpha) r + r_str and the
+//    walkers add (1+alpha) y to it.
+// The first row of a tile, when it started in an earlier tile, is still
+// finished by the fixup.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// r[0..V) += v[0..V) with vector atomics (the result is not read back).
+template <int V>
+__device__ __forceinline__ void red_row(float *p, const float (&v)[V])
+{
+    if constexpr (V == 1) {
+        atomicAdd(p, v[0]);
+    } else if constexpr (V == 2) {
+        atomicAdd(reinterpret_cast<float2 *>(p), make_float2(v[0], v[1]));
+    } else if constexpr (V == 4) {
+        atomicAdd(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+    } else {
+        static_assert(V == 8, "V");
+        atomicAdd(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+        atomicAdd(reinterpret_cast<float4 *>(p) + 1, make_float4(v[4], v[5], v[6], v[7]));
+    }
+}
+
+// Epilogue of Algorithm 1 for one finished row without loads (see above).
+template <int KP, int V>
+__device__ __forceinline__ void epilogue_red(const Params &p, int64_t row, int col0, const float (&s)[V],
+                                             const int (&alive)[V], float (&l1)[V])
+{
+    float yv[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) yv[j] = p.decay * s[j];
+    if (p.mode == MODE_ACC) {
+        st_row<V>(p.y + row * KP + col0, yv);
+        if (p.accumulate) {
+            if (p.ldr == KP) {
+                float add[V];
+#pragma unroll
+                for (int j = 0; j < V; ++j) add[j] = (col0 + j < p.k && alive[j]) ? yv[j] : 0.0f;
+                red_row<V>(p.r + row * KP + col0, add);
+            } else {
+#pragma unroll
+                for (int j = 0; j < V; ++j)
+                    if (col0 + j < p.k && alive[j]) atomicAdd(p.r + row * p.ldr + col0 + j, yv[j]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+            if (col0 + j < p.k && alive[j]) atomicAdd(p.out + row * p.ldo + col0 + j, p.one_plus_alpha * yv[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) l1[j] += alive[j] ? fabsf(yv[j]) : 0.0f;
+}
+
+template <int G, int V, int ITEMS>
+struct __align__(16) PipeTile {
+    static constexpr int NW = 32 / G;
+    static constexpr int L = NW * ITEMS;
+    int64_t rp[L + 2];   // row_ptr[x0+1 .. x1], then a sentinel y0 + INT_MAX
+    // columns and values of nonzeros y0a .. y0a + 4 * chunks, y0a = y0 rounded
+    // down to a multiple of 4 (16-byte copies; the CSR arrays are padded)
+    int32_t col[L + 8];
+    float val[L + 8];
+};
+
+struct TileMeta {
+    int64_t y0, y1;
+    int32_t x0, x1;
+    int defer;           // the tile's first row started in an earlier tile
+};
+
+__device__ __forceinline__ TileMeta tile_meta(const Params &p, int64_t t)
+{
+    TileMeta m;
+    if (t < p.tiles) {
+        m.x0 = __ldg(p.tile_x + t);
+        m.x1 = __ldg(p.tile_x + t + 1);
+        m.y0 = __ldg(p.tile_y + t);
+        m.y1 = __ldg(p.tile_y + t + 1);
+        m.defer = __ldg(p.head_row + t) >= 0;
+    } else {
+        m.x0 = m.x1 = 0;
+        m.y0 = m.y1 = 0;
+        m.defer = 0;
+    }
+    return m;
+}
+
+// 16-byte global -> shared copy that bypasses L1 (the CSR is streamed once).
+__device__ __forceinline__ void cp_async16_cg(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+
+// Issue the cp.async copies of one tile's CSR slice (the caller commits).
+// Columns and values go in 16-byte chunks from y0 rounded down to a multiple
+// of 4 up to y1 rounded up: at most 3 elements past m, inside the CSR padding.
+__device__ __forceinline__ void stage_tile(const Params &p, const TileMeta &m, int64_t *rp_s, int32_t *col_s,
+                                           float *val_s, int lane)
+{
+    const int nrows = m.x1 - m.x0;
+    for (int i = lane; i < nrows; i += 32) cp_async<8>(rp_s + i, p.rp + m.x0 + i + 1);
+    if (lane == 0) rp_s[nrows] = m.y0 + 0x7fffffff;
+    const int64_t y0a = m.y0 & ~(int64_t)3;
+    const int chunks = (int)((m.y1 - y0a + 3) >> 2);
+    for (int i = lane; i < chunks; i += 32) {
+        cp_async16_cg(col_s + 4 * i, p.col + y0a + 4 * i);
+        cp_async16_cg(val_s + 4 * i, p.val + y0a + 4 * i);
+    }
+}
+
+template <int G, int V, int ITEMS, int PF>
+__device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, int64_t t, const int64_t *rp_s,
+                                          const int32_t *col_s, const float *val_s, int lane, const int (&alive)[V])
+{
+    constexpr int NW = 32 / G, KP = G * V;
+    const int w = lane / G, col0 = (lane % G) * V;
+    const int nrows = m.x1 - m.x0, nnz = (int)(m.y1 - m.y0);
+    const int off = (int)(m.y0 & 3);   // position of nonzero y0 in the staged chunks
+    // this walker's diagonal on the tile's merge path
+    const int d = min(w * ITEMS, nrows + nnz);
+    int lo = max(0, d - nnz), hi = min(d, nrows);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)(rp_s[mid] - m.y0) + mid + 1 <= d) lo = mid + 1; else hi = mid;
+    }
+    int xs = lo, ys = d - lo;
+    int row_end = (int)(rp_s[xs] - m.y0);
+    const int avail = nrows + nnz - d;
+    float acc[V], first_val[V], l1[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        acc[j] = 0.0f;
+        first_val[j] = 0.0f;
+        l1[j] = 0.0f;
+    }
+    int first_row = -1;
+#pragma unroll
+    for (int c0 = 0; c0 < ITEMS; c0 += PF) {
+        // decide PF steps and issue their gathers
+        float xv[PF][V];
+        float vv[PF];
+        unsigned nzmask = 0;
+        int xa = xs;
+#pragma unroll
+        for (int it = 0; it < PF; ++it) {
+            if (c0 + it < avail) {
+                if (ys < row_end) {
+                    vv[it] = val_s[off + ys];
+                    ld_row<V>(p.x + (int64_t)col_s[off + ys] * KP + col0, xv[it]);
+                    nzmask |= 1u << it;
+                    ++ys;
+                } else {
+                    ++xa;
+                    row_end = (int)(rp_s[xa] - m.y0);
+                }
+            }
+        }
+        // accumulate, emit finished rows
+#pragma unroll
+        for (int it = 0; it < PF; ++it) {
+            if (c0 + it < avail) {
+                if (nzmask & (1u << it)) {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) acc[j] = fmaf(vv[it], xv[it][j], acc[j]);
+                } else {
+                    if (first_row < 0) {
+                        first_row = xs;
+#pragma unroll
+                        for (int j = 0; j < V; ++j) first_val[j] = acc[j];
+                    } else {
+                        epilogue_red<KP, V>(p, (int64_t)(m.x0 + xs), col0, acc, alive, l1);
+                    }
+#pragma unroll
+                    for (int j = 0; j < V; ++j) acc[j] = 0.0f;
+                    ++xs;
+                }
+            }
+        }
+    }
+
+    // segmented inclusive scan of the walkers' trailing partials (key = row)
+    const int key = xs;
+#pragma unroll
+    for (int off = 1; off < NW; off <<= 1) {
+        const int k2 = __shfl_up_sync(0xffffffffu, key, off * G);
+        const bool take = w >= off && k2 == key;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const float v2 = __shfl_up_sync(0xffffffffu, acc[j], off * G);
+            if (take) acc[j] += v2;
+        }
+    }
+    float prev[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) prev[j] = __shfl_up_sync(0xffffffffu, acc[j], G);
+    if (first_row >= 0) {
+        float tot[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) tot[j] = first_val[j] + (w > 0 ? prev[j] : 0.0f);
+        if (first_row == 0 && m.defer) {
+            st_row<V>(p.head + t * KP + col0, tot);
+        } else {
+            epilogue_red<KP, V>(p, (int64_t)(m.x0 + first_row), col0, tot, alive, l1);
+        }
+    }
+    if (w == NW - 1) st_row<V>(p.carry + t * KP + col0, acc);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        float a = l1[j];
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        l1[j] = a;
+    }
+    if (lane < G) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) p.tl1[t * KP + col0 + j] = l1[j];
+    }
+}
+
+// MINB: resident blocks per SM requested from the register allocator.
+template <int G, int V, int ITEMS, int PF, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
+{
+    using PT = PipeTile<G, V, ITEMS>;
+    static_assert(ITEMS % PF == 0, "PF");
+    static_assert(PF <= 32, "PF");
+    static_assert(sizeof(PT) % 16 == 0 && offsetof(PT, col) % 16 == 0 && offsetof(PT, val) % 16 == 0, "layout");
+    static_assert(2 * sizeof(PT) * WARPS <= 48 * 1024, "static shared memory is limited to 48 KB per block");
+    __shared__ PT S_all[WARPS][2];
+    const CtlView cv = ctl_view(p.ctl);
+    if (*(volatile int32_t *)&cv.hdr->done) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col0 = (lane % G) * V;
+    int alive[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) alive[j] = cv.alive[col0 + j];
+    const int64_t stride = (int64_t)gridDim.x * WARPS;
+    int64_t t = (int64_t)blockIdx.x * WARPS + warp;
+    TileMeta cur = tile_meta(p, t);
+    if (t < p.tiles) stage_tile(p, cur, S_all[warp][0].rp, S_all[warp][0].col, S_all[warp][0].val, lane);
+    cp_async_commit();
+    TileMeta nxt = tile_meta(p, t + stride);
+    int b = 0;
+    for (; t < p.tiles; t += stride) {
+        if (t + stride < p.tiles)
+            stage_tile(p, nxt, S_all[warp][b ^ 1].rp, S_all[warp][b ^ 1].col, S_all[warp][b ^ 1].val, lane);
+        cp_async_commit();
+        const TileMeta after = tile_meta(p, t + 2 * stride);
+        cp_async_wait_group<1>();   // this tile's copies have landed
+        __syncwarp();
+        walk_tile<G, V, ITEMS, PF>(p, cur, t, S_all[warp][b].rp, S_all[warp][b].col, S_all[warp][b].val, lane,
+                                   alive);
+        __syncwarp();               // the buffer is refilled two tiles later
+        cur = nxt;
+        nxt = after;
+        b ^= 1;
+    }
+    cp_async_wait_group<0>();
+}
+
+// Sum over b in [0, nb) of part[b * KP + c] for every column c < KP, by the
+// 256 threads of one block in a fixed order (so the result is deterministic):
+// group grp of the 256 / KP groups adds b = grp, grp + NG, ... in increasing b
+// (loads issued eight at a time), then thread c adds the group sums in group
+// order.  The result for column c is left in s_fin[c] (s_fin holds 256).
+template <int KP>
+__device__ __forceinline__ void block_sum_partials(const double *part, unsigned nb, double *s_fin)
+{
+    static_assert(KP >= 1 && KP <= 256 && 256 % KP == 0, "KP");
+    constexpr unsigned NG = 256 / KP;
+    const int c = threadIdx.x % KP, grp = threadIdx.x / KP;
+    double a = 0.0;
+    unsigned b = grp;
+    for (; b + 7u * NG < nb; b += 8u * NG) {
+        double v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = __ldcg(&part[(int64_t)(b + i * NG) * KP + c]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a += v[i];
+    }
+    for (; b < nb; b += NG) a += __ldcg(&part[(int64_t)b * KP + c]);
+    __syncthreads();
+    s_fin[grp * KP + c] = a;
+    __syncthreads();
+    if (threadIdx.x < KP) {
+        double t = 0.0;
+        for (unsigned g = 0; g < NG; ++g) t += s_fin[g * KP + threadIdx.x];
+        s_fin[threadIdx.x] = t;   // only this thread reads or writes column c's group-0 slot
+    }
+    __syncthreads();
+}
+
 // --------------------------------------------------------------- fixup ---
 constexpr int FIX_WARPS = 8;
 
@@ -842,9 +1134,9 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) fixup_k(Params p)
     constexpr int CW = KP < 32 ? KP : 32;    // columns per lane group
     constexpr int SUB = 32 / CW;             // lanes sharing one column
     constexpr int NCH = KP / CW;             // column chunks per lane
-    constexpr int NG = (FIX_WARPS * 32) / KP > 0 ? (FIX_WARPS * 32) / KP : 1;   // groups in the final reduction
+    static_assert(FIX_WARPS * 32 == 256, "block_sum_partials runs on 256 threads");
     __shared__ float s_l1[FIX_WARPS][KP];
-    __shared__ double s_red[NG * KP];
+    __shared__ double s_red[256];
     __shared__ int s_last;
     const CtlView cv = ctl_view(p.ctl);
     if (*(volatile int32_t *)&cv.hdr->done) return;
@@ -903,16 +1195,9 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) fixup_k(Params p)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (threadIdx.x < NG * KP) {
-        const int c = threadIdx.x % KP, grp = threadIdx.x / KP;
-        double sum = 0.0;
-        for (unsigned b = grp; b < gridDim.x; b += NG) sum += __ldcg(&p.part[(int64_t)b * KP + c]);
-        s_red[grp * KP + c] = sum;
-    }
-    __syncthreads();
+    block_sum_partials<KP>(p.part, gridDim.x, s_red);
     for (int c = threadIdx.x; c < KP; c += FIX_WARPS * 32) {
-        double sum = 0.0;
-        for (int grp = 0; grp < NG; ++grp) sum += s_red[grp * KP + c];
+        const double sum = s_red[c];
         if (c < p.k && cv.alive[c]) {
             cv.norm[c] = sum;
             cv.iters[c] = p.iter;
@@ -941,9 +1226,8 @@ constexpr int FIX_SHORT = 32;
 template <int V>
 __global__ void __launch_bounds__(256) fixup_small_k(Params p)
 {
-    constexpr int NG = 256 / V;
     __shared__ float s_red[8][V];
-    __shared__ double s_fin[NG * V];
+    __shared__ double s_fin[256];
     __shared__ int s_last;
     const CtlView cv = ctl_view(p.ctl);
     if (*(volatile int32_t *)&cv.hdr->done) return;
@@ -1019,17 +1303,10 @@ __global__ void __launch_bounds__(256) fixup_small_k(Params p)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    {
-        const int c = threadIdx.x % V, grp = threadIdx.x / V;
-        double a = 0.0;
-        for (unsigned b = grp; b < gridDim.x; b += NG) a += __ldcg(&p.part[(int64_t)b * V + c]);
-        s_fin[grp * V + c] = a;
-    }
-    __syncthreads();
+    block_sum_partials<V>(p.part, gridDim.x, s_fin);
     if (threadIdx.x < V) {
         const int c = threadIdx.x;
-        double a = 0.0;
-        for (int grp = 0; grp < NG; ++grp) a += s_fin[grp * V + c];
+        const double a = s_fin[c];
         if (c < p.k && cv.alive[c]) {
             cv.norm[c] = a;
             cv.iters[c] = p.iter;
@@ -1124,8 +1401,8 @@ __global__ void copy_iters_k(const void *ctl, int32_t *out, int k)
 // x2 is accumulated in 64-bit fixed point (scale 2^63; every term is
 // non-negative and the total mass is below 1), so the integer atomics make the
 // sum independent of their order: the result is deterministic and rounded to
-// FP32 once.  r starts as x0 + x1; x2 is added to r by the first pulled
-// iteration (Params::own_add).
+// FP32 once.  r starts as x0 + x1; the conversion adds x2 to r for the
+// columns that passed the break test after x1.
 constexpr float FX_SCALE_F = 9223372036854775808.0f;      // 2^63, exact in FP32
 constexpr float FX_INV_F = 1.0842021724855044e-19f;       // 2^-63, exact in FP32
 
@@ -1164,41 +1441,54 @@ __global__ void push_x2_k(const int64_t *rp_a, const int32_t *col_a, const float
 }
 
 // X = x2 in FP32 (padding columns zero); only rows marked in `touched` read U,
-// and U and the marks are cleared for the next chunk; ||x2||_1 per column; the
-// last block applies the break tests after x1 and x2.  A warp covers 32
-// consecutive rows, i.e. one mark word.
+// and U and the marks are cleared for the next chunk; x2 is added to r for the
+// columns that passed the test after x1; ||x2||_1 per column; the last block
+// applies the break tests after x1 and x2.  Grid-stride over rows, one row of
+// KP columns per thread (vector stores); a warp covers 32 consecutive rows,
+// i.e. one mark word, and skips its reduction when the word is empty.
 template <int KP>
-__global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, uint32_t *touched, float *X, int64_t n,
-                                                    int kc, float decay, double eps, double *part, void *ctl)
+__global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, uint32_t *touched, float *X, float *R,
+                                                    int64_t n, int kc, float decay, double eps, double *part,
+                                                    void *ctl)
 {
     __shared__ float s_red[8][KP];
     __shared__ double s_fin[256];
     __shared__ int s_last;
     const CtlView cv = ctl_view(ctl);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t v = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    bool own[KP];
+#pragma unroll
+    for (int j = 0; j < KP; ++j) own[j] = j < kc && cv.norm1[j] >= eps;
     float nrm[KP];
 #pragma unroll
     for (int j = 0; j < KP; ++j) nrm[j] = 0.0f;
-    const uint32_t word = v < n ? touched[v >> 5] : 0u;
-    if (v < n) {
-        const bool hit = (word >> (v & 31)) & 1u;
+    const int64_t step = (int64_t)gridDim.x * 256;
+    for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += step) {
+        const int64_t v = base + threadIdx.x;
+        const uint32_t word = v < n ? touched[v >> 5] : 0u;   // the same word in the whole warp
+        if (v < n) {
+            float x[KP];
 #pragma unroll
-        for (int j = 0; j < KP; ++j) {
-            float x = 0.0f;
-            if (hit && j < kc) {
-                const unsigned long long a = U[v * KP + j];
-                if (a) {
-                    U[v * KP + j] = 0ull;
-                    x = decay * (__ull2float_rn(a) * FX_INV_F);
+            for (int j = 0; j < KP; ++j) x[j] = 0.0f;
+            if ((word >> (v & 31)) & 1u) {
+#pragma unroll
+                for (int j = 0; j < KP; ++j) {
+                    if (j < kc) {
+                        const unsigned long long a = U[v * KP + j];
+                        if (a) {
+                            U[v * KP + j] = 0ull;
+                            x[j] = decay * (__ull2float_rn(a) * FX_INV_F);
+                            if (own[j]) R[v * KP + j] += x[j];
+                        }
+                    }
+                    nrm[j] += x[j];
                 }
             }
-            X[v * KP + j] = x;
-            nrm[j] = x;
+            st_row<KP>(X + v * KP, x);
         }
+        __syncwarp();
+        if (lane == 0 && v < n && word) touched[v >> 5] = 0u;
     }
-    __syncwarp();
-    if (lane == 0 && v < n && word) touched[v >> 5] = 0u;
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
         float a = nrm[j];
@@ -1219,29 +1509,20 @@ __global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, uint3
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    constexpr int NG = 256 / KP;
-    {
-        const int c = threadIdx.x % KP, grp = threadIdx.x / KP;
-        double a = 0.0;
-        for (unsigned b = grp; b < gridDim.x; b += NG) a += __ldcg(&part[(int64_t)b * KP + c]);
-        s_fin[grp * KP + c] = a;
-    }
-    __syncthreads();
+    block_sum_partials<KP>(part, gridDim.x, s_fin);
     if (threadIdx.x < KP) {
         const int c = threadIdx.x;
-        double a = 0.0;
-        for (int grp = 0; grp < NG; ++grp) a += s_fin[grp * KP + c];
+        const double a = s_fin[c];
         if (c < kc) {
             const bool a1 = cv.norm1[c] >= eps;          // Algorithm 1 breaks after x1 when ||x1|| < eps
             const bool a2 = a1 && a >= eps;              // ... or after x2
-            cv.own[c] = a1 ? 1 : 0;
             cv.alive[c] = a2 ? 1 : 0;
             cv.iters[c] = a1 ? 2 : 1;
             cv.norm[c] = a1 ? a : cv.norm1[c];
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) cv.hdr->ticket = 0;   // done stays 0: iteration 3 adds x2 to r
+    if (threadIdx.x == 0) cv.hdr->ticket = 0;   // done stays 0: iteration 3 is pulled
 }
 
 // ------------------------------------------------------------- planning ---
@@ -1371,6 +1652,19 @@ static void launch_spmvg(const Params &p, cudaStream_t s)
     spmvg_tile_k<G, V, ITEMS, PF, WARPS><<<(unsigned)grid, WARPS * 32, 0, s>>>(p);
 }
 
+template <int G, int V, int ITEMS, int PF, int WARPS, int MINB>
+static void launch_spmvp(const Params &p, cudaStream_t s)
+{
+    static int per_sm = 0;
+    if (!per_sm) {
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB>,
+                                                               WARPS * 32, 0));
+        per_sm = std::max(per_sm, 1);
+    }
+    const int64_t grid = std::min<int64_t>((p.tiles + WARPS - 1) / WARPS, (int64_t)per_sm * num_sms());
+    spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB><<<(unsigned)grid, WARPS * 32, 0, s>>>(p);
+}
+
 template <int KP>
 static void launch_fix(const Params &p, unsigned blocks, cudaStream_t s)
 {
@@ -1393,49 +1687,69 @@ struct Variant {
     KCfg cfg;
     void (*spmm)(const Params &, cudaStream_t);
     void (*fix)(const Params &, unsigned, cudaStream_t);
+    bool red;           // epilogue by atomic adds: the final iteration needs out preset
+    const char *name;
 };
 
-#define TPA_VARIANT(G, V, I, PF) {{G, V, I, PF, CTA}, launch_spmm<G, V, I, PF>, launch_fix<G * V>}
-#define TPA_VARIANTW(V, I, W) {{1, V, I, I, 32}, launch_spmvw<V, I, W>, launch_fix<V>}
-#define TPA_VARIANTG(G, V, I, PF) {{G, V, I, PF, 32}, launch_spmvg<G, V, I, PF, 8>, launch_fix<G * V>}
+#define TPA_VARIANT(G, V, I, PF) \
+    {{G, V, I, PF, CTA}, launch_spmm<G, V, I, PF>, launch_fix<G * V>, false, "cta<" #G "," #V "," #I "," #PF ">"}
+#define TPA_VARIANTW(V, I, W) \
+    {{1, V, I, I, 32}, launch_spmvw<V, I, W>, launch_fix<V>, false, "warp<" #V "," #I "," #W ">"}
+#define TPA_VARIANTG(G, V, I, PF) \
+    {{G, V, I, PF, 32}, launch_spmvg<G, V, I, PF, 8>, launch_fix<G * V>, false, "walker<" #G "," #V "," #I "," #PF ">"}
+#define TPA_VARIANTP(G, V, I, PF, W, MB)                                                  \
+    {{G, V, I, PF, 32}, launch_spmvp<G, V, I, PF, W, MB>, launch_fix<G * V>, true,        \
+     "pipe<" #G "," #V "," #I "," #PF "," #W "," #MB ">"}
+// The first variant of each padded width is its default (the fastest measured
+// on R-MAT scale 22 queries); the autotuner may pick any other.
 static const Variant kVariants[] = {
-    TPA_VARIANTW(1, 8, 8),
     TPA_VARIANTW(1, 6, 8),
+    TPA_VARIANTW(2, 6, 8),
+    TPA_VARIANTP(1, 4, 8, 8, 4, 1),
+    TPA_VARIANTP(2, 4, 8, 8, 8, 1),
+    TPA_VARIANT(4, 4, 16, 8),
+    TPA_VARIANT(8, 4, 16, 8),
+    TPA_VARIANT(16, 4, 16, 8),
+    TPA_VARIANT(32, 4, 32, 8),
+    TPA_VARIANT(32, 8, 32, 4),
+    TPA_VARIANTW(1, 8, 8),
     TPA_VARIANTW(1, 7, 8),
     TPA_VARIANTW(2, 8, 4),
-    TPA_VARIANTW(2, 6, 8),
     TPA_VARIANTW(4, 6, 4),
     TPA_VARIANTW(4, 8, 4),
     TPA_VARIANTW(4, 4, 8),
     TPA_VARIANTW(8, 4, 4),
     TPA_VARIANTW(8, 6, 2),
     TPA_VARIANTW(8, 2, 8),
-    TPA_VARIANTG(8, 1, 32, 16),
     TPA_VARIANTG(8, 1, 16, 16),
-    TPA_VARIANTG(4, 2, 32, 16),
     TPA_VARIANTG(2, 4, 16, 8),
-    TPA_VARIANTG(4, 1, 32, 16),
     TPA_VARIANTG(2, 2, 16, 16),
-    TPA_VARIANTG(16, 1, 32, 16),
-    TPA_VARIANTG(8, 2, 32, 16),
     TPA_VARIANTG(8, 4, 32, 8),
-    TPA_VARIANTG(32, 1, 32, 16),
     TPA_VARIANT(1, 1, 8, 8),
     TPA_VARIANT(1, 2, 8, 8),
     TPA_VARIANT(1, 4, 8, 8),
-    TPA_VARIANT(2, 2, 8, 8),
     TPA_VARIANT(2, 4, 16, 8),
     TPA_VARIANT(8, 1, 16, 16),
-    TPA_VARIANT(4, 4, 16, 8),
-    TPA_VARIANT(8, 4, 16, 8),
-    TPA_VARIANT(32, 1, 16, 16),
-    TPA_VARIANT(16, 4, 16, 8),
-    TPA_VARIANT(32, 4, 32, 8),
-    TPA_VARIANT(32, 8, 32, 4),
+    TPA_VARIANT(2, 2, 8, 8),
+    TPA_VARIANTP(1, 2, 8, 8, 4, 1),
+    TPA_VARIANTP(1, 4, 4, 4, 8, 1),
+    TPA_VARIANTP(1, 4, 8, 8, 4, 6),
+    TPA_VARIANTP(2, 2, 8, 8, 8, 1),
+    TPA_VARIANTP(2, 4, 16, 8, 4, 1),
+    TPA_VARIANTP(2, 4, 8, 8, 8, 3),
+    TPA_VARIANTP(2, 4, 8, 4, 8, 1),
+    TPA_VARIANTP(2, 4, 8, 4, 8, 3),
+    TPA_VARIANTP(2, 4, 4, 4, 8, 1),
+    TPA_VARIANTP(2, 4, 8, 8, 4, 1),
+    TPA_VARIANTP(4, 4, 8, 8, 8, 1),
+    TPA_VARIANTP(4, 4, 16, 8, 4, 1),
+    TPA_VARIANTP(4, 4, 8, 4, 8, 2),
+    TPA_VARIANTP(8, 4, 8, 8, 8, 1),
 };
 #undef TPA_VARIANT
 #undef TPA_VARIANTW
 #undef TPA_VARIANTG
+#undef TPA_VARIANTP
 
 // Padded width: the smallest power of two >= k (every power of two up to
 // KP_MAX has at least one kernel variant).
@@ -1451,20 +1765,26 @@ constexpr int NUM_VARIANTS = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 static int g_forced[KP_MAX + 1];
 static bool g_forced_init = false;
 // Seeds per CPI chunk in batched calls (a power of two <= KP_MAX).
-static int g_chunk = KP_MAX;
+// 0 selects the default: narrow chunks for queries (light seeds then take the
+// push path and X[n][8] stays near L2 size), wide chunks for Algorithm 1 runs
+// of many iterations (each streamed nonzero serves more seeds).
+static int g_chunk_query = 0;
+static int g_chunk_cpi = 0;
+constexpr int DEFAULT_CHUNK_QUERY = 8;
+constexpr int DEFAULT_CHUNK_CPI = 128;
 // Push path for the first two family iterations of a query (on by default).
 static bool g_push = true;
 constexpr int PUSH_MAX_OUTDEG = 256;   // seeds with more out-edges keep the pull path
 constexpr int PUSH_BLOCKS = 16;        // blocks per column in push_x2_k
 
-static void launch_convert(int KP, unsigned blocks, unsigned long long *U, uint32_t *touched, float *X, int64_t n,
-                           int kc, float decay, double eps, double *part, void *ctl, cudaStream_t s)
+static void launch_convert(int KP, unsigned blocks, unsigned long long *U, uint32_t *touched, float *X, float *R,
+                           int64_t n, int kc, float decay, double eps, double *part, void *ctl, cudaStream_t s)
 {
     switch (KP) {
-    case 1: convert_x2_k<1><<<blocks, 256, 0, s>>>(U, touched, X, n, kc, decay, eps, part, ctl); break;
-    case 2: convert_x2_k<2><<<blocks, 256, 0, s>>>(U, touched, X, n, kc, decay, eps, part, ctl); break;
-    case 4: convert_x2_k<4><<<blocks, 256, 0, s>>>(U, touched, X, n, kc, decay, eps, part, ctl); break;
-    default: convert_x2_k<8><<<blocks, 256, 0, s>>>(U, touched, X, n, kc, decay, eps, part, ctl); break;
+    case 1: convert_x2_k<1><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl); break;
+    case 2: convert_x2_k<2><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl); break;
+    case 4: convert_x2_k<4><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl); break;
+    default: convert_x2_k<8><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl); break;
     }
 }
 
@@ -1546,7 +1866,7 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     bool push = g_push && a.tpa_final && a.seeds && a.seed_outdeg && last >= 3 && KP <= 8 && a.r_internal;
     for (int j = 0; push && j < kc; ++j) push = a.seed_outdeg[k0 + j] <= PUSH_MAX_OUTDEG;
     if (push) {
-        const unsigned cblocks = (unsigned)((n + 255) / 256);
+        const unsigned cblocks = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)8 * num_sms());
         W.fix.ensure((size_t)std::max<unsigned>(fix_blocks, cblocks) * KP * sizeof(double), s);
         if (!W.u.p || W.u.bytes < (size_t)n * KP * sizeof(unsigned long long) || !W.u_clean) {
             W.u.ensure((size_t)n * KP * sizeof(unsigned long long), s);
@@ -1561,9 +1881,8 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
                                                         g->val_a.as<float>(), a.seeds + k0, KP, c_val, decay_f,
                                                         W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), r,
                                                         W.ctl.p);
-        launch_convert(KP, cblocks, W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), W.x.as<float>(), n, kc,
-                       decay_f, a.eps,
-                       W.fix.as<double>(), W.ctl.p, s);
+        launch_convert(KP, cblocks, W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), W.x.as<float>(), r, n,
+                       kc, decay_f, a.eps, W.fix.as<double>(), W.ctl.p, s);
         note_launch("push", 2);
         TPA_CHECK_LAUNCH();
         W.u_clean = true;
@@ -1610,7 +1929,6 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     p.tl1 = W.tl1.as<float>();
     p.part = W.fix.as<double>();
     p.ctl = W.ctl.p;
-    p.own = ctl_view(W.ctl.p).own;
 
     float *cur = W.x.as<float>(), *nxt = W.y.as<float>();
     // Host-side early stop: every CHUNK iterations, read the device done flag
@@ -1633,9 +1951,14 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
             p.x = cur;
             p.y = nxt;
             p.iter = i;
-            p.own_add = (push && i == 3) ? 1 : 0;
             p.accumulate = i >= a.s_iter ? 1 : 0;
             p.mode = (a.tpa_final && i == last) ? MODE_FINAL : MODE_ACC;
+            if (p.mode == MODE_FINAL && var.red) {
+                // out = (1+alpha) r + r_str; the SpMM adds (1+alpha) y to it
+                finalize_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(r, ldr, a.r_str, p.one_plus_alpha, p.out, p.ldo, n,
+                                                               kc);
+                note_launch("finalize");
+            }
             ProfMark pm = prof_begin(s);
             var.spmm(p, s);
             prof_end(pm, spmm_family(KP), spmm_bytes(n, g->m, KP, kc, p.mode, p.accumulate), s);
@@ -1841,7 +2164,6 @@ void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float
     p.tl1 = W.tl1.as<float>();
     p.part = W.fix.as<double>();
     p.ctl = W.ctl.p;
-    p.own = ctl_view(W.ctl.p).own;
     ProfMark pm = prof_begin(s);
     var.spmm(p, s);
     prof_end(pm, spmm_family(KP), spmm_bytes(g->n, g->m, KP, kc, MODE_ACC, 0), s);
@@ -1854,8 +2176,10 @@ void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float
 
 void run_cpi(tpa_graph *g, const CpiArgs &a, cudaStream_t s)
 {
-    for (int k0 = 0; k0 < a.k; k0 += g_chunk) {
-        const int kc = std::min(g_chunk, a.k - k0);
+    const int chunk = a.tpa_final ? (g_chunk_query ? g_chunk_query : DEFAULT_CHUNK_QUERY)
+                                  : (g_chunk_cpi ? g_chunk_cpi : DEFAULT_CHUNK_CPI);
+    for (int k0 = 0; k0 < a.k; k0 += chunk) {
+        const int kc = std::min(chunk, a.k - k0);
         run_cpi_chunk(g, a, k0, kc, s);
     }
 }
@@ -1883,6 +2207,12 @@ tpa_status tpa_variant_info(int idx, int *kp, int *lanes, int *cols_per_lane, in
     return TPA_OK;
 }
 
+const char *tpa_variant_name(int idx)
+{
+    if (idx < 0 || idx >= NUM_VARIANTS) return nullptr;
+    return kVariants[idx].name;
+}
+
 tpa_status tpa_set_variant(int kp, int idx)
 {
     if (kp < 1 || kp > KP_MAX || (kp & (kp - 1))) {
@@ -1901,17 +2231,31 @@ tpa_status tpa_set_variant(int kp, int idx)
     return TPA_OK;
 }
 
+static bool valid_width(int width) { return width == 0 || (width >= 1 && width <= KP_MAX && !(width & (width - 1))); }
+
 tpa_status tpa_set_batch_width(int width)
 {
-    if (width < 1 || width > KP_MAX || (width & (width - 1))) {
-        set_error("tpa_set_batch_width: %d is not a power of two in [1, %d]", width, KP_MAX);
+    if (!valid_width(width)) {
+        set_error("tpa_set_batch_width: %d is neither 0 nor a power of two in [1, %d]", width, KP_MAX);
         return TPA_EINVAL;
     }
-    g_chunk = width;
+    g_chunk_query = width;
     return TPA_OK;
 }
 
-int tpa_get_batch_width(void) { return g_chunk; }
+int tpa_get_batch_width(void) { return g_chunk_query ? g_chunk_query : DEFAULT_CHUNK_QUERY; }
+
+tpa_status tpa_set_cpi_batch_width(int width)
+{
+    if (!valid_width(width)) {
+        set_error("tpa_set_cpi_batch_width: %d is neither 0 nor a power of two in [1, %d]", width, KP_MAX);
+        return TPA_EINVAL;
+    }
+    g_chunk_cpi = width;
+    return TPA_OK;
+}
+
+int tpa_get_cpi_batch_width(void) { return g_chunk_cpi ? g_chunk_cpi : DEFAULT_CHUNK_CPI; }
 
 tpa_status tpa_set_push(int enable)
 {

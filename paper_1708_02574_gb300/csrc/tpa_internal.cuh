@@ -76,6 +76,11 @@ struct Plan {
 };
 
 // ---------------------------------------------------------------- graph ---
+// The column and value arrays of both CSRs hold CSR_PAD extra zero elements
+// after the m real ones, so kernels may stage a tile's nonzeros in 16-byte
+// chunks rounded outward.
+constexpr int64_t CSR_PAD = 4;
+
 struct Workspace {
     DevBuf x, y, r;         // iterates and accumulator
     DevBuf carry, head, tl1;   // per-tile carries, deferred heads, per-tile L1

@@ -56,9 +56,12 @@ def library():
         "tpa_variant_count": (i32, []),
         "tpa_variant_info": (i32, [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "tpa_variant_name": (ctypes.c_char_p, [i32]),
         "tpa_set_variant": (i32, [i32, i32]),
         "tpa_set_batch_width": (i32, [i32]),
         "tpa_get_batch_width": (i32, []),
+        "tpa_set_cpi_batch_width": (i32, [i32]),
+        "tpa_get_cpi_batch_width": (i32, []),
         "tpa_set_push": (i32, [i32]),
         "tpa_profile_reset": (i32, [i32]),
         "tpa_profile_read": (i32, [P, i32, ctypes.POINTER(i32)]),
@@ -246,14 +249,14 @@ def profile_read() -> dict:
 
 
 def variants() -> list[dict]:
-    """Compiled SpMV/SpMM variants: padded width, lanes per walker, columns per lane, steps, threads."""
+    """Compiled SpMV/SpMM variants: padded width, lanes per walker, columns per lane, steps, threads, name."""
     lib = library()
     out = []
     for i in range(lib.tpa_variant_count()):
         v = [ctypes.c_int() for _ in range(5)]
         _check(lib.tpa_variant_info(i, *[ctypes.byref(x) for x in v]))
         out.append(dict(index=i, kp=v[0].value, lanes=v[1].value, cols_per_lane=v[2].value, items=v[3].value,
-                        threads=v[4].value))
+                        threads=v[4].value, name=lib.tpa_variant_name(i).decode()))
     return out
 
 
@@ -267,6 +270,14 @@ def set_batch_width(width: int) -> None:
 
 def get_batch_width() -> int:
     return int(library().tpa_get_batch_width())
+
+
+def set_cpi_batch_width(width: int) -> None:
+    _check(library().tpa_set_cpi_batch_width(int(width)))
+
+
+def get_cpi_batch_width() -> int:
+    return int(library().tpa_get_cpi_batch_width())
 
 
 def cpi_step_noalloc(n: int, m: int, row_ptr, col, val, c: float, x, y, r=None, l1=None) -> None:

@@ -206,7 +206,7 @@ def narrow_batches():
     t = tpa()
     t.set_batch_width(8)
     yield
-    t.set_batch_width(256)
+    t.set_batch_width(0)
     t.set_push(True)
 
 
