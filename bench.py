@@ -183,17 +183,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, variant: str):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel source.
+def ncu_traffic(variant: str, scale: int):
+    """DRAM bytes (read + write) per launch of a kernel variant from a committed
+    ncu capture, if it was taken on the current kernel source and graph scale.
 
-    profiles/ncu_traffic.txt lines: kernel variant source_hash bytes_per_launch workload..."""
+    profiles/ncu_traffic.txt lines: variant source_hash scale bytes_per_launch note..."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
     cur = kernel_source_hash()
     for line in open(path):
         f = line.split()
-        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == variant and f[2] == cur:
+        if len(f) >= 4 and not line.startswith("#") and f[0] == variant and f[1] == cur and f[2] == str(scale):
             return float(f[3])
     return None
 
@@ -379,14 +380,18 @@ def main(argv=None):
 
     hbm, peak_kind = peaks()
 
+    names = {v["index"]: v["name"] for v in tpa.variants()}
+
     def roofline_of(fam):
         sp = stats.get(fam, {})
         if sp.get("total_ms", 0) <= 0:
             return None
         achieved = sp["alg_bytes"] / (sp["total_ms"] / 1000.0) / 1e9
         per_launch = sp["alg_bytes"] / max(1, sp["launches"])
+        variant = names.get(tpa.get_variant(int(fam[len("spmm_kp"):])), "?")
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": ncu_traffic(fam, "current"), "kernel": f"{fam}: merge-path SpMV/SpMM over CSR(A~^T)",
+                "traffic": ncu_traffic(variant, args.scale), "variant": variant,
+                "kernel": f"{fam}: merge-path SpMV/SpMM over CSR(A~^T), {variant}",
                 "launches": sp["launches"], "avg_launch_ms": sp["total_ms"] / max(1, sp["launches"]),
                 "alg_bytes_per_launch": per_launch, "peak_source": f"{peak_kind} hbm_gbs (copy), burst",
                 "kernel_share_of_step": sp["total_ms"] / (1000.0 * t_rank)}

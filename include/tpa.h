@@ -197,6 +197,10 @@ tpa_status tpa_variant_info(int idx, int *kp, int *lanes, int *cols_per_lane, in
  * library, valid for the life of the process. */
 const char *tpa_variant_name(int idx);
 
+/* Index of the variant in effect for padded width kp (the forced one, else
+ * the default); -1 if kp is not a power of two in [1, 256]. */
+int tpa_get_variant(int kp);
+
 /* Use variant idx for padded width kp (a power of two <= 256); idx = -1
  * restores the default.  TPA_EINVAL if the variant has another width. */
 tpa_status tpa_set_variant(int kp, int idx);

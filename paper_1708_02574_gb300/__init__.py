@@ -38,6 +38,7 @@ from .tpa import (  # noqa: F401
     set_push,
     get_batch_width,
     set_variant,
+    get_variant,
     variants,
 )
 from .autograd import TPALinkLoss  # noqa: F401,E402

@@ -8,14 +8,19 @@ Two knobs are tuned on the graph at hand:
   * the kernel variant per width (lanes per merge-path walker, columns per
     lane, path steps per lane), and the k = 1 variant of preprocessing.
 Every candidate is timed with CUDA events on the current stream after a
-warm-up call; the fastest is applied with tpa_set_variant/tpa_set_batch_width.
-Results differ between candidates only by FP32 rounding order.
+warm-up call; the fastest is applied with tpa_set_variant/tpa_set_batch_width,
+except that a library default within TIE of the fastest is kept (so the
+choice does not flip between runs on timing noise).  Results differ between
+candidates only by FP32 rounding order.
 """
 from __future__ import annotations
 
 import time
 
 from . import tpa
+
+TIE = 0.03   # relative margin within which a default wins
+
 
 
 def _time(fn, reps: int) -> float:
@@ -34,14 +39,17 @@ def _time(fn, reps: int) -> float:
 
 def tune_preprocess(g: tpa.Graph, c: float, T: int, eps: float, reps: int = 1) -> dict:
     """Pick the fastest k = 1 variant by timing tpa_preprocess."""
-    best = None
+    tpa.set_variant(1, -1)
+    default = tpa.get_variant(1)
+    times = {}
     for v in tpa.variants():
         if v["kp"] != 1:
             continue
         tpa.set_variant(1, v["index"])
-        t = _time(lambda: tpa.preprocess(g, c, T, eps), reps)
-        if best is None or t < best[1]:
-            best = (v["index"], t)
+        times[v["index"]] = _time(lambda: tpa.preprocess(g, c, T, eps), reps)
+    best = min(times.items(), key=lambda kv: kv[1])
+    if times[default] <= best[1] * (1.0 + TIE):
+        best = (default, times[default])
     tpa.set_variant(1, best[0])
     tpa.preprocess(g, c, T, eps)
     return {"variant": best[0], "seconds": best[1]}
@@ -53,6 +61,12 @@ def tune_query(g: tpa.Graph, seeds, S: int, widths=(1, 2, 4, 8, 16, 32, 64, 128,
     import torch
     n = g.n
     results = []
+    tpa.set_batch_width(0)
+    default_width = tpa.get_batch_width()
+    defaults = {}
+    for w in widths:
+        tpa.set_variant(w, -1)
+        defaults[w] = tpa.get_variant(w)
     for w in widths:
         q = min(len(seeds), max(max_seeds if w >= 8 else 64, 2 * w))
         sd = torch.as_tensor(seeds[:q], dtype=torch.int32, device="cuda")
@@ -66,6 +80,13 @@ def tune_query(g: tpa.Graph, seeds, S: int, widths=(1, 2, 4, 8, 16, 32, 64, 128,
             results.append({"width": w, "variant": v["index"], "seeds_per_s": q / t})
         tpa.set_variant(w, -1)
     best = max(results, key=lambda r: r["seeds_per_s"])
+    # prefer the default variant of the best width, then the default width's
+    # default variant, when within TIE of the fastest
+    for cand in ([r for r in results if r["width"] == best["width"] and r["variant"] == defaults[best["width"]]] +
+                 [r for r in results if r["width"] == default_width and r["variant"] == defaults[default_width]]):
+        if cand["seeds_per_s"] >= best["seeds_per_s"] / (1.0 + TIE):
+            best = cand
+            break
     tpa.set_batch_width(best["width"])
     tpa.set_variant(best["width"], best["variant"])
     return {"best": best, "all": results}

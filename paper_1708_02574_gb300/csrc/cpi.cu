@@ -1848,7 +1848,7 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     W.ctl.ensure(CTL_BYTES, s);
 
     ctl_init_k<<<1, 256, 0, s>>>(W.ctl.p, kc);
-    note_launch("init", 2);
+    note_launch("init");
     const float c_val = (float)a.c;
     const float pr_val = (float)(a.c * (1.0 / (double)n));
     float *r;
@@ -1889,6 +1889,7 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     } else {
         init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, a.seeds ? a.seeds + k0 : nullptr, kc,
                                                      c_val, pr_val, r, ldr, a.s_iter == 0 ? 1 : 0);
+        note_launch("init");
         TPA_CHECK_LAUNCH();
     }
     if (last == 0) {
@@ -2205,6 +2206,15 @@ tpa_status tpa_variant_info(int idx, int *kp, int *lanes, int *cols_per_lane, in
     if (items) *items = c.ITEMS;
     if (threads) *threads = c.NT;
     return TPA_OK;
+}
+
+int tpa_get_variant(int kp)
+{
+    if (kp < 1 || kp > KP_MAX || (kp & (kp - 1))) return -1;
+    if (g_forced_init && g_forced[kp] >= 0) return g_forced[kp];
+    for (int i = 0; i < NUM_VARIANTS; ++i)
+        if (kVariants[i].cfg.KP() == kp) return i;
+    return -1;
 }
 
 const char *tpa_variant_name(int idx)

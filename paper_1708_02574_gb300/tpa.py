@@ -57,6 +57,7 @@ def library():
         "tpa_variant_info": (i32, [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "tpa_variant_name": (ctypes.c_char_p, [i32]),
+        "tpa_get_variant": (i32, [i32]),
         "tpa_set_variant": (i32, [i32, i32]),
         "tpa_set_batch_width": (i32, [i32]),
         "tpa_get_batch_width": (i32, []),
@@ -258,6 +259,11 @@ def variants() -> list[dict]:
         out.append(dict(index=i, kp=v[0].value, lanes=v[1].value, cols_per_lane=v[2].value, items=v[3].value,
                         threads=v[4].value, name=lib.tpa_variant_name(i).decode()))
     return out
+
+
+def get_variant(kp: int) -> int:
+    """Index of the variant in effect for padded width kp (forced, else default)."""
+    return int(library().tpa_get_variant(int(kp)))
 
 
 def set_variant(kp: int, idx: int) -> None:
