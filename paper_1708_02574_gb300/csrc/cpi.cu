@@ -101,6 +101,9 @@ struct Params {
     float *tl1;      // [tiles][KP] per-tile L1 partials (FP32; FP64 only across blocks)
     double *part;    // [fix blocks][KP]
     void *ctl;
+    // number of [KP] rows of tl1 the SpMM wrote (0 = one per tile); the
+    // pipelined kernel writes one per warp of its grid
+    int64_t l1_slots;
 };
 
 // ------------------------------------------------------------- helpers ---
@@ -116,11 +119,11 @@ __device__ __forceinline__ void ld_row(const float *p, float (&o)[V])
         const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
         o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
     } else {
+        // one 256-bit read-only load (32-byte aligned: every caller's row is)
         static_assert(V == 8, "V");
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-        const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
-        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-        o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+        asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]), "=f"(o[7])
+            : "l"(p));
     }
 }
 
@@ -814,18 +817,20 @@ __global__ void __launch_bounds__(WARPS * 32) spmvg_tile_k(Params p)
 // ------------------------------------------ pipelined group-walker kernel ---
 // The group walker above, reorganised so that no walker waits on memory other
 // than its own prefetched gathers:
-//  - the CSR slice of a warp's next tile (row ends, columns, values) is copied
-//    by cp.async into the second of two shared-memory buffers while the
-//    walkers work on the current tile, and the bounds of the tile after that
-//    are loaded into registers, so a tile's own loads are never on its
-//    critical path;
-//  - columns and values are staged with 16-byte copies (4-byte copies cost
-//    as many L1 wavefronts as the gathers themselves);
-//  - the epilogue reads nothing: y is stored and r gets y by a vector atomic
-//    add.  Each element of r receives exactly one add per launch, so the sum
-//    equals the read-modify-write and is deterministic.  In the final family
-//    iteration a preceding pass has set out = (1+alpha) r + r_str and the
-//    walkers add (1+alpha) y to it.
+//  - a warp's next tile (row ends, columns, values) is staged into the second
+//    of two shared-memory buffers while the walkers work on the current tile;
+//    columns and values of the tile after that are already in registers and
+//    its bounds are loading, so a tile's own loads are never on its critical
+//    path (see stage_tile);
+//  - walkers park the sums of finished rows in shared memory; after the walk
+//    one coalesced pass over the tile's rows (consecutive rows on consecutive
+//    walkers) runs the epilogue.  In accumulate mode it reads nothing: y is
+//    stored and r gets y by a vector atomic add; each element of r receives
+//    exactly one add per launch, so the sum equals the read-modify-write and
+//    is deterministic.  The final family iteration reads r and r~_str for all
+//    the tile's rows at once and writes the TPA scores;
+//  - the L1 partial of the break test is accumulated per lane over all of a
+//    warp's tiles and reduced once per warp (one row of tl1 per warp).
 // The first row of a tile, when it started in an earlier tile, is still
 // finished by the fixup.
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
@@ -849,7 +854,8 @@ __device__ __forceinline__ void red_row(float *p, const float (&v)[V])
     }
 }
 
-// Epilogue of Algorithm 1 for one finished row without loads (see above).
+// Epilogue of Algorithm 1 for one finished row in accumulate mode without
+// loads: y stored, r += y by a vector atomic add.
 template <int KP, int V>
 __device__ __forceinline__ void epilogue_red(const Params &p, int64_t row, int col0, const float (&s)[V],
                                              const int (&alive)[V], float (&l1)[V])
@@ -871,10 +877,6 @@ __device__ __forceinline__ void epilogue_red(const Params &p, int64_t row, int c
                     if (col0 + j < p.k && alive[j]) atomicAdd(p.r + row * p.ldr + col0 + j, yv[j]);
             }
         }
-    } else {
-#pragma unroll
-        for (int j = 0; j < V; ++j)
-            if (col0 + j < p.k && alive[j]) atomicAdd(p.out + row * p.ldo + col0 + j, p.one_plus_alpha * yv[j]);
     }
 #pragma unroll
     for (int j = 0; j < V; ++j) l1[j] += alive[j] ? fabsf(yv[j]) : 0.0f;
@@ -884,12 +886,20 @@ template <int G, int V, int ITEMS>
 struct __align__(16) PipeTile {
     static constexpr int NW = 32 / G;
     static constexpr int L = NW * ITEMS;
+    static constexpr int CH = (L + 6) / 4 + 1;      // 4-nonzero chunks a tile's nonzeros can span
+    static constexpr int PCH = (2 * CH + 7) & ~7;   // 16-byte pair chunks, whole swizzle groups
     int64_t rp[L + 2];   // row_ptr[x0+1 .. x1], then a sentinel y0 + INT_MAX
-    // columns and values of nonzeros y0a .. y0a + 4 * chunks, y0a = y0 rounded
-    // down to a multiple of 4 (16-byte copies; the CSR arrays are padded)
-    int32_t col[L + 8];
-    float val[L + 8];
+    // (column, value bits) of nonzeros y0a .. y0a + 4 * chunks, y0a = y0
+    // rounded down to a multiple of 4; nonzero e of the slice is the pair at
+    // word pair_word(e): one 8-byte shared load per step
+    int32_t cv[4 * PCH];
 };
+
+// Slot of 16-byte chunk q: an XOR swizzle inside each group of 8 chunks (one
+// 128-byte bank row), so walkers a few chunks apart share banks less often.
+__device__ __forceinline__ int chunk_slot(int q) { return (q & ~7) | ((q ^ (q >> 3)) & 7); }
+// First word of the (column, value) pair of nonzero e (two pairs per chunk).
+__device__ __forceinline__ int pair_word(int e) { return 4 * chunk_slot(e >> 1) + 2 * (e & 1); }
 
 struct TileMeta {
     int64_t y0, y1;
@@ -921,26 +931,74 @@ __device__ __forceinline__ void cp_async16_cg(void *smem, const void *gmem)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
 }
 
-// Issue the cp.async copies of one tile's CSR slice (the caller commits).
-// Columns and values go in 16-byte chunks from y0 rounded down to a multiple
-// of 4 up to y1 rounded up: at most 3 elements past m, inside the CSR padding.
-__device__ __forceinline__ void stage_tile(const Params &p, const TileMeta &m, int64_t *rp_s, int32_t *col_s,
-                                           float *val_s, int lane)
+// A tile's CSR slice is staged in two parts.  The row ends (a few per tile)
+// go by 8-byte cp.async.  Columns and values (8 bytes per nonzero, the bulk)
+// are loaded with coalesced 16-byte loads into registers one tile ahead and
+// stored to shared memory just before that tile is walked: a cp.async costs an
+// L1 wavefront per 32-byte sector on each side, a coalesced load one per
+// 128-byte line.  Chunks beyond 32 * RC (at most a few per tile) go by cp.async.
+// Columns and values run from y0 rounded down to a multiple of 4 up to y1
+// rounded up: at most 3 elements past m, inside the CSR padding.
+__device__ __forceinline__ int tile_chunks(const TileMeta &m)
 {
+    return m.y1 > m.y0 ? (int)((m.y1 - (m.y0 & ~(int64_t)3) + 3) >> 2) : 0;
+}
+
+template <int RC>
+struct ChunkRegs {
+    int4 c[RC > 0 ? RC : 1];
+    float4 v[RC > 0 ? RC : 1];
+};
+
+template <int RC>
+__device__ __forceinline__ void load_chunks(const Params &p, const TileMeta &m, ChunkRegs<RC> &r, int lane)
+{
+    const int chunks = tile_chunks(m);
+    const int64_t y0a = m.y0 & ~(int64_t)3;
+#pragma unroll
+    for (int k = 0; k < RC; ++k) {
+        const int q = lane + 32 * k;
+        if (q < chunks) {
+            r.c[k] = __ldcs(reinterpret_cast<const int4 *>(p.col + y0a) + q);
+            r.v[k] = __ldcs(reinterpret_cast<const float4 *>(p.val + y0a) + q);
+        }
+    }
+}
+
+// Store the register chunks of tile m interleaved as (column, value) pairs,
+// and issue the cp.async copies of its row ends and of the elements of chunks
+// past 32 * RC (a few per tile at most; the caller commits).
+template <int RC>
+__device__ __forceinline__ void stage_tile(const Params &p, const TileMeta &m, const ChunkRegs<RC> &r,
+                                           int64_t *rp_s, int32_t *cv_s, int lane)
+{
+    const int chunks = tile_chunks(m);
+    const int64_t y0a = m.y0 & ~(int64_t)3;
+#pragma unroll
+    for (int k = 0; k < RC; ++k) {
+        const int q = lane + 32 * k;
+        if (q < chunks) {
+            const int4 c = r.c[k];
+            const float4 v = r.v[k];
+            *reinterpret_cast<int4 *>(cv_s + 4 * chunk_slot(2 * q)) =
+                make_int4(c.x, __float_as_int(v.x), c.y, __float_as_int(v.y));
+            *reinterpret_cast<int4 *>(cv_s + 4 * chunk_slot(2 * q + 1)) =
+                make_int4(c.z, __float_as_int(v.z), c.w, __float_as_int(v.w));
+        }
+    }
+    for (int e = 128 * RC + lane; e < 4 * chunks; e += 32) {
+        cp_async<4>(cv_s + pair_word(e), p.col + y0a + e);
+        cp_async<4>(cv_s + pair_word(e) + 1, p.val + y0a + e);
+    }
     const int nrows = m.x1 - m.x0;
     for (int i = lane; i < nrows; i += 32) cp_async<8>(rp_s + i, p.rp + m.x0 + i + 1);
     if (lane == 0) rp_s[nrows] = m.y0 + 0x7fffffff;
-    const int64_t y0a = m.y0 & ~(int64_t)3;
-    const int chunks = (int)((m.y1 - y0a + 3) >> 2);
-    for (int i = lane; i < chunks; i += 32) {
-        cp_async16_cg(col_s + 4 * i, p.col + y0a + 4 * i);
-        cp_async16_cg(val_s + 4 * i, p.val + y0a + 4 * i);
-    }
 }
 
 template <int G, int V, int ITEMS, int PF>
 __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, int64_t t, const int64_t *rp_s,
-                                          const int32_t *col_s, const float *val_s, int lane, const int (&alive)[V])
+                                          const int32_t *cv_s, float *rs_s, int lane, const int (&alive)[V],
+                                          float (&l1)[V])
 {
     constexpr int NW = 32 / G, KP = G * V;
     const int w = lane / G, col0 = (lane % G) * V;
@@ -956,12 +1014,11 @@ __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, in
     int xs = lo, ys = d - lo;
     int row_end = (int)(rp_s[xs] - m.y0);
     const int avail = nrows + nnz - d;
-    float acc[V], first_val[V], l1[V];
+    float acc[V], first_val[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) {
         acc[j] = 0.0f;
         first_val[j] = 0.0f;
-        l1[j] = 0.0f;
     }
     int first_row = -1;
 #pragma unroll
@@ -975,8 +1032,9 @@ __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, in
         for (int it = 0; it < PF; ++it) {
             if (c0 + it < avail) {
                 if (ys < row_end) {
-                    vv[it] = val_s[off + ys];
-                    ld_row<V>(p.x + (int64_t)col_s[off + ys] * KP + col0, xv[it]);
+                    const int2 e = *reinterpret_cast<const int2 *>(cv_s + pair_word(off + ys));
+                    vv[it] = __int_as_float(e.y);
+                    ld_row<V>(p.x + (int64_t)e.x * KP + col0, xv[it]);
                     nzmask |= 1u << it;
                     ++ys;
                 } else {
@@ -998,7 +1056,7 @@ __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, in
 #pragma unroll
                         for (int j = 0; j < V; ++j) first_val[j] = acc[j];
                     } else {
-                        epilogue_red<KP, V>(p, (int64_t)(m.x0 + xs), col0, acc, alive, l1);
+                        st_row<V>(rs_s + xs * KP + col0, acc);   // finished: epilogue after the walk
                     }
 #pragma unroll
                     for (int j = 0; j < V; ++j) acc[j] = 0.0f;
@@ -1027,13 +1085,89 @@ __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, in
         float tot[V];
 #pragma unroll
         for (int j = 0; j < V; ++j) tot[j] = first_val[j] + (w > 0 ? prev[j] : 0.0f);
-        if (first_row == 0 && m.defer) {
+        if (first_row == 0 && m.defer)
             st_row<V>(p.head + t * KP + col0, tot);
-        } else {
-            epilogue_red<KP, V>(p, (int64_t)(m.x0 + first_row), col0, tot, alive, l1);
-        }
+        else
+            st_row<V>(rs_s + first_row * KP + col0, tot);
     }
     if (w == NW - 1) st_row<V>(p.carry + t * KP + col0, acc);
+    __syncwarp();
+    // epilogue of the tile's finished rows, consecutive rows on consecutive
+    // walkers (coalesced): accumulate by atomics (no load), the final family
+    // iteration reads r and r~_str for all rows of the tile at once
+    for (int r = w; r < nrows; r += NW) {
+        if (r == 0 && m.defer) continue;   // finished by the fixup
+        float sv[V];
+        ld_row_smem<V>(rs_s + r * KP + col0, sv);
+        if (p.mode == MODE_ACC)
+            epilogue_red<KP, V>(p, (int64_t)(m.x0 + r), col0, sv, alive, l1);
+        else
+            epilogue<KP, V>(p, (int64_t)(m.x0 + r), col0, sv, alive, l1);
+    }
+}
+
+// Shared memory per warp: two tile buffers and the row sums of one tile.
+template <int G, int V, int ITEMS>
+struct PipeSmem {
+    using PT = PipeTile<G, V, ITEMS>;
+    static constexpr size_t RS = (size_t)PT::L * G * V * sizeof(float);
+    static constexpr size_t PER_WARP = 2 * sizeof(PT) + RS;
+};
+
+// MINB: resident blocks per SM requested from the register allocator.
+template <int G, int V, int ITEMS, int PF, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
+{
+    using PT = PipeTile<G, V, ITEMS>;
+    using SM = PipeSmem<G, V, ITEMS>;
+    static_assert(ITEMS % PF == 0, "PF");
+    static_assert(PF <= 32, "PF");
+    static_assert(sizeof(PT) % 16 == 0 && offsetof(PT, cv) % 16 == 0, "layout");
+    static_assert(SM::PER_WARP % 16 == 0, "warp slices must stay 16-byte aligned");
+    extern __shared__ __align__(16) unsigned char pipe_smem[];
+    const CtlView cv = ctl_view(p.ctl);
+    if (*(volatile int32_t *)&cv.hdr->done) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col0 = (lane % G) * V;
+    unsigned char *base = pipe_smem + (size_t)warp * SM::PER_WARP;
+    PT *buf = reinterpret_cast<PT *>(base);
+    float *rs_s = reinterpret_cast<float *>(base + 2 * sizeof(PT));
+    int alive[V];
+    float l1[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        alive[j] = cv.alive[col0 + j];
+        l1[j] = 0.0f;
+    }
+    constexpr int RC = PT::CH / 32;   // chunks per lane held in registers
+    const int64_t stride = (int64_t)gridDim.x * WARPS;
+    int64_t t = (int64_t)blockIdx.x * WARPS + warp;
+    TileMeta cur = tile_meta(p, t);
+    ChunkRegs<RC> rg;
+    if (t < p.tiles) {
+        load_chunks<RC>(p, cur, rg, lane);   // the first tile waits for its loads
+        stage_tile<RC>(p, cur, rg, buf[0].rp, buf[0].cv, lane);
+    }
+    cp_async_commit();
+    TileMeta nxt = tile_meta(p, t + stride);
+    load_chunks<RC>(p, nxt, rg, lane);
+    int b = 0;
+    for (; t < p.tiles; t += stride) {
+        if (t + stride < p.tiles) stage_tile<RC>(p, nxt, rg, buf[b ^ 1].rp, buf[b ^ 1].cv, lane);
+        cp_async_commit();
+        const TileMeta after = tile_meta(p, t + 2 * stride);
+        load_chunks<RC>(p, after, rg, lane);   // in flight during this walk
+        cp_async_wait_group<1>();              // this tile's copies have landed
+        __syncwarp();
+        walk_tile<G, V, ITEMS, PF>(p, cur, t, buf[b].rp, buf[b].cv, rs_s, lane, alive, l1);
+        __syncwarp();                          // buffers and row sums are rewritten next iteration
+        cur = nxt;
+        nxt = after;
+        b ^= 1;
+    }
+    cp_async_wait_group<0>();
+    // this warp's L1 partial over all its tiles (fixed order: deterministic
+    // for a given grid), one row of tl1 per warp of the grid
 #pragma unroll
     for (int j = 0; j < V; ++j) {
         float a = l1[j];
@@ -1042,50 +1176,10 @@ __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, in
         l1[j] = a;
     }
     if (lane < G) {
+        const int64_t slot = (int64_t)blockIdx.x * WARPS + warp;
 #pragma unroll
-        for (int j = 0; j < V; ++j) p.tl1[t * KP + col0 + j] = l1[j];
+        for (int j = 0; j < V; ++j) p.tl1[slot * (G * V) + col0 + j] = l1[j];
     }
-}
-
-// MINB: resident blocks per SM requested from the register allocator.
-template <int G, int V, int ITEMS, int PF, int WARPS, int MINB>
-__global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
-{
-    using PT = PipeTile<G, V, ITEMS>;
-    static_assert(ITEMS % PF == 0, "PF");
-    static_assert(PF <= 32, "PF");
-    static_assert(sizeof(PT) % 16 == 0 && offsetof(PT, col) % 16 == 0 && offsetof(PT, val) % 16 == 0, "layout");
-    static_assert(2 * sizeof(PT) * WARPS <= 48 * 1024, "static shared memory is limited to 48 KB per block");
-    __shared__ PT S_all[WARPS][2];
-    const CtlView cv = ctl_view(p.ctl);
-    if (*(volatile int32_t *)&cv.hdr->done) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int col0 = (lane % G) * V;
-    int alive[V];
-#pragma unroll
-    for (int j = 0; j < V; ++j) alive[j] = cv.alive[col0 + j];
-    const int64_t stride = (int64_t)gridDim.x * WARPS;
-    int64_t t = (int64_t)blockIdx.x * WARPS + warp;
-    TileMeta cur = tile_meta(p, t);
-    if (t < p.tiles) stage_tile(p, cur, S_all[warp][0].rp, S_all[warp][0].col, S_all[warp][0].val, lane);
-    cp_async_commit();
-    TileMeta nxt = tile_meta(p, t + stride);
-    int b = 0;
-    for (; t < p.tiles; t += stride) {
-        if (t + stride < p.tiles)
-            stage_tile(p, nxt, S_all[warp][b ^ 1].rp, S_all[warp][b ^ 1].col, S_all[warp][b ^ 1].val, lane);
-        cp_async_commit();
-        const TileMeta after = tile_meta(p, t + 2 * stride);
-        cp_async_wait_group<1>();   // this tile's copies have landed
-        __syncwarp();
-        walk_tile<G, V, ITEMS, PF>(p, cur, t, S_all[warp][b].rp, S_all[warp][b].col, S_all[warp][b].val, lane,
-                                   alive);
-        __syncwarp();               // the buffer is refilled two tiles later
-        cur = nxt;
-        nxt = after;
-        b ^= 1;
-    }
-    cp_async_wait_group<0>();
 }
 
 // Sum over b in [0, nb) of part[b * KP + c] for every column c < KP, by the
@@ -1153,7 +1247,7 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) fixup_k(Params p)
 #pragma unroll
         for (int i = 0; i < NCH; ++i) {
             const int c = i * CW + cl;
-            float l1 = sub == 0 ? p.tl1[t * KP + c] : 0.0f;
+            float l1 = (sub == 0 && t < (p.l1_slots ? p.l1_slots : p.tiles)) ? p.tl1[t * KP + c] : 0.0f;
             if (h >= 0) {
                 float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
                 int64_t u = first + sub;
@@ -1241,7 +1335,9 @@ __global__ void __launch_bounds__(256) fixup_small_k(Params p)
     const int64_t first = mine ? (int64_t)p.head_first[t] : 0;
     float l1[V];
 #pragma unroll
-    for (int q = 0; q < V; ++q) l1[q] = mine ? p.tl1[t * V + q] : 0.0f;
+    const bool has_l1 = mine && t < (p.l1_slots ? p.l1_slots : p.tiles);
+#pragma unroll
+    for (int q = 0; q < V; ++q) l1[q] = has_l1 ? p.tl1[t * V + q] : 0.0f;
     const bool longspan = h >= 0 && t - first > FIX_SHORT;
     if (h >= 0 && !longspan) {
         float sum[V];
@@ -1406,50 +1502,93 @@ __global__ void copy_iters_k(const void *ctl, int32_t *out, int k)
 constexpr float FX_SCALE_F = 9223372036854775808.0f;      // 2^63, exact in FP32
 constexpr float FX_INV_F = 1.0842021724855044e-19f;       // 2^-63, exact in FP32
 
-__global__ void push_x2_k(const int64_t *rp_a, const int32_t *col_a, const float *val_a, const int32_t *seeds,
-                          int KP, float c_f, float decay, unsigned long long *U, uint32_t *touched, float *R,
-                          void *ctl)
+// One block per (column j, slice): the block loads the seed's out-edges (at
+// most PUSH_THREADS, one per thread) with the out-degree of each neighbour,
+// takes an exclusive prefix sum of those degrees, and then treats the edges
+// of all neighbours as one flat range split over the column's blocks (a
+// binary search in the prefix finds each edge's neighbour), so the work of a
+// seed is spread evenly whatever its neighbours' degrees.  Block 0 also
+// writes x0 and x1 into r and ||x1||_1 (summed in out-edge order).
+constexpr int PUSH_THREADS = 256;
+
+__global__ void __launch_bounds__(PUSH_THREADS) push_x2_k(const int64_t *rp_a, const int32_t *col_a,
+                                                          const float *val_a, const int32_t *seeds, int KP, float c_f,
+                                                          float decay, unsigned long long *U, uint32_t *touched,
+                                                          float *R, void *ctl)
 {
+    __shared__ int64_t s_start[PUSH_THREADS];     // first out-edge of neighbour k
+    __shared__ int64_t s_pref[PUSH_THREADS + 1];  // exclusive prefix of the neighbours' out-degrees
+    __shared__ float s_x1[PUSH_THREADS];
+    __shared__ int64_t s_warp[PUSH_THREADS / 32];
     const CtlView cv = ctl_view(ctl);
-    const int j = blockIdx.y;
+    const int j = blockIdx.y, k = threadIdx.x, lane = k & 31, warp = k >> 5;
     const int32_t s = seeds[j];
-    const int64_t e0 = rp_a[s], e1 = rp_a[s + 1];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        R[(int64_t)s * KP + j] = c_f;                                   // x0
-        float nrm = 0.0f;
-        for (int64_t e = e0; e < e1; ++e) {
-            const float x1u = decay * (val_a[e] * c_f);                 // x1, as the pull computes it
-            R[(int64_t)col_a[e] * KP + j] = x1u;
-            nrm += x1u;
+    const int64_t e0 = rp_a[s];
+    const int deg_s = (int)(rp_a[s + 1] - e0);    // <= PUSH_THREADS (checked by the host)
+    int64_t dk = 0;
+    if (k < deg_s) {
+        const int32_t u = col_a[e0 + k];
+        const float x1u = decay * (val_a[e0 + k] * c_f);   // x1, as the pull computes it
+        const int64_t f0 = rp_a[u];
+        s_x1[k] = x1u;
+        s_start[k] = f0;
+        dk = rp_a[u + 1] - f0;
+        if (blockIdx.x == 0) R[(int64_t)u * KP + j] = x1u;
+    }
+    // exclusive prefix of dk over the block
+    int64_t v = dk;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < PUSH_THREADS / 32 ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < PUSH_THREADS / 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
         }
+        if (lane < PUSH_THREADS / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    s_pref[k + 1] = v + (warp > 0 ? s_warp[warp - 1] : 0);
+    if (k == 0) s_pref[0] = 0;
+    __syncthreads();
+    if (blockIdx.x == 0 && k == 0) {
+        R[(int64_t)s * KP + j] = c_f;                   // x0
+        float nrm = 0.0f;
+        for (int i = 0; i < deg_s; ++i) nrm += s_x1[i];
         cv.norm1[j] = (double)nrm;
     }
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = e0; e < e1; ++e) {
-        const int32_t u = col_a[e];
-        const float x1u = decay * (val_a[e] * c_f);
-        const int64_t f0 = rp_a[u], f1 = rp_a[u + 1];
-        for (int64_t f = f0 + gt; f < f1; f += gs) {
-            const float q = val_a[f] * x1u;
-            const int32_t v = col_a[f];
-            atomicAdd(&U[(int64_t)v * KP + j], __float2ull_rn(q * FX_SCALE_F));
-            const uint32_t bit = 1u << (v & 31);
-            if (!(touched[v >> 5] & bit)) atomicOr(&touched[v >> 5], bit);   // rows the conversion must read
+    const int64_t E = s_pref[deg_s];
+    for (int64_t f = (int64_t)blockIdx.x * PUSH_THREADS + k; f < E; f += (int64_t)gridDim.x * PUSH_THREADS) {
+        int lo = 0, hi = deg_s - 1;                     // the last neighbour whose range starts at or before f
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pref[mid] <= f) lo = mid; else hi = mid - 1;
         }
+        const int64_t edge = s_start[lo] + (f - s_pref[lo]);
+        const int32_t w = col_a[edge];
+        const float q = val_a[edge] * s_x1[lo];
+        atomicAdd(&U[(int64_t)w * KP + j], __float2ull_rn(q * FX_SCALE_F));
+        atomicOr(&touched[w >> 5], 1u << (w & 31));     // rows the conversion must read
     }
 }
 
-// X = x2 in FP32 (padding columns zero); only rows marked in `touched` read U,
-// and U and the marks are cleared for the next chunk; x2 is added to r for the
-// columns that passed the test after x1; ||x2||_1 per column; the last block
-// applies the break tests after x1 and x2.  Grid-stride over rows, one row of
-// KP columns per thread (vector stores); a warp covers 32 consecutive rows,
-// i.e. one mark word, and skips its reduction when the word is empty.
+// x2 in FP32 into X, a buffer that is zero outside the rows marked in
+// `touched` (clear_x2_k restores that after the first pulled iteration): a
+// warp covers 32 consecutive rows, i.e. one mark word, and skips an empty
+// word without touching memory; marked rows read U (then cleared) and store
+// their KP columns (padding columns zero).  x2 is added to r for the columns
+// that passed the test after x1; ||x2||_1 per column; the last block applies
+// the break tests after x1 and x2.
 template <int KP>
-__global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, uint32_t *touched, float *X, float *R,
-                                                    int64_t n, int kc, float decay, double eps, double *part,
-                                                    void *ctl)
+__global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, const uint32_t *touched, float *X,
+                                                    float *R, int64_t n, int kc, float decay, double eps,
+                                                    double *part, void *ctl)
 {
     __shared__ float s_red[8][KP];
     __shared__ double s_fin[256];
@@ -1466,28 +1605,23 @@ __global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, uint3
     for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += step) {
         const int64_t v = base + threadIdx.x;
         const uint32_t word = v < n ? touched[v >> 5] : 0u;   // the same word in the whole warp
-        if (v < n) {
+        if ((word >> (v & 31)) & 1u) {
             float x[KP];
 #pragma unroll
-            for (int j = 0; j < KP; ++j) x[j] = 0.0f;
-            if ((word >> (v & 31)) & 1u) {
-#pragma unroll
-                for (int j = 0; j < KP; ++j) {
-                    if (j < kc) {
-                        const unsigned long long a = U[v * KP + j];
-                        if (a) {
-                            U[v * KP + j] = 0ull;
-                            x[j] = decay * (__ull2float_rn(a) * FX_INV_F);
-                            if (own[j]) R[v * KP + j] += x[j];
-                        }
+            for (int j = 0; j < KP; ++j) {
+                x[j] = 0.0f;
+                if (j < kc) {
+                    const unsigned long long a = U[v * KP + j];
+                    if (a) {
+                        U[v * KP + j] = 0ull;
+                        x[j] = decay * (__ull2float_rn(a) * FX_INV_F);
+                        if (own[j]) R[v * KP + j] += x[j];
                     }
-                    nrm[j] += x[j];
                 }
+                nrm[j] += x[j];
             }
             st_row<KP>(X + v * KP, x);
         }
-        __syncwarp();
-        if (lane == 0 && v < n && word) touched[v >> 5] = 0u;
     }
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
@@ -1523,6 +1657,26 @@ __global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, uint3
     }
     __syncthreads();
     if (threadIdx.x == 0) cv.hdr->ticket = 0;   // done stays 0: iteration 3 is pulled
+}
+
+// Restore the x2 buffer to zero and clear the row marks after the first pulled
+// iteration has read x2: one thread per mark word.
+template <int KP>
+__global__ void clear_x2_k(uint32_t *touched, float *X, int64_t nwords)
+{
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t word = touched[w];
+        if (!word) continue;
+        touched[w] = 0u;
+        float z[KP];
+#pragma unroll
+        for (int j = 0; j < KP; ++j) z[j] = 0.0f;
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            st_row<KP>(X + (w * 32 + b) * KP, z);
+        }
+    }
 }
 
 // ------------------------------------------------------------- planning ---
@@ -1616,7 +1770,7 @@ static int num_sms()
 
 // Persistent grid: resident CTAs per SM x SMs, capped by the tile count.
 template <int G, int V, int ITEMS, int PF>
-static void launch_spmm(const Params &p, cudaStream_t s)
+static int64_t launch_spmm(const Params &p, cudaStream_t s)
 {
     static int per_sm = 0;
     if (!per_sm) {
@@ -1625,10 +1779,11 @@ static void launch_spmm(const Params &p, cudaStream_t s)
     }
     const int64_t grid = std::min<int64_t>(p.tiles, (int64_t)per_sm * num_sms());
     spmm_tile_k<G, V, ITEMS, PF><<<(unsigned)grid, CTA, 0, s>>>(p);
+    return p.tiles;
 }
 
 template <int V, int ITEMS, int WARPS>
-static void launch_spmvw(const Params &p, cudaStream_t s)
+static int64_t launch_spmvw(const Params &p, cudaStream_t s)
 {
     static int per_sm = 0;
     if (!per_sm) {
@@ -1637,10 +1792,11 @@ static void launch_spmvw(const Params &p, cudaStream_t s)
     }
     const int64_t grid = std::min<int64_t>((p.tiles + WARPS - 1) / WARPS, (int64_t)per_sm * num_sms());
     spmvw_tile_k<V, ITEMS, WARPS><<<(unsigned)grid, WARPS * 32, 0, s>>>(p);
+    return p.tiles;
 }
 
 template <int G, int V, int ITEMS, int PF, int WARPS>
-static void launch_spmvg(const Params &p, cudaStream_t s)
+static int64_t launch_spmvg(const Params &p, cudaStream_t s)
 {
     static int per_sm = 0;
     if (!per_sm) {
@@ -1650,19 +1806,27 @@ static void launch_spmvg(const Params &p, cudaStream_t s)
     }
     const int64_t grid = std::min<int64_t>((p.tiles + WARPS - 1) / WARPS, (int64_t)per_sm * num_sms());
     spmvg_tile_k<G, V, ITEMS, PF, WARPS><<<(unsigned)grid, WARPS * 32, 0, s>>>(p);
+    return p.tiles;
 }
 
+// Returns the rows of tl1 written: one per warp of the grid (at most
+// tiles + 7, the size the workspace reserves).
 template <int G, int V, int ITEMS, int PF, int WARPS, int MINB>
-static void launch_spmvp(const Params &p, cudaStream_t s)
+static int64_t launch_spmvp(const Params &p, cudaStream_t s)
 {
+    constexpr size_t smem = WARPS * PipeSmem<G, V, ITEMS>::PER_WARP;
+    static_assert(smem <= 227 * 1024, "shared memory per block");
     static int per_sm = 0;
     if (!per_sm) {
+        TPA_CUDA(cudaFuncSetAttribute(spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB>,
-                                                               WARPS * 32, 0));
+                                                               WARPS * 32, smem));
         per_sm = std::max(per_sm, 1);
     }
     const int64_t grid = std::min<int64_t>((p.tiles + WARPS - 1) / WARPS, (int64_t)per_sm * num_sms());
-    spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB><<<(unsigned)grid, WARPS * 32, 0, s>>>(p);
+    spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB><<<(unsigned)grid, WARPS * 32, smem, s>>>(p);
+    return grid * WARPS;
 }
 
 template <int KP>
@@ -1685,27 +1849,26 @@ static unsigned fix_grid(int KP, int64_t tiles)
 
 struct Variant {
     KCfg cfg;
-    void (*spmm)(const Params &, cudaStream_t);
+    int64_t (*spmm)(const Params &, cudaStream_t);   // returns the rows of tl1 written
     void (*fix)(const Params &, unsigned, cudaStream_t);
-    bool red;           // epilogue by atomic adds: the final iteration needs out preset
     const char *name;
 };
 
 #define TPA_VARIANT(G, V, I, PF) \
-    {{G, V, I, PF, CTA}, launch_spmm<G, V, I, PF>, launch_fix<G * V>, false, "cta<" #G "," #V "," #I "," #PF ">"}
+    {{G, V, I, PF, CTA}, launch_spmm<G, V, I, PF>, launch_fix<G * V>, "cta<" #G "," #V "," #I "," #PF ">"}
 #define TPA_VARIANTW(V, I, W) \
-    {{1, V, I, I, 32}, launch_spmvw<V, I, W>, launch_fix<V>, false, "warp<" #V "," #I "," #W ">"}
+    {{1, V, I, I, 32}, launch_spmvw<V, I, W>, launch_fix<V>, "warp<" #V "," #I "," #W ">"}
 #define TPA_VARIANTG(G, V, I, PF) \
-    {{G, V, I, PF, 32}, launch_spmvg<G, V, I, PF, 8>, launch_fix<G * V>, false, "walker<" #G "," #V "," #I "," #PF ">"}
-#define TPA_VARIANTP(G, V, I, PF, W, MB)                                                  \
-    {{G, V, I, PF, 32}, launch_spmvp<G, V, I, PF, W, MB>, launch_fix<G * V>, true,        \
+    {{G, V, I, PF, 32}, launch_spmvg<G, V, I, PF, 8>, launch_fix<G * V>, "walker<" #G "," #V "," #I "," #PF ">"}
+#define TPA_VARIANTP(G, V, I, PF, W, MB)                                 \
+    {{G, V, I, PF, 32}, launch_spmvp<G, V, I, PF, W, MB>, launch_fix<G * V>, \
      "pipe<" #G "," #V "," #I "," #PF "," #W "," #MB ">"}
 // The first variant of each padded width is its default (the fastest measured
 // on R-MAT scale 22 queries); the autotuner may pick any other.
 static const Variant kVariants[] = {
     TPA_VARIANTW(1, 6, 8),
     TPA_VARIANTW(2, 6, 8),
-    TPA_VARIANTP(1, 4, 8, 8, 4, 1),
+    TPA_VARIANTP(1, 4, 4, 4, 8, 1),
     TPA_VARIANTP(2, 4, 8, 8, 8, 1),
     TPA_VARIANT(4, 4, 16, 8),
     TPA_VARIANT(8, 4, 16, 8),
@@ -1732,15 +1895,22 @@ static const Variant kVariants[] = {
     TPA_VARIANT(8, 1, 16, 16),
     TPA_VARIANT(2, 2, 8, 8),
     TPA_VARIANTP(1, 2, 8, 8, 4, 1),
-    TPA_VARIANTP(1, 4, 4, 4, 8, 1),
+    TPA_VARIANTP(1, 4, 8, 8, 4, 1),
     TPA_VARIANTP(1, 4, 8, 8, 4, 6),
     TPA_VARIANTP(2, 2, 8, 8, 8, 1),
     TPA_VARIANTP(2, 4, 16, 8, 4, 1),
     TPA_VARIANTP(2, 4, 8, 8, 8, 3),
     TPA_VARIANTP(2, 4, 8, 4, 8, 1),
     TPA_VARIANTP(2, 4, 8, 4, 8, 3),
+    TPA_VARIANTP(2, 4, 8, 8, 4, 5),
+    TPA_VARIANTP(2, 4, 8, 4, 4, 6),
+    TPA_VARIANTP(2, 4, 8, 4, 4, 8),
     TPA_VARIANTP(2, 4, 4, 4, 8, 1),
     TPA_VARIANTP(2, 4, 8, 8, 4, 1),
+    TPA_VARIANTP(1, 8, 4, 4, 8, 1),
+    TPA_VARIANTP(1, 8, 4, 4, 4, 1),
+    TPA_VARIANTP(1, 8, 8, 4, 4, 1),
+    TPA_VARIANTP(1, 8, 4, 2, 8, 1),
     TPA_VARIANTP(4, 4, 8, 8, 8, 1),
     TPA_VARIANTP(4, 4, 16, 8, 4, 1),
     TPA_VARIANTP(4, 4, 8, 4, 8, 2),
@@ -1775,7 +1945,8 @@ constexpr int DEFAULT_CHUNK_CPI = 128;
 // Push path for the first two family iterations of a query (on by default).
 static bool g_push = true;
 constexpr int PUSH_MAX_OUTDEG = 256;   // seeds with more out-edges keep the pull path
-constexpr int PUSH_BLOCKS = 16;        // blocks per column in push_x2_k
+static_assert(PUSH_MAX_OUTDEG <= PUSH_THREADS, "push_x2_k takes one thread per out-edge of the seed");
+constexpr int PUSH_BLOCKS = 32;        // blocks per column in push_x2_k
 
 static void launch_convert(int KP, unsigned blocks, unsigned long long *U, uint32_t *touched, float *X, float *R,
                            int64_t n, int kc, float decay, double eps, double *part, void *ctl, cudaStream_t s)
@@ -1785,6 +1956,18 @@ static void launch_convert(int KP, unsigned blocks, unsigned long long *U, uint3
     case 2: convert_x2_k<2><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl); break;
     case 4: convert_x2_k<4><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl); break;
     default: convert_x2_k<8><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl); break;
+    }
+}
+
+static void launch_clear_x2(int KP, uint32_t *touched, float *X, int64_t n, cudaStream_t s)
+{
+    const int64_t nwords = (n + 31) / 32;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nwords + 255) / 256, 8 * num_sms()));
+    switch (KP) {
+    case 1: clear_x2_k<1><<<blocks, 256, 0, s>>>(touched, X, nwords); break;
+    case 2: clear_x2_k<2><<<blocks, 256, 0, s>>>(touched, X, nwords); break;
+    case 4: clear_x2_k<4><<<blocks, 256, 0, s>>>(touched, X, nwords); break;
+    default: clear_x2_k<8><<<blocks, 256, 0, s>>>(touched, X, nwords); break;
     }
 }
 
@@ -1842,7 +2025,7 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     W.y.ensure((size_t)n * KP * sizeof(float), s);
     W.carry.ensure((size_t)P.tiles * KP * sizeof(float), s);
     W.head.ensure((size_t)P.tiles * KP * sizeof(float), s);
-    W.tl1.ensure((size_t)P.tiles * KP * sizeof(float), s);
+    W.tl1.ensure((size_t)(P.tiles + 8) * KP * sizeof(float), s);   // per tile, or per warp of a grid
     const unsigned fix_blocks = fix_grid(KP, P.tiles);
     W.fix.ensure((size_t)fix_blocks * KP * sizeof(double), s);
     W.ctl.ensure(CTL_BYTES, s);
@@ -1868,24 +2051,26 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     if (push) {
         const unsigned cblocks = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)8 * num_sms());
         W.fix.ensure((size_t)std::max<unsigned>(fix_blocks, cblocks) * KP * sizeof(double), s);
+        // U, the row marks and the x2 buffer are all zero between chunks
         if (!W.u.p || W.u.bytes < (size_t)n * KP * sizeof(unsigned long long) || !W.u_clean) {
             W.u.ensure((size_t)n * KP * sizeof(unsigned long long), s);
             W.touched.ensure((size_t)((n + 31) / 32) * sizeof(uint32_t), s);
+            W.x2.ensure((size_t)n * 8 * sizeof(float), s);
             TPA_CUDA(cudaMemsetAsync(W.u.p, 0, W.u.bytes, s));
             TPA_CUDA(cudaMemsetAsync(W.touched.p, 0, W.touched.bytes, s));
+            TPA_CUDA(cudaMemsetAsync(W.x2.p, 0, W.x2.bytes, s));
         }
         W.u_clean = false;
         TPA_CUDA(cudaMemsetAsync(r, 0, (size_t)n * KP * sizeof(float), s));
         const float decay_f = (float)(1.0 - a.c);
-        push_x2_k<<<dim3(PUSH_BLOCKS, kc), 256, 0, s>>>(g->rp_a.as<int64_t>(), g->col_a.as<int32_t>(),
+        push_x2_k<<<dim3(PUSH_BLOCKS, kc), PUSH_THREADS, 0, s>>>(g->rp_a.as<int64_t>(), g->col_a.as<int32_t>(),
                                                         g->val_a.as<float>(), a.seeds + k0, KP, c_val, decay_f,
                                                         W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), r,
                                                         W.ctl.p);
-        launch_convert(KP, cblocks, W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), W.x.as<float>(), r, n,
+        launch_convert(KP, cblocks, W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), W.x2.as<float>(), r, n,
                        kc, decay_f, a.eps, W.fix.as<double>(), W.ctl.p, s);
         note_launch("push", 2);
         TPA_CHECK_LAUNCH();
-        W.u_clean = true;
     } else {
         init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, a.seeds ? a.seeds + k0 : nullptr, kc,
                                                      c_val, pr_val, r, ldr, a.s_iter == 0 ? 1 : 0);
@@ -1931,7 +2116,9 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     p.part = W.fix.as<double>();
     p.ctl = W.ctl.p;
 
-    float *cur = W.x.as<float>(), *nxt = W.y.as<float>();
+    // with the push path, iteration 3 reads the sparse x2 buffer and writes y;
+    // from then on x and y alternate
+    float *cur = push ? W.x2.as<float>() : W.x.as<float>(), *nxt = W.y.as<float>();
     // Host-side early stop: every CHUNK iterations, read the device done flag
     // of the chunk before last, so launches never run far past convergence.
     const int CHUNK = 8;
@@ -1954,14 +2141,8 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
             p.iter = i;
             p.accumulate = i >= a.s_iter ? 1 : 0;
             p.mode = (a.tpa_final && i == last) ? MODE_FINAL : MODE_ACC;
-            if (p.mode == MODE_FINAL && var.red) {
-                // out = (1+alpha) r + r_str; the SpMM adds (1+alpha) y to it
-                finalize_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(r, ldr, a.r_str, p.one_plus_alpha, p.out, p.ldo, n,
-                                                               kc);
-                note_launch("finalize");
-            }
             ProfMark pm = prof_begin(s);
-            var.spmm(p, s);
+            p.l1_slots = var.spmm(p, s);
             prof_end(pm, spmm_family(KP), spmm_bytes(n, g->m, KP, kc, p.mode, p.accumulate), s);
             ProfMark pf = prof_begin(s);
             var.fix(p, fix_blocks, s);
@@ -1974,7 +2155,16 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
                 note_launch("finalize");
             }
             TPA_CHECK_LAUNCH();
-            std::swap(cur, nxt);
+            if (push && i == 3) {
+                launch_clear_x2(KP, W.touched.as<uint32_t>(), W.x2.as<float>(), n, s);
+                note_launch("push");
+                TPA_CHECK_LAUNCH();
+                W.u_clean = true;
+                cur = nxt;
+                nxt = W.x.as<float>();
+            } else {
+                std::swap(cur, nxt);
+            }
             if (hflag && i % CHUNK == 0) {
                 const int slot = chunk & 1;
                 if (chunk >= 2) {
@@ -2137,7 +2327,7 @@ void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float
     Workspace &W = g->ws;
     W.carry.ensure((size_t)P.tiles * KP * sizeof(float), s);
     W.head.ensure((size_t)P.tiles * KP * sizeof(float), s);
-    W.tl1.ensure((size_t)P.tiles * KP * sizeof(float), s);
+    W.tl1.ensure((size_t)(P.tiles + 8) * KP * sizeof(float), s);   // per tile, or per warp of a grid
     const unsigned fix_blocks = fix_grid(KP, P.tiles);
     W.fix.ensure((size_t)fix_blocks * KP * sizeof(double), s);
     W.ctl.ensure(CTL_BYTES, s);
@@ -2166,7 +2356,7 @@ void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float
     p.part = W.fix.as<double>();
     p.ctl = W.ctl.p;
     ProfMark pm = prof_begin(s);
-    var.spmm(p, s);
+    p.l1_slots = var.spmm(p, s);
     prof_end(pm, spmm_family(KP), spmm_bytes(g->n, g->m, KP, kc, MODE_ACC, 0), s);
     var.fix(p, fix_blocks, s);
     note_launch("init");
