@@ -378,6 +378,10 @@ def main(argv=None):
     torch.cuda.synchronize()
     bcpi_sps = len(bseeds) / (time.perf_counter() - c0)
 
+    # batched serving: uneven request batches (sizes uniform over {1,7,32,100,256})
+    # through tpa_query per batch and through a tpa_server replaying CUDA graphs
+    serving = measure_serving(tpa, torch, g, cand, stream)
+
     hbm, peak_kind = peaks()
 
     names = {v["index"]: v["name"] for v in tpa.variants()}
@@ -423,12 +427,42 @@ def main(argv=None):
                 "online_seeds_per_s": Q / (phases["queries"] / 1000.0),
                 "per_seed_cpi": {"value": cpi_sps, "unit": "seeds/s", "seeds": len(cpi_seeds), "eps": EPS},
                 "batched_cpi": {"value": bcpi_sps, "unit": "seeds/s", "seeds": int(bseeds.numel()), "eps": EPS},
-                "roofline_spmv_k1": roof_k1, "autotune": tuned, "kernels": stats}
+                "roofline_spmv_k1": roof_k1, "serving": serving, "autotune": tuned, "kernels": stats}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def measure_serving(tpa, torch, g, cand, stream, total=2048):
+    """Seeds/s of a stream of uneven batches, direct tpa_query calls against
+    CUDA-graph replays (tpa_server), each after one untimed pass over the sizes."""
+    import synth
+    sizes = synth.batch_sizes(total)
+    seeds = synth.query_seeds(cand, total, key=5)
+    batches, off = [], 0
+    for k in sizes:
+        batches.append(torch.from_numpy(seeds[off:off + k]).cuda())
+        off += k
+    out = torch.empty((g.n, max(sizes)), dtype=torch.float32, device="cuda")
+    srv = tpa.Server(g, S, max_k=max(sizes), out=out)
+    res = {"batches": len(sizes), "seeds": total, "sizes": sorted(set(sizes))}
+    for name, run in (("direct", lambda b: tpa.query(g, b, S)),
+                      ("graphs", lambda b: srv.query(b))):
+        for b in batches:
+            run(b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for b in batches:
+            run(b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name + "_seeds_per_s"] = total / (e0.elapsed_time(e1) / 1000.0)
+    res["server"] = srv.stats(max(sizes))
+    srv.free()
+    return res
 
 
 def measure_e2e(args, tpa, torch, n, src, dst, seeds):

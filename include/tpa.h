@@ -224,6 +224,47 @@ int tpa_get_cpi_batch_width(void);
  * only by FP32 rounding order.  enable = 0 pulls every iteration. */
 tpa_status tpa_set_push(int enable);
 
+/* ---------------------------------------------------- batched serving ---
+ * Algorithm 3 for a stream of request batches of uneven size, with the launch
+ * sequence of each batch size captured once in a CUDA graph and replayed.
+ * Not part of the paper (its online phase answers one seed at a time).
+ *
+ * A server answers into one caller-owned device buffer out (float32, node-
+ * major, row stride ldo >= max_k): after tpa_server_query with k seeds,
+ * out[v * ldo + j] for j < k is the TPA score of node v for seeds[j].  A
+ * server keeps its own workspace (about 6 n * 8 floats for chunks of 8 seeds)
+ * and graphs that point at it and at the graph's CSR: it must be freed before
+ * the graph, and calls on one server must not overlap.  Results equal those
+ * of tpa_query with the same settings bit for bit.  A change of a kernel
+ * setting (tpa_set_variant, tpa_set_batch_width, tpa_set_push) makes the
+ * server capture again. */
+typedef struct tpa_server tpa_server;
+
+/* Create a server for queries with S family steps and at most max_k seeds
+ * per batch on a preprocessed graph.  out: device buffer of n rows of ldo
+ * floats, or NULL to let the server allocate one (ldo is then max_k; see
+ * tpa_server_result).  Errors: TPA_ESTATE before tpa_preprocess; TPA_EINVAL
+ * for S outside [1, T], max_k < 1, ldo < max_k or a host out. */
+tpa_status tpa_server_create(tpa_graph *g, int S, int max_k, float *out, int64_t ldo, void *stream,
+                             tpa_server **srv);
+
+/* Answer one batch of k <= max_k seeds (host or device int32, 0 <= id < n;
+ * ids are checked on the host, so device ids cost one small copy and a wait).
+ * The first batch of a size runs directly and captures the graph for that
+ * size; later batches of the size replay it.  Work is issued on stream. */
+tpa_status tpa_server_query(tpa_server *srv, const int32_t *seeds, int k, void *stream);
+
+/* The output buffer and its row stride. */
+tpa_status tpa_server_result(const tpa_server *srv, float **out, int64_t *ldo);
+
+/* Graphs captured so far, graph replays, and kernel launches per replay of
+ * the graph for batch size k (0 if none). */
+tpa_status tpa_server_stats(const tpa_server *srv, int k, int64_t *graphs, int64_t *replays,
+                            int64_t *launches_per_replay);
+
+/* Release the server (waits for its work). */
+void tpa_server_free(tpa_server *srv);
+
 /* ------------------------------------------------------ measurement ---
  * Not part of the paper's method: launch accounting and kernel timing for
  * benchmarks.  The statistics are process-wide and thread-safe. */

@@ -13,6 +13,7 @@ from __future__ import annotations
 from .tpa import (  # noqa: F401
     TpaError,
     Graph,
+    Server,
     build_graph,
     cpi,
     cpi_exact,

@@ -223,12 +223,6 @@ __global__ void theta_grad_k(const float *feat, const float *w, const float *gw,
     if (threadIdx.x == 0) *ticket = 0;
 }
 
-double alpha_of(double c, int S, int T)
-{
-    const double a = std::pow(1.0 - c, (double)S), b = std::pow(1.0 - c, (double)T);
-    return (a - b) / (1.0 - a);
-}
-
 }  // namespace
 
 void ensure_row_ids(tpa_graph *g, cudaStream_t s)

@@ -66,7 +66,7 @@ void copy_in(void *dst_dev, const void *src_any, size_t bytes, cudaStream_t s)
     if (bytes) TPA_CUDA(cudaMemcpyAsync(dst_dev, src_any, bytes, cudaMemcpyDefault, s));
 }
 
-static double alpha_of(double c, int S, int T)
+double alpha_of(double c, int S, int T)
 {
     // Section III-B: ||r_neighbor||_1 / ||r_family||_1 by Lemma 2
     const double a = std::pow(1.0 - c, (double)S), b = std::pow(1.0 - c, (double)T);
@@ -291,7 +291,7 @@ tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *ou
     a.r_str = g->r_str.as<float>();
     a.out = dout;
     a.ldo = k;
-    std::vector<int32_t> od = seed_outdegrees(g, a.seeds, k, s);
+    std::vector<int32_t> od = seed_outdegrees(g, a.seeds, k, s);   // the host picks each chunk's branch
     a.seed_outdeg = od.data();
     run_cpi(g, a, s);
     if (host_out) {

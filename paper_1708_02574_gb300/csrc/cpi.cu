@@ -32,6 +32,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstddef>
 #include <cmath>
 #include <vector>
@@ -104,7 +105,21 @@ struct Params {
     // number of [KP] rows of tl1 the SpMM wrote (0 = one per tile); the
     // pipelined kernel writes one per warp of its grid
     int64_t l1_slots;
+    // branch gate of a query chunk whose path the device chooses:
+    // GATE_NONE runs always, GATE_PULL / GATE_PUSH only on that branch
+    int gate;
 };
+
+enum Gate : int { GATE_NONE = 0, GATE_PULL = 1, GATE_PUSH = 2 };
+
+// Whether a launch of a gated branch is off for the chunk (Ctl::push is set
+// by push_decide_k before the branch kernels run).
+__device__ __forceinline__ bool gate_off(int gate, const void *ctl)
+{
+    if (gate == GATE_NONE) return false;
+    const int32_t push = *(volatile const int32_t *)&reinterpret_cast<const Ctl *>(ctl)->push;
+    return gate == GATE_PUSH ? push == 0 : push != 0;
+}
 
 // ------------------------------------------------------------- helpers ---
 template <int V>
@@ -257,7 +272,7 @@ __global__ void __launch_bounds__(CTA) spmm_tile_k(Params p)
     __shared__ Sm S;
 
     const CtlView cv = ctl_view(p.ctl);
-    if (*(volatile int32_t *)&cv.hdr->done) return;
+    if (gate_off(p.gate, p.ctl) || *(volatile int32_t *)&cv.hdr->done) return;
 
     const int vt = threadIdx.x / G, g = threadIdx.x % G;
     const int col0 = g * V;
@@ -507,7 +522,7 @@ spmvw_tile_k(Params p)
     static_assert(sizeof(WT) * WARPS <= 48 * 1024, "static shared memory is limited to 48 KB per block");
     __shared__ WT S_all[WARPS];
     const CtlView cv = ctl_view(p.ctl);
-    if (*(volatile int32_t *)&cv.hdr->done) return;
+    if (gate_off(p.gate, p.ctl) || *(volatile int32_t *)&cv.hdr->done) return;
     int alive[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) alive[j] = cv.alive[j];
@@ -691,7 +706,7 @@ __global__ void __launch_bounds__(WARPS * 32) spmvg_tile_k(Params p)
     static_assert(sizeof(GT) * WARPS <= 48 * 1024, "static shared memory is limited to 48 KB per block");
     __shared__ GT S_all[WARPS];
     const CtlView cv = ctl_view(p.ctl);
-    if (*(volatile int32_t *)&cv.hdr->done) return;
+    if (gate_off(p.gate, p.ctl) || *(volatile int32_t *)&cv.hdr->done) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int w = lane / G, gl = lane % G, col0 = gl * V;
     int alive[V];
@@ -1126,7 +1141,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
     static_assert(SM::PER_WARP % 16 == 0, "warp slices must stay 16-byte aligned");
     extern __shared__ __align__(16) unsigned char pipe_smem[];
     const CtlView cv = ctl_view(p.ctl);
-    if (*(volatile int32_t *)&cv.hdr->done) return;
+    if (gate_off(p.gate, p.ctl) || *(volatile int32_t *)&cv.hdr->done) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int col0 = (lane % G) * V;
     unsigned char *base = pipe_smem + (size_t)warp * SM::PER_WARP;
@@ -1233,7 +1248,7 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) fixup_k(Params p)
     __shared__ double s_red[256];
     __shared__ int s_last;
     const CtlView cv = ctl_view(p.ctl);
-    if (*(volatile int32_t *)&cv.hdr->done) return;
+    if (gate_off(p.gate, p.ctl) || *(volatile int32_t *)&cv.hdr->done) return;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cl = lane % CW, sub = lane / CW;
@@ -1324,7 +1339,7 @@ __global__ void __launch_bounds__(256) fixup_small_k(Params p)
     __shared__ double s_fin[256];
     __shared__ int s_last;
     const CtlView cv = ctl_view(p.ctl);
-    if (*(volatile int32_t *)&cv.hdr->done) return;
+    if (gate_off(p.gate, p.ctl) || *(volatile int32_t *)&cv.hdr->done) return;
     int alive[V];
 #pragma unroll
     for (int q = 0; q < V; ++q) alive[q] = cv.alive[q];
@@ -1422,8 +1437,9 @@ __global__ void __launch_bounds__(256) fixup_small_k(Params p)
 // x0 = c q per column (one-hot at seeds[j], or c/n everywhere when seeds is null);
 // r = x0 when s_iter == 0, else 0.
 __global__ void init_k(float *x, int KP, int64_t n, const int32_t *seeds, int k, float c_val, float pr_val,
-                       float *r, int64_t ldr, int acc0)
+                       float *r, int64_t ldr, int acc0, const void *ctl, int gate)
 {
+    if (gate_off(gate, ctl)) return;
     const int64_t total = n * KP;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = i / KP;
@@ -1449,6 +1465,7 @@ __global__ void ctl_init_k(void *ctl, int k)
         cv.hdr->done = 0;
         cv.hdr->ticket = 0;
         cv.hdr->iter = 0;
+        cv.hdr->push = 0;
     }
 }
 
@@ -1514,8 +1531,9 @@ constexpr int PUSH_THREADS = 256;
 __global__ void __launch_bounds__(PUSH_THREADS) push_x2_k(const int64_t *rp_a, const int32_t *col_a,
                                                           const float *val_a, const int32_t *seeds, int KP, float c_f,
                                                           float decay, unsigned long long *U, uint32_t *touched,
-                                                          float *R, void *ctl)
+                                                          float *R, void *ctl, int gate)
 {
+    if (gate_off(gate, ctl)) return;
     __shared__ int64_t s_start[PUSH_THREADS];     // first out-edge of neighbour k
     __shared__ int64_t s_pref[PUSH_THREADS + 1];  // exclusive prefix of the neighbours' out-degrees
     __shared__ float s_x1[PUSH_THREADS];
@@ -1588,8 +1606,9 @@ __global__ void __launch_bounds__(PUSH_THREADS) push_x2_k(const int64_t *rp_a, c
 template <int KP>
 __global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, const uint32_t *touched, float *X,
                                                     float *R, int64_t n, int kc, float decay, double eps,
-                                                    double *part, void *ctl)
+                                                    double *part, void *ctl, int gate)
 {
+    if (gate_off(gate, ctl)) return;
     __shared__ float s_red[8][KP];
     __shared__ double s_fin[256];
     __shared__ int s_last;
@@ -1659,11 +1678,35 @@ __global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, const
     if (threadIdx.x == 0) cv.hdr->ticket = 0;   // done stays 0: iteration 3 is pulled
 }
 
+// Per query chunk: the push branch is taken when every seed has at most
+// PUSH_MAX_OUTDEG out-edges (the push kernel takes one thread per out-edge).
+__global__ void push_decide_k(const int32_t *seeds, int kc, const int32_t *outdeg, int max_outdeg, void *ctl)
+{
+    const int lane = threadIdx.x;
+    bool ok = true;
+    for (int j = lane; j < kc; j += 32) ok = ok && outdeg[seeds[j]] <= max_outdeg;
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) reinterpret_cast<Ctl *>(ctl)->push = ok ? 1 : 0;
+}
+
+// x[0..count) = 0 on a gated branch.
+__global__ void zero_k(float *x, int64_t count, const void *ctl, int gate)
+{
+    if (gate_off(gate, ctl)) return;
+    const int64_t n4 = count / 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+        reinterpret_cast<float4 *>(x)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = 0.0f;
+}
+
 // Restore the x2 buffer to zero and clear the row marks after the first pulled
 // iteration has read x2: one thread per mark word.
 template <int KP>
-__global__ void clear_x2_k(uint32_t *touched, float *X, int64_t nwords)
+__global__ void clear_x2_k(uint32_t *touched, float *X, int64_t nwords, const void *ctl, int gate)
 {
+    if (gate_off(gate, ctl)) return;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += (int64_t)gridDim.x * blockDim.x) {
         uint32_t word = touched[w];
         if (!word) continue;
@@ -1932,6 +1975,8 @@ int kp_for(int k)
 
 constexpr int NUM_VARIANTS = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 // Variant chosen per padded width (index into kVariants, -1 = default).
+static std::atomic<uint64_t> g_epoch{0};
+uint64_t settings_epoch() { return g_epoch.load(); }
 static int g_forced[KP_MAX + 1];
 static bool g_forced_init = false;
 // Seeds per CPI chunk in batched calls (a power of two <= KP_MAX).
@@ -1949,25 +1994,26 @@ static_assert(PUSH_MAX_OUTDEG <= PUSH_THREADS, "push_x2_k takes one thread per o
 constexpr int PUSH_BLOCKS = 32;        // blocks per column in push_x2_k
 
 static void launch_convert(int KP, unsigned blocks, unsigned long long *U, uint32_t *touched, float *X, float *R,
-                           int64_t n, int kc, float decay, double eps, double *part, void *ctl, cudaStream_t s)
+                           int64_t n, int kc, float decay, double eps, double *part, void *ctl, int gate,
+                           cudaStream_t s)
 {
     switch (KP) {
-    case 1: convert_x2_k<1><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl); break;
-    case 2: convert_x2_k<2><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl); break;
-    case 4: convert_x2_k<4><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl); break;
-    default: convert_x2_k<8><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl); break;
+    case 1: convert_x2_k<1><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl, gate); break;
+    case 2: convert_x2_k<2><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl, gate); break;
+    case 4: convert_x2_k<4><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl, gate); break;
+    default: convert_x2_k<8><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl, gate); break;
     }
 }
 
-static void launch_clear_x2(int KP, uint32_t *touched, float *X, int64_t n, cudaStream_t s)
+static void launch_clear_x2(int KP, uint32_t *touched, float *X, int64_t n, void *ctl, int gate, cudaStream_t s)
 {
     const int64_t nwords = (n + 31) / 32;
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nwords + 255) / 256, 8 * num_sms()));
     switch (KP) {
-    case 1: clear_x2_k<1><<<blocks, 256, 0, s>>>(touched, X, nwords); break;
-    case 2: clear_x2_k<2><<<blocks, 256, 0, s>>>(touched, X, nwords); break;
-    case 4: clear_x2_k<4><<<blocks, 256, 0, s>>>(touched, X, nwords); break;
-    default: clear_x2_k<8><<<blocks, 256, 0, s>>>(touched, X, nwords); break;
+    case 1: clear_x2_k<1><<<blocks, 256, 0, s>>>(touched, X, nwords, ctl, gate); break;
+    case 2: clear_x2_k<2><<<blocks, 256, 0, s>>>(touched, X, nwords, ctl, gate); break;
+    case 4: clear_x2_k<4><<<blocks, 256, 0, s>>>(touched, X, nwords, ctl, gate); break;
+    default: clear_x2_k<8><<<blocks, 256, 0, s>>>(touched, X, nwords, ctl, gate); break;
     }
 }
 
@@ -2045,10 +2091,25 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
         ldr = a.ldr;
     }
     const int last = a.t_iter >= 0 ? a.t_iter : iteration_bound(a.c, a.eps);
-    // Push path for the first two family iterations (light seeds, narrow chunks).
-    bool push = g_push && a.tpa_final && a.seeds && a.seed_outdeg && last >= 3 && KP <= 8 && a.r_internal;
-    for (int j = 0; push && j < kc; ++j) push = a.seed_outdeg[k0 + j] <= PUSH_MAX_OUTDEG;
-    if (push) {
+    // Query chunks of at most 8 seeds have two branches for x1 and x2: push
+    // along CSR(A~) when every seed is light, pull otherwise.  With the seeds'
+    // out-degrees on the host the branch is chosen here and only its kernels
+    // are launched; without them (a launch sequence being captured into a
+    // CUDA graph) the device chooses (push_decide_k) and the kernels of the
+    // other branch return at once.  On both branches x2 ends in the x2
+    // buffer, which iteration 3 reads.
+    const bool two_way = g_push && a.tpa_final && a.seeds && last >= 3 && KP <= 8 && a.r_internal;
+    bool host_decided = false, host_push = false;
+    if (two_way && a.seed_outdeg) {
+        host_decided = true;
+        host_push = true;
+        for (int j = 0; j < kc; ++j) host_push = host_push && a.seed_outdeg[k0 + j] <= PUSH_MAX_OUTDEG;
+    }
+    const bool run_push = two_way && (!host_decided || host_push);
+    const bool run_pull = two_way && (!host_decided || !host_push);
+    const int gate_push = host_decided ? GATE_NONE : GATE_PUSH;
+    const int gate_pull = host_decided ? GATE_NONE : GATE_PULL;
+    if (two_way) {
         const unsigned cblocks = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)8 * num_sms());
         W.fix.ensure((size_t)std::max<unsigned>(fix_blocks, cblocks) * KP * sizeof(double), s);
         // U, the row marks and the x2 buffer are all zero between chunks
@@ -2061,19 +2122,30 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
             TPA_CUDA(cudaMemsetAsync(W.x2.p, 0, W.x2.bytes, s));
         }
         W.u_clean = false;
-        TPA_CUDA(cudaMemsetAsync(r, 0, (size_t)n * KP * sizeof(float), s));
-        const float decay_f = (float)(1.0 - a.c);
-        push_x2_k<<<dim3(PUSH_BLOCKS, kc), PUSH_THREADS, 0, s>>>(g->rp_a.as<int64_t>(), g->col_a.as<int32_t>(),
-                                                        g->val_a.as<float>(), a.seeds + k0, KP, c_val, decay_f,
-                                                        W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), r,
-                                                        W.ctl.p);
-        launch_convert(KP, cblocks, W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), W.x2.as<float>(), r, n,
-                       kc, decay_f, a.eps, W.fix.as<double>(), W.ctl.p, s);
-        note_launch("push", 2);
+        if (!host_decided) {
+            push_decide_k<<<1, 32, 0, s>>>(a.seeds + k0, kc, g->outdeg.as<int32_t>(), PUSH_MAX_OUTDEG, W.ctl.p);
+            note_launch("push");
+        }
+        if (run_push) {   // r = x0 + x1, x2 into the x2 buffer
+            const float decay_f = (float)(1.0 - a.c);
+            zero_k<<<grid_1d(n * KP / 4, 256), 256, 0, s>>>(r, n * KP, W.ctl.p, gate_push);
+            push_x2_k<<<dim3(PUSH_BLOCKS, kc), PUSH_THREADS, 0, s>>>(
+                g->rp_a.as<int64_t>(), g->col_a.as<int32_t>(), g->val_a.as<float>(), a.seeds + k0, KP, c_val,
+                decay_f, W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), r, W.ctl.p, gate_push);
+            launch_convert(KP, cblocks, W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), W.x2.as<float>(), r,
+                           n, kc, decay_f, a.eps, W.fix.as<double>(), W.ctl.p, gate_push, s);
+            note_launch("push", 3);
+        }
+        if (run_pull) {   // x0; iterations 1 and 2 are pulled below
+            init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, a.seeds + k0, kc, c_val, pr_val, r,
+                                                         ldr, a.s_iter == 0 ? 1 : 0, W.ctl.p, gate_pull);
+            note_launch("init");
+        }
         TPA_CHECK_LAUNCH();
     } else {
         init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, a.seeds ? a.seeds + k0 : nullptr, kc,
-                                                     c_val, pr_val, r, ldr, a.s_iter == 0 ? 1 : 0);
+                                                     c_val, pr_val, r, ldr, a.s_iter == 0 ? 1 : 0, W.ctl.p,
+                                                     GATE_NONE);
         note_launch("init");
         TPA_CHECK_LAUNCH();
     }
@@ -2116,9 +2188,9 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     p.part = W.fix.as<double>();
     p.ctl = W.ctl.p;
 
-    // with the push path, iteration 3 reads the sparse x2 buffer and writes y;
-    // from then on x and y alternate
-    float *cur = push ? W.x2.as<float>() : W.x.as<float>(), *nxt = W.y.as<float>();
+    // x and y alternate; on a two-way chunk iteration 2 writes and iteration
+    // 3 reads the x2 buffer
+    float *cur = W.x.as<float>(), *nxt = W.y.as<float>();
     // Host-side early stop: every CHUNK iterations, read the device done flag
     // of the chunk before last, so launches never run far past convergence.
     const int CHUNK = 8;
@@ -2135,9 +2207,14 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
             TPA_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
         }
         int chunk = 0;
-        for (int i = push ? 3 : 1; i <= last; ++i) {
+        for (int i = two_way && !run_pull ? 3 : 1; i <= last; ++i) {
+            if (two_way && i == 3) {   // iteration 3 reads x2 from the x2 buffer and writes y
+                cur = W.x2.as<float>();
+                nxt = W.y.as<float>();
+            }
             p.x = cur;
-            p.y = nxt;
+            p.y = (two_way && i == 2) ? W.x2.as<float>() : nxt;
+            p.gate = (two_way && i <= 2) ? gate_pull : GATE_NONE;
             p.iter = i;
             p.accumulate = i >= a.s_iter ? 1 : 0;
             p.mode = (a.tpa_final && i == last) ? MODE_FINAL : MODE_ACC;
@@ -2155,14 +2232,21 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
                 note_launch("finalize");
             }
             TPA_CHECK_LAUNCH();
-            if (push && i == 3) {
-                launch_clear_x2(KP, W.touched.as<uint32_t>(), W.x2.as<float>(), n, s);
-                note_launch("push");
+            if (two_way && i == 3) {
+                // restore the x2 buffer: sparse on the push branch, whole on the pull branch
+                if (run_push) {
+                    launch_clear_x2(KP, W.touched.as<uint32_t>(), W.x2.as<float>(), n, W.ctl.p, gate_push, s);
+                    note_launch("push");
+                }
+                if (run_pull) {
+                    zero_k<<<grid_1d(n * KP / 4, 256), 256, 0, s>>>(W.x2.as<float>(), n * KP, W.ctl.p, gate_pull);
+                    note_launch("push");
+                }
                 TPA_CHECK_LAUNCH();
                 W.u_clean = true;
                 cur = nxt;
                 nxt = W.x.as<float>();
-            } else {
+            } else if (!(two_way && i == 2)) {
                 std::swap(cur, nxt);
             }
             if (hflag && i % CHUNK == 0) {
@@ -2428,6 +2512,7 @@ tpa_status tpa_set_variant(int kp, int idx)
         g_forced_init = true;
     }
     g_forced[kp] = idx < 0 ? -1 : idx;
+    ++g_epoch;
     return TPA_OK;
 }
 
@@ -2440,6 +2525,7 @@ tpa_status tpa_set_batch_width(int width)
         return TPA_EINVAL;
     }
     g_chunk_query = width;
+    ++g_epoch;
     return TPA_OK;
 }
 
@@ -2452,6 +2538,7 @@ tpa_status tpa_set_cpi_batch_width(int width)
         return TPA_EINVAL;
     }
     g_chunk_cpi = width;
+    ++g_epoch;
     return TPA_OK;
 }
 
@@ -2460,6 +2547,7 @@ int tpa_get_cpi_batch_width(void) { return g_chunk_cpi ? g_chunk_cpi : DEFAULT_C
 tpa_status tpa_set_push(int enable)
 {
     g_push = enable != 0;
+    ++g_epoch;
     return TPA_OK;
 }
 

@@ -59,6 +59,22 @@ void note_launch(const char *family, int count)
 
 void note_launch_count(int count) { g_launches += (uint64_t)count; }
 
+uint64_t launches_so_far() { return g_launches.load(); }
+
+bool prof_pause()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    const bool was = g_timing;
+    g_timing = false;
+    return was;
+}
+
+void prof_resume(bool timing)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_timing = timing;
+}
+
 ProfMark prof_begin(cudaStream_t s)
 {
     ProfMark m{nullptr};

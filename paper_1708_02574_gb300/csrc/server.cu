@@ -1,0 +1,254 @@
+// Batched query serving (Algorithm 3 over a stream of request batches).
+//
+// A request batch of k seeds is answered by the same launch sequence that
+// tpa_query issues (query chunks whose push/pull branch is chosen on the
+// device, so the sequence depends only on k and the kernel settings).  The
+// first batch of each size runs directly and that sequence is then captured
+// once into a CUDA graph; later batches of the size copy their seeds into
+// the server's seed buffer and replay the graph: one launch instead of about
+// ten per chunk of eight seeds.  The server owns a workspace of its own,
+// swapped into the graph handle while a batch runs, so the device pointers a
+// captured graph holds stay valid whatever the graph handle does in between.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <map>
+#include <utility>
+
+#include "tpa_internal.cuh"
+
+using namespace tpa;
+
+struct tpa_server {
+    tpa_graph *g = nullptr;
+    int S = 0, max_k = 0;
+    float *out = nullptr;
+    int64_t ldo = 0;
+    DevBuf out_buf;                 // when the server allocated out
+    DevBuf seeds;                   // int32[max_k], read by the captured graphs
+    int32_t *h_seeds = nullptr;     // pinned staging of the seed copy
+    cudaEvent_t staged = nullptr;   // the last seed copy has left h_seeds
+    cudaStream_t cap = nullptr;     // capture stream
+    Workspace ws;
+    struct Entry {
+        cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0;
+    };
+    std::map<int, Entry> graphs;
+    uint64_t epoch = 0;
+    int64_t replays = 0;
+};
+
+namespace {
+
+// The server's workspace stands in for the graph's while a batch is issued.
+struct WorkspaceSwap {
+    tpa_graph *g;
+    Workspace *w;
+    WorkspaceSwap(tpa_graph *g_, Workspace *w_) : g(g_), w(w_) { std::swap(g->ws, *w); }
+    ~WorkspaceSwap() { std::swap(g->ws, *w); }
+};
+
+void issue_batch(tpa_server *srv, int k, cudaStream_t s)
+{
+    tpa_graph *g = srv->g;
+    CpiArgs a;
+    a.seeds = srv->seeds.as<int32_t>();
+    a.k = k;
+    a.c = g->c;
+    a.eps = g->eps;
+    a.s_iter = 0;
+    a.t_iter = srv->S - 1;
+    a.r_internal = true;
+    a.tpa_final = true;
+    a.alpha = alpha_of(g->c, srv->S, g->T);
+    a.r_str = g->r_str.as<float>();
+    a.out = srv->out;
+    a.ldo = srv->ldo;
+    run_cpi(g, a, s);
+}
+
+void drop_graphs(tpa_server *srv)
+{
+    for (auto &kv : srv->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    srv->graphs.clear();
+}
+
+// Capture the launch sequence of a batch of k seeds (the workspace already has
+// its sizes for k, so nothing is allocated while capturing).
+tpa_server::Entry capture(tpa_server *srv, int k)
+{
+    tpa_server::Entry e;
+    const bool timing = prof_pause();
+    const uint64_t l0 = launches_so_far();
+    cudaGraph_t graph = nullptr;
+    TPA_CUDA(cudaStreamBeginCapture(srv->cap, cudaStreamCaptureModeThreadLocal));
+    try {
+        issue_batch(srv, k, srv->cap);
+    } catch (...) {
+        cudaStreamEndCapture(srv->cap, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        prof_resume(timing);
+        throw;
+    }
+    const cudaError_t ce = cudaStreamEndCapture(srv->cap, &graph);
+    prof_resume(timing);
+    e.launches = (int64_t)(launches_so_far() - l0);
+    note_launch_count(-(int)e.launches);   // nothing ran while capturing
+    if (ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        TPA_CUDA(ce);
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    TPA_CUDA(ie);
+    return e;
+}
+
+}  // namespace
+
+#define SRV_BEGIN \
+    clear_error(); \
+    try {
+#define SRV_END                                   \
+    }                                             \
+    catch (const Fail &f) {                       \
+        return f.st;                              \
+    }                                             \
+    catch (const std::bad_alloc &) {              \
+        set_error("host allocation failed");      \
+        return TPA_ENOMEM;                        \
+    }                                             \
+    catch (...) {                                 \
+        set_error("unexpected C++ exception");    \
+        return TPA_ECUDA;                         \
+    }                                             \
+    return TPA_OK;
+
+extern "C" {
+
+tpa_status tpa_server_create(tpa_graph *g, int S, int max_k, float *out, int64_t ldo, void *stream,
+                             tpa_server **srv_out)
+{
+    SRV_BEGIN
+    TPA_REQUIRE(g != nullptr && srv_out != nullptr, "tpa_server_create: NULL argument");
+    if (!g->has_pre) {
+        set_error("tpa_server_create: the graph is not preprocessed");
+        throw Fail{TPA_ESTATE};
+    }
+    TPA_REQUIRE(S >= 1 && S <= g->T, "tpa_server_create: S = %d outside [1, T = %d]", S, g->T);
+    TPA_REQUIRE(max_k >= 1, "tpa_server_create: max_k = %d < 1", max_k);
+    TPA_REQUIRE(out == nullptr || is_device_ptr(out), "tpa_server_create: out must be device memory");
+    TPA_REQUIRE(out == nullptr || ldo >= max_k, "tpa_server_create: ldo = %lld < max_k = %d", (long long)ldo, max_k);
+    cudaStream_t s = (cudaStream_t)stream;
+    tpa_server *srv = new tpa_server();
+    try {
+        srv->g = g;
+        srv->S = S;
+        srv->max_k = max_k;
+        if (out) {
+            srv->out = out;
+            srv->ldo = ldo;
+        } else {
+            srv->out_buf.ensure((size_t)g->n * max_k * sizeof(float), s);
+            srv->out = srv->out_buf.as<float>();
+            srv->ldo = max_k;
+        }
+        srv->seeds.ensure((size_t)max_k * sizeof(int32_t), s);
+        TPA_CUDA(cudaHostAlloc((void **)&srv->h_seeds, (size_t)max_k * sizeof(int32_t), cudaHostAllocDefault));
+        TPA_CUDA(cudaEventCreateWithFlags(&srv->staged, cudaEventDisableTiming));
+        TPA_CUDA(cudaStreamCreateWithFlags(&srv->cap, cudaStreamNonBlocking));
+        srv->epoch = settings_epoch();
+    } catch (...) {
+        tpa_server_free(srv);
+        throw;
+    }
+    *srv_out = srv;
+    SRV_END
+}
+
+tpa_status tpa_server_query(tpa_server *srv, const int32_t *seeds, int k, void *stream)
+{
+    SRV_BEGIN
+    TPA_REQUIRE(srv != nullptr && seeds != nullptr, "tpa_server_query: NULL argument");
+    TPA_REQUIRE(k >= 1 && k <= srv->max_k, "tpa_server_query: k = %d outside [1, %d]", k, srv->max_k);
+    cudaStream_t s = (cudaStream_t)stream;
+    tpa_graph *g = srv->g;
+    // stage and check the ids, then copy them to the seed buffer the graphs read
+    TPA_CUDA(cudaEventSynchronize(srv->staged));
+    if (is_device_ptr(seeds)) {
+        TPA_CUDA(cudaMemcpyAsync(srv->h_seeds, seeds, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        TPA_CUDA(cudaStreamSynchronize(s));
+    } else {
+        memcpy(srv->h_seeds, seeds, (size_t)k * sizeof(int32_t));
+    }
+    for (int j = 0; j < k; ++j)
+        TPA_REQUIRE(srv->h_seeds[j] >= 0 && srv->h_seeds[j] < g->n, "seed %d (index %d) is outside [0, %lld)",
+                    srv->h_seeds[j], j, (long long)g->n);
+    TPA_CUDA(cudaMemcpyAsync(srv->seeds.p, srv->h_seeds, (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    TPA_CUDA(cudaEventRecord(srv->staged, s));
+
+    if (srv->epoch != settings_epoch()) {   // a kernel setting changed: recapture
+        TPA_CUDA(cudaStreamSynchronize(s));
+        drop_graphs(srv);
+        srv->epoch = settings_epoch();
+    }
+    WorkspaceSwap swap(g, &srv->ws);
+    auto it = srv->graphs.find(k);
+    if (it == srv->graphs.end()) {
+        issue_batch(srv, k, s);                 // this batch's answer; sizes the workspace for k
+        TPA_CUDA(cudaStreamSynchronize(s));     // the capture must not race the direct run
+        srv->graphs[k] = capture(srv, k);
+    } else {
+        TPA_CUDA(cudaGraphLaunch(it->second.exec, s));
+        note_launch_count((int)it->second.launches);
+        ++srv->replays;
+    }
+    SRV_END
+}
+
+tpa_status tpa_server_result(const tpa_server *srv, float **out, int64_t *ldo)
+{
+    SRV_BEGIN
+    TPA_REQUIRE(srv != nullptr, "tpa_server_result: NULL server");
+    if (out) *out = srv->out;
+    if (ldo) *ldo = srv->ldo;
+    SRV_END
+}
+
+tpa_status tpa_server_stats(const tpa_server *srv, int k, int64_t *graphs, int64_t *replays,
+                            int64_t *launches_per_replay)
+{
+    SRV_BEGIN
+    TPA_REQUIRE(srv != nullptr, "tpa_server_stats: NULL server");
+    if (graphs) *graphs = (int64_t)srv->graphs.size();
+    if (replays) *replays = srv->replays;
+    if (launches_per_replay) {
+        auto it = srv->graphs.find(k);
+        *launches_per_replay = it == srv->graphs.end() ? 0 : it->second.launches;
+    }
+    SRV_END
+}
+
+void tpa_server_free(tpa_server *srv)
+{
+    if (!srv) return;
+    cudaDeviceSynchronize();
+    drop_graphs(srv);
+    cudaStream_t s = 0;
+    DevBuf *bufs[] = {&srv->out_buf, &srv->seeds, &srv->ws.x, &srv->ws.y, &srv->ws.r, &srv->ws.carry,
+                      &srv->ws.head, &srv->ws.tl1, &srv->ws.fix, &srv->ws.ctl, &srv->ws.seeds, &srv->ws.out,
+                      &srv->ws.iters, &srv->ws.u, &srv->ws.touched, &srv->ws.x2};
+    for (DevBuf *b : bufs) b->release(s);
+    if (srv->ws.hflag) cudaFreeHost(srv->ws.hflag);
+    if (srv->h_seeds) cudaFreeHost(srv->h_seeds);
+    if (srv->staged) cudaEventDestroy(srv->staged);
+    if (srv->cap) cudaStreamDestroy(srv->cap);
+    cudaDeviceSynchronize();
+    delete srv;
+}
+
+}  // extern "C"

@@ -42,6 +42,9 @@ struct Fail {
 // profile.cu: launch accounting and optional event timing
 void note_launch(const char *family, int count = 1);
 void note_launch_count(int count);   // counter only; never allocates
+uint64_t launches_so_far();
+bool prof_pause();                   // stop event timing (during graph capture); returns the previous state
+void prof_resume(bool timing);
 struct ProfMark {
     cudaEvent_t a;
 };
@@ -130,7 +133,7 @@ struct Ctl {
     int32_t done;           // 1 once no column is alive
     int32_t ticket;         // last-block-done counter for the fixup reduction
     int32_t iter;           // current iteration index (written by the host-side schedule)
-    int32_t pad;
+    int32_t push;           // 1: this query chunk takes the push path for x1, x2 (decided on the device)
 };
 // Per-column state follows the Ctl header in the control buffer:
 //   int32 alive[kpad], int32 iters[kpad], double norm[kpad]
@@ -171,7 +174,9 @@ struct CpiArgs {
     float *out = nullptr;
     int64_t ldo = 1;
     int32_t *iters_out = nullptr;   // device int32[k] or nullptr
-    const int32_t *seed_outdeg = nullptr;   // host int32[k]: out-degrees of the seeds (enables the push path)
+    // host int32[k]: out-degrees of the seeds.  Given, query chunks choose
+    // their push/pull branch on the host; absent (graph capture), on the device.
+    const int32_t *seed_outdeg = nullptr;
 };
 
 // adjoint.cu
@@ -181,10 +186,18 @@ void theta_grad(const float *feat, const float *w, const float *gw, int d, int64
 double loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const int32_t *neg, int ntrip, double c,
                  int S, int T, int K, float *grad_w, cudaStream_t s);
 
-// Out-degrees of k device-resident seeds, copied to the host.
+
+// Out-degrees of k device-resident seeds, copied to the host (one small copy and a wait).
 std::vector<int32_t> seed_outdegrees(tpa_graph *g, const int32_t *d_seeds, int k, cudaStream_t s);
 
 void run_cpi(tpa_graph *g, const CpiArgs &a, cudaStream_t s);
+
+// Counter bumped by every change of a kernel setting (variant, chunk widths,
+// push path): launch sequences captured before a change are stale.
+uint64_t settings_epoch();
+
+// TPA's neighbor scale alpha (Section III-B, Lemma 2).
+double alpha_of(double c, int S, int T);
 
 // One CPI propagation step for a single vector with all scratch taken from
 // `scratch` (at least step1_scratch_bytes(n, m) bytes of device memory).

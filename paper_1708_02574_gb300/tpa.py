@@ -52,6 +52,11 @@ def library():
         "tpa_edge_weights": (i32, [P, P, i32, i64, P, P]),
         "tpa_loss_grad": (i32, [P, P, P, P, i32, f64, i32, i32, i32, ctypes.POINTER(f64), P, P]),
         "tpa_theta_grad": (i32, [P, P, P, i32, i64, P, P]),
+        "tpa_server_create": (i32, [P, i32, i32, P, i64, P, ctypes.POINTER(P)]),
+        "tpa_server_query": (i32, [P, P, i32, P]),
+        "tpa_server_result": (i32, [P, ctypes.POINTER(P), ctypes.POINTER(i64)]),
+        "tpa_server_stats": (i32, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "tpa_server_free": (None, [P]),
         "tpa_launch_count": (ctypes.c_uint64, []),
         "tpa_variant_count": (i32, []),
         "tpa_variant_info": (i32, [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -190,6 +195,46 @@ def query(g: Graph, seeds, S: int = 5, out=None):
         out = torch.empty((n, k), dtype=torch.float32, device="cuda")
     _check(library().tpa_query(g.handle, _ptr(s), int(k), int(S), _ptr(out), _stream()))
     return out
+
+
+class Server:
+    """tpa_server: request batches of up to max_k seeds answered by CUDA-graph
+    replays.  Results land in ``out`` (a CUDA float32 tensor [n, max_k], the
+    first k columns after a batch of k seeds); the graph must outlive it."""
+
+    def __init__(self, g: Graph, S: int = 5, max_k: int = 256, out=None):
+        torch = _torch()
+        n, _ = graph_info(g)
+        if out is None:
+            out = torch.empty((n, max_k), dtype=torch.float32, device="cuda")
+        assert out.dtype == torch.float32 and out.is_cuda and out.is_contiguous() and out.shape[0] == n
+        self.g, self.out, self.max_k = g, out, int(max_k)
+        self._h = ctypes.c_void_p()
+        _check(library().tpa_server_create(g.handle, int(S), int(max_k), _ptr(out), int(out.shape[1]), _stream(),
+                                           ctypes.byref(self._h)))
+
+    def query(self, seeds):
+        """Answer one batch; returns the [n, k] view of ``out`` holding its scores."""
+        s = _as_i32(seeds)
+        k = len(s)
+        _check(library().tpa_server_query(self._h, _ptr(s), int(k), _stream()))
+        return self.out[:, :k]
+
+    def stats(self, k: int = 0) -> dict:
+        gr, rp, lp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(library().tpa_server_stats(self._h, int(k), ctypes.byref(gr), ctypes.byref(rp), ctypes.byref(lp)))
+        return {"graphs": gr.value, "replays": rp.value, "launches_per_replay": lp.value}
+
+    def free(self):
+        if self._h:
+            library().tpa_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def cpi(g: Graph, seeds, c: float = 0.15, eps: float = 1e-9, s_iter: int = 0, t_iter: int = -1, out=None):
