@@ -125,3 +125,56 @@ def test_unit_weights_keep_preprocessing(problem):
     _, _, v1 = t.get_csr(g, 1)
     assert np.array_equal(v0.cpu().numpy(), v1.cpu().numpy())
     t.query(g, [1], S)    # still preprocessed
+
+
+# ---------------------------------------------------------------------------
+# Differentiation at full size: R-MAT scale 20 (1,048,576 nodes, 16,777,216 raw
+# edges, key 1), 8 features per edge ~ N(0,1) (key 4), theta ~ N(0, 0.1^2)
+# (key 5), 4,096 triples (key 6), K = 24 stranger steps.  The oracle computes
+# the first 32 triples (the loss and its gradient are sums over triples, so a
+# subset is a complete sample); the full 4,096-triple loss and gradient must
+# equal the sum of four 1,024-triple parts (linearity holds at any size).
+
+@pytest.fixture(scope="module")
+def scale20():
+    import torch
+    n = 1 << 20
+    s, d = synth.rmat_edges(20, 16)
+    og = oracle.build_graph(n, s, d)
+    g = tpa().build_graph(n, s, d)
+    feat = synth.edge_features(og.m, 8)
+    th = synth.theta(8)
+    cand = synth.nodes_with_out_edge(n, s, d)
+    seeds, pos, neg = synth.triples(n, s, d, cand, 4096)
+    fd, td = torch.from_numpy(feat).cuda(), torch.from_numpy(th).cuda()
+    w = tpa().edge_weights(fd, td)
+    tpa().set_edge_weights(g, w)
+    return dict(og=og, g=g, feat=feat, theta=th, fd=fd, w=w, seeds=seeds, pos=pos, neg=neg)
+
+
+def test_scale20_loss_grad_sampled_triples(scale20):
+    t = tpa()
+    K, sl = 24, slice(0, 32)
+    loss, gw = t.loss_grad(scale20["g"], scale20["seeds"][sl], scale20["pos"][sl], scale20["neg"][sl], C, S, T, K)
+    wd = oracle.edge_weights(scale20["theta"], scale20["feat"])
+    rloss, rgw, _, _ = oracle.loss_grad(scale20["og"], wd, scale20["seeds"][sl], scale20["pos"][sl],
+                                        scale20["neg"][sl], C, S, T, K)
+    assert abs(loss - rloss) <= 1e-5 * abs(rloss)
+    assert rel(gw.cpu().numpy(), rgw) < 1e-3, rel(gw.cpu().numpy(), rgw)
+    gth = t.theta_grad(scale20["fd"], scale20["w"], gw).cpu().numpy()
+    assert rel(gth, oracle.theta_grad(scale20["feat"], wd, rgw)) < 1e-3
+
+
+def test_scale20_loss_grad_is_a_sum_over_triples(scale20):
+    import torch
+    t = tpa()
+    K = 24
+    loss, gw = t.loss_grad(scale20["g"], scale20["seeds"], scale20["pos"], scale20["neg"], C, S, T, K)
+    parts, gsum = 0.0, torch.zeros_like(gw, dtype=torch.float64)
+    for q in range(4):
+        sl = slice(1024 * q, 1024 * (q + 1))
+        lq, gq = t.loss_grad(scale20["g"], scale20["seeds"][sl], scale20["pos"][sl], scale20["neg"][sl], C, S, T, K)
+        parts += lq
+        gsum += gq.double()
+    assert np.isfinite(loss) and abs(loss - parts) <= 1e-6 * abs(parts)
+    assert rel(gw.cpu().numpy(), gsum.cpu().numpy()) < 1e-5

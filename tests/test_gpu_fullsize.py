@@ -61,3 +61,31 @@ def test_fullsize_query_batch(full):
     for j in cols:
         ref = oracle.query(full["og"], int(seeds[j]), C, S, T, full["rs"], EPS)
         parity(out[:, j].cpu().numpy(), ref, f"scale 22 batch column {j} seed {seeds[j]}")
+
+
+# ---------------------------------------------------------------------------
+# The batched-serving graph at full size: R-MAT scale 24 (16,777,216 nodes,
+# 268,435,456 raw edges, key 1): the whole r~_stranger vector of
+# preprocessing against the oracle.
+
+SCALE24 = 24
+
+
+@pytest.fixture(scope="module")
+def full24():
+    import torch
+    import paper_1708_02574_gb300 as tpa
+    n = 1 << SCALE24
+    s, d = synth.rmat_edges(SCALE24, 16)
+    g = tpa.build_graph(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
+    tpa.preprocess(g, C, T, EPS)
+    og = oracle.build_graph(n, s, d)
+    del s, d
+    rs, it = oracle.preprocess(og, C, T, EPS)
+    return dict(n=n, g=g, og=og, rs=rs, it=it, tpa=tpa, torch=torch)
+
+
+def test_scale24_preprocess(full24):
+    r, it = full24["tpa"].get_stranger(full24["g"])
+    parity(r.cpu().numpy(), full24["rs"], "r_stranger scale 24")
+    assert abs(it - full24["it"]) <= 1
