@@ -61,6 +61,20 @@ bool is_device_ptr(const void *p)
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked host memory the device can reach (allocated
+// or registered with CUDA), else nullptr.
+void *mapped_host_ptr(void *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return attr.type == cudaMemoryTypeHost ? attr.devicePointer : nullptr;
+}
+
 void copy_in(void *dst_dev, const void *src_any, size_t bytes, cudaStream_t s)
 {
     if (bytes) TPA_CUDA(cudaMemcpyAsync(dst_dev, src_any, bytes, cudaMemcpyDefault, s));
@@ -272,11 +286,18 @@ tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *ou
     std::vector<int32_t> hs = read_seeds(seeds, k, g->n, s);
     g->ws.seeds.ensure((size_t)k * sizeof(int32_t), s);
     TPA_CUDA(cudaMemcpyAsync(g->ws.seeds.p, hs.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    // Host output: page-locked memory is written by the kernels directly (over
+    // the host link, while later chunks compute); other host memory is staged.
     const bool host_out = !is_device_ptr(out);
+    float *mapped = host_out ? static_cast<float *>(mapped_host_ptr(out)) : nullptr;
     float *dout = out;
     if (host_out) {
-        g->ws.out.ensure((size_t)g->n * k * sizeof(float), s);
-        dout = g->ws.out.as<float>();
+        if (mapped) {
+            dout = mapped;
+        } else {
+            g->ws.out.ensure((size_t)g->n * k * sizeof(float), s);
+            dout = g->ws.out.as<float>();
+        }
     }
     CpiArgs a;
     a.seeds = g->ws.seeds.as<int32_t>();
@@ -295,7 +316,8 @@ tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *ou
     a.seed_outdeg = od.data();
     run_cpi(g, a, s);
     if (host_out) {
-        TPA_CUDA(cudaMemcpyAsync(out, dout, (size_t)g->n * k * sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (!mapped)
+            TPA_CUDA(cudaMemcpyAsync(out, dout, (size_t)g->n * k * sizeof(float), cudaMemcpyDeviceToHost, s));
         TPA_CUDA(cudaStreamSynchronize(s));
     }
     API_END

@@ -236,13 +236,26 @@ __device__ __forceinline__ void epilogue(const Params &p, int64_t row, int col0,
         }
     } else {
         const float rs = p.r_str[row];
+        float fam[V], o[V];
+        if (p.ldr == KP && V > 1) {
+            ld_row_rw<V>(p.r + row * KP + col0, fam);
+        } else {
 #pragma unroll
-        for (int j = 0; j < V; ++j)
-            if (col0 + j < p.k) {
-                float fam = p.r[row * p.ldr + col0 + j];
-                if (alive[j]) fam += yv[j];
-                p.out[row * p.ldo + col0 + j] = fmaf(p.one_plus_alpha, fam, rs);
-            }
+            for (int j = 0; j < V; ++j) fam[j] = col0 + j < p.k ? p.r[row * p.ldr + col0 + j] : 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < V; ++j) o[j] = fmaf(p.one_plus_alpha, alive[j] ? fam[j] + yv[j] : fam[j], rs);
+        float *dst = p.out + row * p.ldo + col0;
+        bool vec = false;
+        if constexpr (V == 4 || V == 8)   // whole aligned rows go as 16-byte stores (fewer host-link writes)
+            vec = col0 + V <= p.k && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+        if (vec) {
+            st_row<V>(dst, o);
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+                if (col0 + j < p.k) dst[j] = o[j];
+        }
     }
 #pragma unroll
     for (int j = 0; j < V; ++j) l1[j] += alive[j] ? fabsf(yv[j]) : 0.0f;

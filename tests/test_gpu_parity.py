@@ -161,6 +161,17 @@ def test_host_buffers_through_c_abi(rmat14):
     assert np.array_equal(out, dev)
 
 
+def test_pinned_host_output_written_directly(rmat14):
+    """Page-locked host output: the kernels write the scores straight into it."""
+    import torch
+    t = tpa()
+    seeds = synth.query_seeds(rmat14["cand"], 13, key=14)
+    out = torch.empty((rmat14["n"], 13), dtype=torch.float32).pin_memory()
+    t.query(rmat14["g"], seeds, S, out=out)
+    dev = t.query(rmat14["g"], seeds, S).cpu()
+    assert torch.equal(out, dev)
+
+
 def test_deterministic(rmat14):
     seeds = synth.query_seeds(rmat14["cand"], 32, key=4)
     a = tpa().query(rmat14["g"], seeds, S).cpu().numpy()
