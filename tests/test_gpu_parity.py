@@ -161,12 +161,13 @@ def test_host_buffers_through_c_abi(rmat14):
     assert np.array_equal(out, dev)
 
 
-def test_pinned_host_output_written_directly(rmat14):
+@pytest.mark.parametrize("k", [13, 150])
+def test_pinned_host_output(rmat14, k):
     """Page-locked host output: the kernels write the scores straight into it."""
     import torch
     t = tpa()
-    seeds = synth.query_seeds(rmat14["cand"], 13, key=14)
-    out = torch.empty((rmat14["n"], 13), dtype=torch.float32).pin_memory()
+    seeds = synth.query_seeds(rmat14["cand"], k, key=14)
+    out = torch.full((rmat14["n"], k), -1.0, dtype=torch.float32).pin_memory()
     t.query(rmat14["g"], seeds, S, out=out)
     dev = t.query(rmat14["g"], seeds, S).cpu()
     assert torch.equal(out, dev)
