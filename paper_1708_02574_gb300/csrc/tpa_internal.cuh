@@ -94,7 +94,7 @@ struct Workspace {
     DevBuf iters;           // int32 per-column iteration counts
     DevBuf u;               // push path: 64-bit fixed-point accumulator [n][KP]
     DevBuf touched;         // push path: one bit per row reached by the push
-    DevBuf x2;              // push path: x2 [n][KP <= 8], zero outside the marked rows
+    DevBuf x2;              // push path: x2 [n][KP <= 16], zero outside the marked rows
     bool u_clean = false;   // u, touched and x2 are known to be all zero
     int32_t *hflag = nullptr;   // pinned host mirror of the done flag (2 slots)
 };
