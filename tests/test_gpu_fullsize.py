@@ -89,3 +89,95 @@ def test_scale24_preprocess(full24):
     r, it = full24["tpa"].get_stranger(full24["g"])
     parity(r.cpu().numpy(), full24["rs"], "r_stranger scale 24")
     assert abs(it - full24["it"]) <= 1
+
+
+# ---------------------------------------------------------------------------
+# Billion-edge graph: R-MAT scale 26, edge factor 28 (67,108,864 nodes,
+# 1,879,048,192 raw edges, key 1), preprocessing and one batch of 64 queries
+# (seeds uniform over nodes with an out-edge, key 2).  The FP64 oracle cannot
+# run at this size, so the checks are properties that hold at any size:
+# CSR invariants and sampled rows against the raw edge list, bounds of
+# Lemma 2 / Theorem 2 on r~_stranger and r_TPA, push against pull branch, and
+# batched against single-seed queries.
+
+SCALE26, EF26, SEEDS26 = 26, 28, 64
+
+
+@pytest.fixture(scope="module")
+def big26():
+    import torch
+    import paper_1708_02574_gb300 as tpa
+    n = 1 << SCALE26
+    torch.cuda.empty_cache()
+    s, d = synth.rmat_edges(SCALE26, EF26)
+    g = tpa.build_graph(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
+    torch.cuda.empty_cache()
+    tpa.preprocess(g, C, T, EPS)
+    cand = synth.nodes_with_out_edge(n, s, d)
+    seeds = synth.query_seeds(cand, SEEDS26)
+    return dict(n=n, s=s, d=d, g=g, seeds=seeds, tpa=tpa, torch=torch)
+
+
+def test_scale26_csr_invariants(big26):
+    tpa, torch = big26["tpa"], big26["torch"]
+    g, n = big26["g"], big26["n"]
+    rp_t, col_t, val_t = tpa.get_csr(g, 0)
+    rp_a, _, _ = tpa.get_csr(g, 1)
+    m = g.m
+    assert m > 10 ** 9 and int(rp_t[-1]) == m and int(rp_a[-1]) == m
+    assert bool((rp_t[1:] >= rp_t[:-1]).all()) and bool((rp_a[1:] >= rp_a[:-1]).all())
+    assert int(col_t.min()) >= 0 and int(col_t.max()) < n
+    outdeg = (rp_a[1:] - rp_a[:-1]).to(torch.float64)
+    # val = RN32(1 / outdeg(source)) on every edge of CSR(A~^T), in slices
+    step = 1 << 27
+    for e0 in range(0, m, step):
+        c = col_t[e0:e0 + step].long()
+        assert torch.equal(val_t[e0:e0 + step], (1.0 / outdeg[c]).to(torch.float32)), e0
+    del c
+    # sampled destination rows: strictly increasing sources, no self-loop, and
+    # exactly the distinct sources of the raw edges into that row
+    rng = np.random.default_rng(26)
+    rows = [0, 1] + [int(r) for r in rng.integers(0, n, 2)]
+    s, d = big26["s"], big26["d"]
+    rp = rp_t.cpu().numpy()
+    for v in rows:
+        got = col_t[int(rp[v]):int(rp[v + 1])].cpu().numpy()
+        assert np.all(np.diff(got) > 0) and not np.any(got == v)
+        raw = s[d == v]
+        assert np.array_equal(got, np.unique(raw[raw != v])), v
+
+
+def test_scale26_preprocess_bounds(big26):
+    tpa = big26["tpa"]
+    r, it = tpa.get_stranger(big26["g"])
+    assert bool((r >= 0).all())
+    mass = float(r.double().sum())
+    assert 0.0 < mass <= (1 - C) ** T + 1e-6       # Lemma 2 with mass lost at deadends
+    assert 0 < it <= 130
+
+
+def test_scale26_batched_queries(big26):
+    tpa, torch = big26["tpa"], big26["torch"]
+    g, seeds = big26["g"], big26["seeds"]
+    r_str, _ = tpa.get_stranger(g)
+    out = tpa.query(g, seeds, S)
+    alpha = ((1 - C) ** S - (1 - C) ** T) / (1 - (1 - C) ** S)
+    own = out[torch.from_numpy(seeds).long().cuda(), torch.arange(len(seeds), device="cuda")]
+    assert bool((own >= (1 + alpha) * C - 1e-6).all())               # x0 = c e_s alone
+    for j0 in range(0, len(seeds), 8):                                # column blocks bound the memory
+        blk = out[:, j0:j0 + 8]
+        assert bool((blk >= 0).all())
+        assert bool((blk.double().sum(0) <= 1.0 + 1e-5).all())
+        assert bool((blk >= r_str[:, None] - 1e-7).all())            # the family part is non-negative
+    try:
+        tpa.set_push(False)
+        pulled = tpa.query(g, seeds, S)
+    finally:
+        tpa.set_push(True)
+    for j0 in range(0, len(seeds), 8):
+        diff = (out[:, j0:j0 + 8].double() - pulled[:, j0:j0 + 8].double()).abs()
+        assert float(diff.sum(0).max()) <= 1e-5 and float(diff.max()) <= 1e-7, j0
+    del pulled, diff
+    one = tpa.query(g, seeds[5:6], S)
+    d1 = (one[:, 0].double() - out[:, 5].double()).abs()
+    assert float(d1.sum()) <= 1e-5 and float(d1.max()) <= 1e-7
