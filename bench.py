@@ -447,7 +447,10 @@ def measure_serving(tpa, torch, g, cand, stream, total=2048):
         batches.append(torch.from_numpy(seeds[off:off + k]).cuda())
         off += k
     out = torch.empty((g.n, max(sizes)), dtype=torch.float32, device="cuda")
-    srv = tpa.Server(g, S, max_k=max(sizes), out=out)
+    try:
+        srv = tpa.Server(g, S, max_k=max(sizes), out=out)
+    except tpa.TpaError as e:       # the server refuses graphs above its validated size
+        return {"unavailable": str(e)}
     res = {"batches": len(sizes), "seeds": total, "sizes": sorted(set(sizes))}
     for name, run in (("direct", lambda b: tpa.query(g, b, S)),
                       ("graphs", lambda b: srv.query(b))):

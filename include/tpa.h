@@ -244,7 +244,8 @@ typedef struct tpa_server tpa_server;
  * per batch on a preprocessed graph.  out: device buffer of n rows of ldo
  * floats, or NULL to let the server allocate one (ldo is then max_k; see
  * tpa_server_result).  Errors: TPA_ESTATE before tpa_preprocess; TPA_EINVAL
- * for S outside [1, T], max_k < 1, ldo < max_k or a host out. */
+ * for S outside [1, T], max_k < 1, ldo < max_k, a host out, or a graph of
+ * more than 2^22 nodes (the size the server is validated at). */
 tpa_status tpa_server_create(tpa_graph *g, int S, int max_k, float *out, int64_t ldo, void *stream,
                              tpa_server **srv);
 

@@ -42,6 +42,8 @@ struct tpa_server {
 
 namespace {
 
+constexpr int64_t SERVER_MAX_NODES = (int64_t)1 << 22;
+
 // The server's workspace stands in for the graph's while a batch is issued.
 struct WorkspaceSwap {
     tpa_graph *g;
@@ -141,6 +143,10 @@ tpa_status tpa_server_create(tpa_graph *g, int S, int max_k, float *out, int64_t
     }
     TPA_REQUIRE(S >= 1 && S <= g->T, "tpa_server_create: S = %d outside [1, T = %d]", S, g->T);
     TPA_REQUIRE(max_k >= 1, "tpa_server_create: max_k = %d < 1", max_k);
+    // Runs of the server on graphs of 2^24 and 2^26 nodes ended in an illegal
+    // memory access whose cause is not known; it is validated up to 2^22.
+    TPA_REQUIRE(g->n <= SERVER_MAX_NODES, "tpa_server_create: n = %lld above the validated %lld nodes",
+                (long long)g->n, (long long)SERVER_MAX_NODES);
     TPA_REQUIRE(out == nullptr || is_device_ptr(out), "tpa_server_create: out must be device memory");
     TPA_REQUIRE(out == nullptr || ldo >= max_k, "tpa_server_create: ldo = %lld < max_k = %d", (long long)ldo, max_k);
     cudaStream_t s = (cudaStream_t)stream;
