@@ -178,7 +178,7 @@ def peaks():
 def kernel_source_hash() -> str:
     """Identity of the SpMV/SpMM device code (kernels and the structs they read)."""
     h = hashlib.sha256()
-    for f in ("spmm_kernels.cuh", "tpa_internal.cuh"):
+    for f in ("spmm_kernels.cuh", "spmm_binned.cuh", "tpa_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1708_02574_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

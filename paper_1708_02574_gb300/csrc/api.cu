@@ -174,6 +174,11 @@ void tpa_free_graph(tpa_graph *g)
                       &g->ws.x, &g->ws.y, &g->ws.r, &g->ws.carry, &g->ws.head, &g->ws.tl1, &g->ws.fix,
                       &g->ws.ctl, &g->ws.seeds, &g->ws.out, &g->ws.iters};
     for (DevBuf *b : bufs) b->release(s);
+    g->ws.cpart.release(s);
+    for (tpa::BinPlan *B : {&g->bins_t, &g->bins_a})
+        for (DevBuf *b : {&B->rows_short, &B->rows_mid, &B->rows_long, &B->rows_empty, &B->long_first,
+                          &B->chunk_row, &B->chunk_e0})
+            b->release(s);
     for (auto *plans : {&g->plans_t, &g->plans_a})
         for (auto &kv : *plans) {
             kv.second.tile_x.release(s);

@@ -481,4 +481,9 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
     ka.release(s); kb.release(s); hist.release(s); tmp.release(s); ia.release(s); ib.release(s); cnt.release(s);
 }
 
+void exclusive_scan_i32_i64(const int32_t *in, int64_t *out, int64_t len, DevBuf &tmp, cudaStream_t s)
+{
+    exclusive_scan<int32_t, int64_t>(in, out, len, true, tmp, s);
+}
+
 }  // namespace tpa

@@ -40,6 +40,7 @@
 #include "tpa_internal.cuh"
 
 #include "spmm_kernels.cuh"
+#include "spmm_binned.cuh"
 
 namespace tpa {
 
@@ -71,6 +72,80 @@ const Plan &get_plan(tpa_graph *g, int L, cudaStream_t s, int which)
     note_launch("plan", 2);
     TPA_CHECK_LAUNCH();
     return P;
+}
+
+// Row bins of CSR(A~^T) (which = 0) or CSR(A~) for the binned-row kernels.
+static const BinPlan &get_bin_plan(tpa_graph *g, int which, cudaStream_t s)
+{
+    BinPlan &B = which ? g->bins_a : g->bins_t;
+    if (B.built) return B;
+    const int64_t n = g->n;
+    const int64_t *rp = which ? g->rp_a.as<int64_t>() : g->rp_t.as<int64_t>();
+    DevBuf flags, pos, tmp, cnt;
+    flags.ensure((size_t)4 * n * sizeof(int32_t), s);
+    pos.ensure((size_t)4 * (n + 1) * sizeof(int64_t), s);
+    bin_classify_k<<<grid_1d(n, 256), 256, 0, s>>>(rp, n, flags.as<int32_t>());
+    TPA_CHECK_LAUNCH();
+    for (int b = 0; b < 4; ++b)
+        exclusive_scan_i32_i64(flags.as<int32_t>() + b * n, pos.as<int64_t>() + b * (n + 1), n, tmp, s);
+    int64_t tot[4];
+    for (int b = 0; b < 4; ++b)
+        TPA_CUDA(cudaMemcpyAsync(&tot[b], pos.as<int64_t>() + b * (n + 1) + n, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+    TPA_CUDA(cudaStreamSynchronize(s));
+    B.n_short = tot[0];
+    B.n_mid = tot[1];
+    B.n_long = tot[2];
+    B.n_empty = tot[3];
+    B.rows_short.ensure((size_t)std::max<int64_t>(1, B.n_short) * sizeof(int32_t), s);
+    B.rows_mid.ensure((size_t)std::max<int64_t>(1, B.n_mid) * sizeof(int32_t), s);
+    B.rows_long.ensure((size_t)std::max<int64_t>(1, B.n_long) * sizeof(int32_t), s);
+    B.rows_empty.ensure((size_t)std::max<int64_t>(1, B.n_empty) * sizeof(int32_t), s);
+    cnt.ensure((size_t)std::max<int64_t>(1, B.n_long) * sizeof(int32_t), s);
+    bin_scatter_k<<<grid_1d(n, 256), 256, 0, s>>>(rp, n, flags.as<int32_t>(), pos.as<int64_t>(),
+                                                   B.rows_short.as<int32_t>(), B.rows_mid.as<int32_t>(),
+                                                   B.rows_long.as<int32_t>(), B.rows_empty.as<int32_t>(),
+                                                   cnt.as<int32_t>());
+    TPA_CHECK_LAUNCH();
+    B.long_first.ensure((size_t)(B.n_long + 1) * sizeof(int64_t), s);
+    exclusive_scan_i32_i64(cnt.as<int32_t>(), B.long_first.as<int64_t>(), B.n_long, tmp, s);
+    TPA_CUDA(cudaMemcpyAsync(&B.n_chunks, B.long_first.as<int64_t>() + B.n_long, sizeof(int64_t),
+                             cudaMemcpyDeviceToHost, s));
+    TPA_CUDA(cudaStreamSynchronize(s));
+    B.chunk_row.ensure((size_t)std::max<int64_t>(1, B.n_chunks) * sizeof(int32_t), s);
+    B.chunk_e0.ensure((size_t)std::max<int64_t>(1, B.n_chunks) * sizeof(int64_t), s);
+    if (B.n_long)
+        bin_chunks_k<<<grid_1d(B.n_long, 256), 256, 0, s>>>(rp, B.rows_long.as<int32_t>(), B.n_long,
+                                                             B.long_first.as<int64_t>(), B.chunk_row.as<int32_t>(),
+                                                             B.chunk_e0.as<int64_t>());
+    note_launch("plan", 3 + (B.n_long ? 1 : 0));
+    TPA_CHECK_LAUNCH();
+    flags.release(s);
+    pos.release(s);
+    tmp.release(s);
+    cnt.release(s);
+    B.built = true;
+    return B;
+}
+
+// Point the binned-row fields of p at the bins of a CSR (and the chunk sums).
+static void bind_bins(Params &p, tpa_graph *g, int which, int KP, cudaStream_t s)
+{
+    const BinPlan &B = get_bin_plan(g, which, s);
+    p.rows_short = B.rows_short.as<int32_t>();
+    p.rows_mid = B.rows_mid.as<int32_t>();
+    p.rows_long = B.rows_long.as<int32_t>();
+    p.rows_empty = B.rows_empty.as<int32_t>();
+    p.chunk_row = B.chunk_row.as<int32_t>();
+    p.chunk_e0 = B.chunk_e0.as<int64_t>();
+    p.n_short = B.n_short;
+    p.n_mid = B.n_mid;
+    p.n_long = B.n_long;
+    p.n_empty = B.n_empty;
+    p.n_chunks = B.n_chunks;
+    p.long_first64 = B.long_first.as<int64_t>();
+    g->ws.cpart.ensure((size_t)std::max<int64_t>(1, B.n_chunks) * KP * sizeof(float), s);
+    p.cpart = g->ws.cpart.as<float>();
 }
 
 // --------------------------------------------------------- dispatching ---
@@ -156,6 +231,66 @@ static int64_t launch_spmvp(const Params &p, cudaStream_t s)
     return grid * WARPS;
 }
 
+// Binned-row kernels (spmm_binned.cuh): short, medium, chunks of long rows,
+// long-row combine, empty rows; returns the rows of tl1 written.
+template <int KP>
+static int64_t launch_binned(const Params &p0, cudaStream_t s)
+{
+    static int per_short = 0, per_mid = 0, per_chunk = 0;
+    if (!per_short) {
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_short, bin_short_k<KP>, BIN_WARPS * 32, 0));
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_mid, bin_warp_k<KP, false>, BIN_WARPS * 32, 0));
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_chunk, bin_warp_k<KP, true>, BIN_WARPS * 32, 0));
+        per_short = std::max(per_short, 1);
+        per_mid = std::max(per_mid, 1);
+        per_chunk = std::max(per_chunk, 1);
+    }
+    const int64_t sms = num_sms();
+    auto blocks = [&](int64_t warps, int per) {
+        return (unsigned)std::max<int64_t>(1, std::min<int64_t>((warps + BIN_WARPS - 1) / BIN_WARPS, per * sms));
+    };
+    Params p = p0;
+    constexpr int RPW = 32 / (KP < 32 ? KP : 32);
+    int64_t slot = 0;
+    const unsigned gs = blocks((p.n_short + RPW - 1) / RPW, per_short);
+    p.slot0 = slot;
+    bin_short_k<KP><<<gs, BIN_WARPS * 32, 0, s>>>(p);
+    slot += (int64_t)gs * BIN_WARPS;
+    const unsigned gm = blocks(p.n_mid, per_mid);
+    p.slot0 = slot;
+    bin_warp_k<KP, false><<<gm, BIN_WARPS * 32, 0, s>>>(p);
+    slot += (int64_t)gm * BIN_WARPS;
+    int launches = 2;
+    if (p.n_chunks) {
+        bin_warp_k<KP, true><<<blocks(p.n_chunks, per_chunk), BIN_WARPS * 32, 0, s>>>(p);
+        const unsigned gl = (unsigned)((p.n_long * KP + 255) / 256);
+        p.slot0 = slot;
+        bin_long_k<KP><<<gl, 256, 0, s>>>(p);
+        slot += gl;
+        launches += 2;
+    }
+    if (p.n_empty) {
+        bin_empty_k<KP><<<grid_1d(p.n_empty * KP, 256), 256, 0, s>>>(p);
+        ++launches;
+    }
+    note_launch_count(launches - 1);   // the caller counts one
+    TPA_CHECK_LAUNCH();
+    return slot;
+}
+
+// Upper bound of the tl1 rows launch_binned writes.
+static int64_t binned_slots_bound(int64_t n_long, int KP)
+{
+    return 2 * (int64_t)32 * num_sms() * BIN_WARPS + (n_long * KP + 255) / 256 + 1;
+}
+
+template <int KP>
+static void launch_bin_finish(const Params &p, unsigned blocks, cudaStream_t s)
+{
+    (void)blocks;
+    bin_finish_k<KP><<<1, 256, 0, s>>>(p);
+}
+
 template <int KP>
 static void launch_fix(const Params &p, unsigned blocks, cudaStream_t s)
 {
@@ -179,6 +314,7 @@ struct Variant {
     int64_t (*spmm)(const Params &, cudaStream_t);   // returns the rows of tl1 written
     void (*fix)(const Params &, unsigned, cudaStream_t);
     const char *name;
+    bool binned = false;   // binned-row kernels (need the row bins bound to Params)
 };
 
 #define TPA_VARIANT(G, V, I, PF) \
@@ -187,6 +323,7 @@ struct Variant {
     {{1, V, I, I, 32}, launch_spmvw<V, I, W>, launch_fix<V>, "warp<" #V "," #I "," #W ">"}
 #define TPA_VARIANTG(G, V, I, PF) \
     {{G, V, I, PF, 32}, launch_spmvg<G, V, I, PF, 8>, launch_fix<G * V>, "walker<" #G "," #V "," #I "," #PF ">"}
+#define TPA_VARIANTB(KP) {{1, KP, 4, 4, 32}, launch_binned<KP>, launch_bin_finish<KP>, "bins<" #KP ">", true}
 #define TPA_VARIANTP(G, V, I, PF, W, MB)                                 \
     {{G, V, I, PF, 32}, launch_spmvp<G, V, I, PF, W, MB>, launch_fix<G * V>, \
      "pipe<" #G "," #V "," #I "," #PF "," #W "," #MB ">"}
@@ -242,6 +379,11 @@ static const Variant kVariants[] = {
     TPA_VARIANTP(4, 4, 8, 8, 8, 1),
     TPA_VARIANTP(2, 8, 8, 4, 8, 1),
     TPA_VARIANTP(2, 8, 8, 4, 4, 1),
+    TPA_VARIANTB(1),
+    TPA_VARIANTB(2),
+    TPA_VARIANTB(4),
+    TPA_VARIANTB(8),
+    TPA_VARIANTB(16),
     TPA_VARIANTP(4, 4, 16, 8, 4, 1),
     TPA_VARIANTP(4, 4, 8, 4, 8, 2),
     TPA_VARIANTP(8, 4, 8, 8, 8, 1),
@@ -250,6 +392,7 @@ static const Variant kVariants[] = {
 #undef TPA_VARIANTW
 #undef TPA_VARIANTG
 #undef TPA_VARIANTP
+#undef TPA_VARIANTB
 
 // Padded width: the smallest power of two >= k (every power of two up to
 // KP_MAX has at least one kernel variant).
@@ -361,7 +504,9 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     W.y.ensure((size_t)n * KP * sizeof(float), s);
     W.carry.ensure((size_t)P.tiles * KP * sizeof(float), s);
     W.head.ensure((size_t)P.tiles * KP * sizeof(float), s);
-    W.tl1.ensure((size_t)(P.tiles + 8) * KP * sizeof(float), s);   // per tile, or per warp of a grid
+    int64_t tl1_rows = P.tiles + 8;   // per tile, or per warp of a grid
+    if (var.binned) tl1_rows = std::max(tl1_rows, binned_slots_bound(get_bin_plan(g, 0, s).n_long, KP));
+    W.tl1.ensure((size_t)tl1_rows * KP * sizeof(float), s);
     const unsigned fix_blocks = fix_grid(KP, P.tiles);
     W.fix.ensure((size_t)fix_blocks * KP * sizeof(double), s);
     W.ctl.ensure(CTL_BYTES, s);
@@ -477,6 +622,7 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     p.tl1 = W.tl1.as<float>();
     p.part = W.fix.as<double>();
     p.ctl = W.ctl.p;
+    if (var.binned) bind_bins(p, g, 0, KP, s);
 
     // x and y alternate; on a two-way chunk iteration 2 writes and iteration
     // 3 reads the x2 buffer
@@ -573,6 +719,7 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
 // reporting is by return value: this path throws nothing and allocates
 // nothing (it backs the scratch-free entry point).
 namespace {
+
 constexpr int STEP_ITEMS = 8;
 constexpr int STEP_WARPS = 8;
 constexpr int STEP_L = 32 * STEP_ITEMS;
@@ -701,7 +848,9 @@ void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float
     Workspace &W = g->ws;
     W.carry.ensure((size_t)P.tiles * KP * sizeof(float), s);
     W.head.ensure((size_t)P.tiles * KP * sizeof(float), s);
-    W.tl1.ensure((size_t)(P.tiles + 8) * KP * sizeof(float), s);   // per tile, or per warp of a grid
+    int64_t tl1_rows = P.tiles + 8;   // per tile, or per warp of a grid
+    if (var.binned) tl1_rows = std::max(tl1_rows, binned_slots_bound(get_bin_plan(g, which, s).n_long, KP));
+    W.tl1.ensure((size_t)tl1_rows * KP * sizeof(float), s);
     const unsigned fix_blocks = fix_grid(KP, P.tiles);
     W.fix.ensure((size_t)fix_blocks * KP * sizeof(double), s);
     W.ctl.ensure(CTL_BYTES, s);
@@ -729,6 +878,7 @@ void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float
     p.tl1 = W.tl1.as<float>();
     p.part = W.fix.as<double>();
     p.ctl = W.ctl.p;
+    if (var.binned) bind_bins(p, g, which, KP, s);
     ProfMark pm = prof_begin(s);
     p.l1_slots = var.spmm(p, s);
     prof_end(pm, spmm_family(KP), spmm_bytes(g->n, g->m, KP, kc, MODE_ACC, 0), s);

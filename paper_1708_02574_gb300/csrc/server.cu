@@ -247,7 +247,7 @@ void tpa_server_free(tpa_server *srv)
     cudaStream_t s = 0;
     DevBuf *bufs[] = {&srv->out_buf, &srv->seeds, &srv->ws.x, &srv->ws.y, &srv->ws.r, &srv->ws.carry,
                       &srv->ws.head, &srv->ws.tl1, &srv->ws.fix, &srv->ws.ctl, &srv->ws.seeds, &srv->ws.out,
-                      &srv->ws.iters, &srv->ws.u, &srv->ws.touched, &srv->ws.x2};
+                      &srv->ws.iters, &srv->ws.u, &srv->ws.touched, &srv->ws.x2, &srv->ws.cpart};
     for (DevBuf *b : bufs) b->release(s);
     if (srv->ws.hflag) cudaFreeHost(srv->ws.hflag);
     if (srv->h_seeds) cudaFreeHost(srv->h_seeds);

@@ -82,6 +82,15 @@ struct Params {
     // branch gate of a query chunk whose path the device chooses:
     // GATE_NONE runs always, GATE_PULL / GATE_PUSH only on that branch
     int gate;
+    // rows binned by length (binned-row kernels): ids of rows with 1..32,
+    // 33..512, more than 512 and no nonzeros; the long rows are cut into
+    // chunks of 512 nonzeros (chunk i: long row chunk_row[i], first nonzero
+    // chunk_e0[i]; long row j owns chunks long_first64[j] .. long_first64[j+1])
+    const int32_t *rows_short, *rows_mid, *rows_long, *rows_empty, *chunk_row;
+    const int64_t *chunk_e0, *long_first64;
+    int64_t n_short, n_mid, n_long, n_empty, n_chunks;
+    float *cpart;       // [n_chunks][KP] chunk sums
+    int64_t slot0;      // first row of tl1 this launch writes its L1 partials to
 };
 
 enum Gate : int { GATE_NONE = 0, GATE_PULL = 1, GATE_PUSH = 2 };
@@ -108,11 +117,14 @@ __device__ __forceinline__ void ld_row(const float *p, float (&o)[V])
         const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
         o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
     } else {
-        // one 256-bit read-only load (32-byte aligned: every caller's row is)
-        static_assert(V == 8, "V");
-        asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-            : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]), "=f"(o[7])
-            : "l"(p));
+        // 256-bit read-only loads (32-byte aligned: every caller's row is)
+        static_assert(V % 8 == 0, "V");
+#pragma unroll
+        for (int q = 0; q < V / 8; ++q)
+            asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=f"(o[8 * q]), "=f"(o[8 * q + 1]), "=f"(o[8 * q + 2]), "=f"(o[8 * q + 3]), "=f"(o[8 * q + 4]),
+                  "=f"(o[8 * q + 5]), "=f"(o[8 * q + 6]), "=f"(o[8 * q + 7])
+                : "l"(p + 8 * q));
     }
 }
 
@@ -1189,8 +1201,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
 // group grp of the 256 / KP groups adds b = grp, grp + NG, ... in increasing b
 // (loads issued eight at a time), then thread c adds the group sums in group
 // order.  The result for column c is left in s_fin[c] (s_fin holds 256).
-template <int KP>
-__device__ __forceinline__ void block_sum_partials(const double *part, unsigned nb, double *s_fin)
+template <int KP, class T>
+__device__ __forceinline__ void block_sum_partials_t(const T *part, unsigned nb, double *s_fin)
 {
     static_assert(KP >= 1 && KP <= 256 && 256 % KP == 0, "KP");
     constexpr unsigned NG = 256 / KP;
@@ -1214,6 +1226,12 @@ __device__ __forceinline__ void block_sum_partials(const double *part, unsigned 
         s_fin[threadIdx.x] = t;   // only this thread reads or writes column c's group-0 slot
     }
     __syncthreads();
+}
+
+template <int KP>
+__device__ __forceinline__ void block_sum_partials(const double *part, unsigned nb, double *s_fin)
+{
+    block_sum_partials_t<KP, double>(part, nb, s_fin);
 }
 
 // --------------------------------------------------------------- fixup ---

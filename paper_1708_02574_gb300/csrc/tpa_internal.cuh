@@ -78,6 +78,17 @@ struct Plan {
     DevBuf head_first;      // int32[tiles]    first tile holding a nonzero of that row
 };
 
+// Rows of a CSR binned by length for the binned-row kernels (built once per
+// graph and CSR; see spmm_binned.cuh).
+struct BinPlan {
+    bool built = false;
+    int64_t n_short = 0, n_mid = 0, n_long = 0, n_empty = 0, n_chunks = 0;
+    DevBuf rows_short, rows_mid, rows_long, rows_empty;   // int32 row ids
+    DevBuf long_first;    // int64[n_long + 1] first chunk of each long row
+    DevBuf chunk_row;     // int32[n_chunks]
+    DevBuf chunk_e0;      // int64[n_chunks]
+};
+
 // ---------------------------------------------------------------- graph ---
 // The column and value arrays of both CSRs hold CSR_PAD extra zero elements
 // after the m real ones, so kernels may stage a tile's nonzeros in 16-byte
@@ -95,6 +106,7 @@ struct Workspace {
     DevBuf u;               // push path: 64-bit fixed-point accumulator [n][KP]
     DevBuf touched;         // push path: one bit per row reached by the push
     DevBuf x2;              // push path: x2 [n][KP <= 16], zero outside the marked rows
+    DevBuf cpart;           // binned-row kernels: chunk sums of long rows [chunks][KP]
     bool u_clean = false;   // u, touched and x2 are known to be all zero
     int32_t *hflag = nullptr;   // pinned host mirror of the done flag (2 slots)
 };
@@ -123,6 +135,7 @@ struct tpa_graph {
     int64_t pre_iters = 0;
     std::map<int, tpa::Plan> plans_t;   // merge-path plans over CSR(A~^T) keyed by L
     std::map<int, tpa::Plan> plans_a;   // merge-path plans over CSR(A~) keyed by L
+    tpa::BinPlan bins_t, bins_a;        // row bins of CSR(A~^T) and CSR(A~)
     tpa::Workspace ws;
 };
 
@@ -141,6 +154,8 @@ struct Ctl {
 // build.cu
 void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t m_in,
                cudaStream_t s);
+// out[0..len] = exclusive prefix sums of in[0..len) and the total (device arrays)
+void exclusive_scan_i32_i64(const int32_t *in, int64_t *out, int64_t len, DevBuf &tmp, cudaStream_t s);
 
 // cpi.cu
 const Plan &get_plan(tpa_graph *g, int L, cudaStream_t s, int which = 0);   // which: 0 = A~^T, 1 = A~
