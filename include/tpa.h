@@ -237,7 +237,9 @@ tpa_status tpa_set_push(int enable);
  * the graph, and calls on one server must not overlap.  Results equal those
  * of tpa_query with the same settings bit for bit.  A change of a kernel
  * setting (tpa_set_variant, tpa_set_batch_width, tpa_set_push) makes the
- * server capture again. */
+ * server capture again, and so does a batch that needs more workspace than
+ * any before it (its buffers are reallocated, and graphs captured over the
+ * old ones are dropped, never replayed). */
 typedef struct tpa_server tpa_server;
 
 /* Create a server for queries with S family steps and at most max_k seeds
@@ -258,10 +260,11 @@ tpa_status tpa_server_query(tpa_server *srv, const int32_t *seeds, int k, void *
 /* The output buffer and its row stride. */
 tpa_status tpa_server_result(const tpa_server *srv, float **out, int64_t *ldo);
 
-/* Graphs captured so far, graph replays, and kernel launches per replay of
- * the graph for batch size k (0 if none). */
+/* Graphs held now, graph replays, kernel launches per replay of the graph
+ * for batch size k (0 if none), and captures so far (every batch is either
+ * a replay or a direct run followed by a capture).  NULL outputs are skipped. */
 tpa_status tpa_server_stats(const tpa_server *srv, int k, int64_t *graphs, int64_t *replays,
-                            int64_t *launches_per_replay);
+                            int64_t *launches_per_replay, int64_t *captures);
 
 /* Release the server (waits for its work). */
 void tpa_server_free(tpa_server *srv);

@@ -13,8 +13,10 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <cstring>
 #include <map>
 #include <utility>
+#include <vector>
 
 #include "tpa_internal.cuh"
 
@@ -34,10 +36,12 @@ struct tpa_server {
     struct Entry {
         cudaGraphExec_t exec = nullptr;
         int64_t launches = 0;
+        std::vector<uint64_t> ident;   // what the graph refers to (see identity())
     };
     std::map<int, Entry> graphs;
     uint64_t epoch = 0;
     int64_t replays = 0;
+    int64_t captures = 0;
 };
 
 namespace {
@@ -71,6 +75,46 @@ void issue_batch(tpa_server *srv, int k, cudaStream_t s)
     run_cpi(g, a, s);
 }
 
+// Everything a captured batch refers to besides the server's seed and output
+// buffers: the device addresses of the workspace in use (a workspace buffer
+// that has to grow for a larger batch is reallocated), of the graph's arrays,
+// plans and row bins, and the graph's scalars.  A graph captured under another
+// identity would touch freed memory, so it is never replayed.
+std::vector<uint64_t> identity(const tpa_graph *g)
+{
+    std::vector<uint64_t> v;
+    auto addr = [&v](const DevBuf &b) {
+        v.push_back((uint64_t)(uintptr_t)b.p);
+        v.push_back((uint64_t)b.bytes);
+    };
+    const Workspace &w = g->ws;
+    for (const DevBuf *b : {&w.x, &w.y, &w.r, &w.carry, &w.head, &w.tl1, &w.fix, &w.ctl, &w.seeds, &w.out, &w.iters,
+                            &w.u, &w.touched, &w.x2, &w.cpart})
+        addr(*b);
+    v.push_back((uint64_t)(uintptr_t)w.hflag);
+    for (const DevBuf *b : {&g->rp_t, &g->col_t, &g->val_t, &g->rp_a, &g->col_a, &g->val_a, &g->outdeg, &g->perm_a2t,
+                            &g->w_a, &g->inv_d, &g->row_a, &g->r_str})
+        addr(*b);
+    for (const auto *plans : {&g->plans_t, &g->plans_a})
+        for (const auto &kv : *plans) {
+            v.push_back((uint64_t)kv.first);
+            for (const DevBuf *b : {&kv.second.tile_x, &kv.second.tile_y, &kv.second.head_row, &kv.second.head_first})
+                addr(*b);
+        }
+    for (const BinPlan *B : {&g->bins_t, &g->bins_a})
+        for (const DevBuf *b : {&B->rows_short, &B->rows_mid, &B->rows_long, &B->rows_empty, &B->long_first,
+                                &B->chunk_row, &B->chunk_e0})
+            addr(*b);
+    uint64_t bits;
+    memcpy(&bits, &g->c, sizeof bits);
+    v.push_back(bits);
+    memcpy(&bits, &g->eps, sizeof bits);
+    v.push_back(bits);
+    v.push_back((uint64_t)g->T);
+    v.push_back((uint64_t)g->weighted);
+    return v;
+}
+
 void drop_graphs(tpa_server *srv)
 {
     for (auto &kv : srv->graphs)
@@ -86,6 +130,7 @@ tpa_server::Entry capture(tpa_server *srv, int k)
     const bool timing = prof_pause();
     const uint64_t l0 = launches_so_far();
     cudaGraph_t graph = nullptr;
+    e.ident = identity(srv->g);
     TPA_CUDA(cudaStreamBeginCapture(srv->cap, cudaStreamCaptureModeThreadLocal));
     try {
         issue_batch(srv, k, srv->cap);
@@ -107,6 +152,11 @@ tpa_server::Entry capture(tpa_server *srv, int k)
     const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
     cudaGraphDestroy(graph);
     TPA_CUDA(ie);
+    if (identity(srv->g) != e.ident) {   // the direct run sized everything: nothing may move while capturing
+        cudaGraphExecDestroy(e.exec);
+        set_error("tpa_server_query: a buffer was reallocated while a batch was captured");
+        throw Fail{TPA_ECUDA};
+    }
     return e;
 }
 
@@ -204,10 +254,25 @@ tpa_status tpa_server_query(tpa_server *srv, const int32_t *seeds, int k, void *
     }
     WorkspaceSwap swap(g, &srv->ws);
     auto it = srv->graphs.find(k);
+    if (it != srv->graphs.end() && it->second.ident != identity(g)) {
+        TPA_CUDA(cudaStreamSynchronize(s));
+        drop_graphs(srv);                       // stale: they refer to reallocated buffers
+        it = srv->graphs.end();
+    }
     if (it == srv->graphs.end()) {
         issue_batch(srv, k, s);                 // this batch's answer; sizes the workspace for k
         TPA_CUDA(cudaStreamSynchronize(s));     // the capture must not race the direct run
+        const std::vector<uint64_t> now = identity(g);
+        for (auto e = srv->graphs.begin(); e != srv->graphs.end();) {   // a buffer grew: older graphs are stale
+            if (e->second.ident != now) {
+                cudaGraphExecDestroy(e->second.exec);
+                e = srv->graphs.erase(e);
+            } else {
+                ++e;
+            }
+        }
         srv->graphs[k] = capture(srv, k);
+        ++srv->captures;
     } else {
         TPA_CUDA(cudaGraphLaunch(it->second.exec, s));
         note_launch_count((int)it->second.launches);
@@ -226,7 +291,7 @@ tpa_status tpa_server_result(const tpa_server *srv, float **out, int64_t *ldo)
 }
 
 tpa_status tpa_server_stats(const tpa_server *srv, int k, int64_t *graphs, int64_t *replays,
-                            int64_t *launches_per_replay)
+                            int64_t *launches_per_replay, int64_t *captures)
 {
     SRV_BEGIN
     TPA_REQUIRE(srv != nullptr, "tpa_server_stats: NULL server");
@@ -236,6 +301,7 @@ tpa_status tpa_server_stats(const tpa_server *srv, int k, int64_t *graphs, int64
         auto it = srv->graphs.find(k);
         *launches_per_replay = it == srv->graphs.end() ? 0 : it->second.launches;
     }
+    if (captures) *captures = srv->captures;
     SRV_END
 }
 

@@ -55,7 +55,8 @@ def library():
         "tpa_server_create": (i32, [P, i32, i32, P, i64, P, ctypes.POINTER(P)]),
         "tpa_server_query": (i32, [P, P, i32, P]),
         "tpa_server_result": (i32, [P, ctypes.POINTER(P), ctypes.POINTER(i64)]),
-        "tpa_server_stats": (i32, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "tpa_server_stats": (i32, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                   ctypes.POINTER(i64)]),
         "tpa_server_free": (None, [P]),
         "tpa_launch_count": (ctypes.c_uint64, []),
         "tpa_variant_count": (i32, []),
@@ -221,9 +222,10 @@ class Server:
         return self.out[:, :k]
 
     def stats(self, k: int = 0) -> dict:
-        gr, rp, lp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-        _check(library().tpa_server_stats(self._h, int(k), ctypes.byref(gr), ctypes.byref(rp), ctypes.byref(lp)))
-        return {"graphs": gr.value, "replays": rp.value, "launches_per_replay": lp.value}
+        gr, rp, lp, cp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(library().tpa_server_stats(self._h, int(k), ctypes.byref(gr), ctypes.byref(rp), ctypes.byref(lp),
+                                          ctypes.byref(cp)))
+        return {"graphs": gr.value, "replays": rp.value, "launches_per_replay": lp.value, "captures": cp.value}
 
     def free(self):
         if self._h:

@@ -63,6 +63,28 @@ def test_fullsize_query_batch(full):
         parity(out[:, j].cpu().numpy(), ref, f"scale 22 batch column {j} seed {seeds[j]}")
 
 
+def test_fullsize_server_growing_batches(full):
+    """Batched serving on the full-size graph with batch sizes whose workspace
+    grows (width-1 chunks, then chunks of 8): every batch equals tpa_query bit
+    for bit, and graphs captured over reallocated buffers are never replayed."""
+    tpa, torch = full["tpa"], full["torch"]
+    seeds = full["seeds"]
+    sizes = [1, 256, 1, 7, 256, 100, 1, 7]
+    srv = tpa.Server(full["g"], S, max_k=256)
+    off = 0
+    for k in sizes:
+        sd = seeds[off:off + k]
+        off += k
+        got = srv.query(torch.from_numpy(sd).cuda()).clone()
+        assert torch.equal(got, tpa.query(full["g"], sd, S)), k
+    st = srv.stats()
+    assert st["replays"] + st["captures"] == len(sizes) and st["replays"] >= 2
+    j = 3
+    ref = oracle.query(full["og"], int(seeds[off - sizes[-1] + j]), C, S, T, full["rs"], EPS)
+    parity(got[:, j].cpu().numpy(), ref, "server scale 22")
+    srv.free()
+
+
 # ---------------------------------------------------------------------------
 # The batched-serving graph at full size: R-MAT scale 24 (16,777,216 nodes,
 # 268,435,456 raw edges, key 1): the whole r~_stranger vector of

@@ -59,9 +59,35 @@ def test_server_uneven_batches(graph14):
                 parity(got[:, j].cpu().numpy(),
                        oracle.query(graph14["og"], int(sd[j]), C, S, T, graph14["rs"], EPS), f"batch {b} col {j}")
     st = srv.stats(256)
-    assert st["graphs"] == len(set(sizes))
-    assert st["replays"] == len(sizes) - len(set(sizes))
+    # every batch is a replay or a direct run + capture; a batch that grew the
+    # workspace drops the graphs captured over the old buffers
+    assert st["replays"] + st["captures"] == len(sizes)
+    assert len(set(sizes)) <= st["captures"] < len(sizes)
+    assert 1 <= st["graphs"] <= len(set(sizes))
     assert st["launches_per_replay"] > 0
+    srv.free()
+
+
+def test_server_workspace_growth_recaptures(graph14):
+    """A batch of 1 seed runs chunks of width 1; a later batch of 256 needs
+    chunks of 8 and grows every workspace buffer.  The graph captured for 1
+    refers to the old buffers, so it must be dropped and captured again, not
+    replayed."""
+    import torch
+    t = tpa()
+    sd = synth.query_seeds(graph14["cand"], 256, key=14)
+    srv = t.Server(graph14["g"], S, max_k=256)
+    expect = [(1, dict(graphs=1, replays=0, captures=1)),
+              (256, dict(graphs=1, replays=0, captures=2)),     # grew: the graph for 1 is gone
+              (1, dict(graphs=2, replays=0, captures=3)),
+              (1, dict(graphs=2, replays=1, captures=3)),
+              (256, dict(graphs=2, replays=2, captures=3))]
+    for k, st in expect:
+        got = srv.query(sd[:k]).clone()
+        assert torch.equal(got, t.query(graph14["g"], sd[:k], S)), k
+        now = srv.stats(k)
+        assert {key: now[key] for key in st} == st, (k, now)
+    parity(got[:, 255].cpu().numpy(), oracle.query(graph14["og"], int(sd[255]), C, S, T, graph14["rs"], EPS), "k 256")
     srv.free()
 
 
