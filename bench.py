@@ -61,8 +61,8 @@ def profile_case(args):
 
     preprocess: build the graph and run TPA preprocessing once (about 106 k = 1
     SpMV launches).  query8: the same, then two queries of 8 seeds with at most
-    256 out-edges (push path for x1 and x2, then two pulled SpMM launches each,
-    the first one masked by the rows x2 reaches).  Library defaults, no tuning."""
+    256 out-edges (push path for x1 and x2, then two pulled SpMM launches
+    each, each with its fixup).  Library defaults, no tuning."""
     import torch
     import synth
     import paper_1708_02574_gb300 as tpa
