@@ -88,9 +88,11 @@ def test_fullsize_server_growing_batches(full):
 # ---------------------------------------------------------------------------
 # The batched-serving graph at full size: R-MAT scale 24 (16,777,216 nodes,
 # 268,435,456 raw edges, key 1): the whole r~_stranger vector of
-# preprocessing against the oracle.
+# preprocessing against the oracle, and the 8,192-seed stream of uneven
+# request batches (sizes uniform over {1, 7, 32, 100, 256}, key 3; seeds
+# uniform over nodes with an out-edge, key 2) answered by tpa_query.
 
-SCALE24 = 24
+SCALE24, SEEDS24 = 24, 8192
 
 
 @pytest.fixture(scope="module")
@@ -102,15 +104,49 @@ def full24():
     g = tpa.build_graph(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
     tpa.preprocess(g, C, T, EPS)
     og = oracle.build_graph(n, s, d)
+    cand = synth.nodes_with_out_edge(n, s, d)
     del s, d
     rs, it = oracle.preprocess(og, C, T, EPS)
-    return dict(n=n, g=g, og=og, rs=rs, it=it, tpa=tpa, torch=torch)
+    seeds = synth.query_seeds(cand, SEEDS24)
+    sizes = synth.batch_sizes(SEEDS24)
+    return dict(n=n, g=g, og=og, rs=rs, it=it, seeds=seeds, sizes=sizes, tpa=tpa, torch=torch)
 
 
 def test_scale24_preprocess(full24):
     r, it = full24["tpa"].get_stranger(full24["g"])
     parity(r.cpu().numpy(), full24["rs"], "r_stranger scale 24")
     assert abs(it - full24["it"]) <= 1
+
+
+def test_scale24_uneven_batches(full24):
+    """Every batch of the stream: the bounds of Lemma 2 and Theorem 2 on each
+    column (the seed's own score is at least (1+alpha)c, scores are
+    non-negative, sum to at most 1 and are at least r~_stranger); the first
+    and last column of one batch of each size against the FP64 oracle."""
+    tpa, torch = full24["tpa"], full24["torch"]
+    g, seeds, sizes = full24["g"], full24["seeds"], full24["sizes"]
+    assert sum(sizes) == SEEDS24 and set(sizes[:-1]) == {1, 7, 32, 100, 256}   # the last one is truncated
+    r_str, _ = tpa.get_stranger(g)
+    alpha = ((1 - C) ** S - (1 - C) ** T) / (1 - (1 - C) ** S)
+    off, checked = 0, set()
+    for b, k in enumerate(sizes):
+        sd = seeds[off:off + k]
+        off += k
+        out = tpa.query(g, torch.from_numpy(sd).cuda(), S)
+        assert out.shape == (full24["n"], k)
+        own = out[torch.from_numpy(sd).long().cuda(), torch.arange(k, device="cuda")]
+        assert bool((own >= (1 + alpha) * C - 1e-6).all()), b
+        for j0 in range(0, k, 32):
+            blk = out[:, j0:j0 + 32]
+            assert bool((blk >= r_str[:, None] - 1e-7).all()), b
+            assert bool((blk.double().sum(0) <= 1.0 + 1e-5).all()), b
+        if k not in checked:
+            checked.add(k)
+            for j in sorted({0, k - 1}):
+                ref = oracle.query(full24["og"], int(sd[j]), C, S, T, full24["rs"], EPS)
+                parity(out[:, j].cpu().numpy(), ref, f"scale 24 batch {b} (k={k}) column {j}")
+        del out
+    assert off == SEEDS24 and checked == set(sizes)
 
 
 # ---------------------------------------------------------------------------
