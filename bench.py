@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--valued-products", action="store_true",
+                    help="products that read the value array instead of the default pattern-only products")
     ap.add_argument("--profile-case", choices=["preprocess", "query8"], default=None,
                     help="run one small case for an ncu capture and exit (no JSON line): preprocessing of the "
                          "graph, or two 8-seed queries of light seeds after it")
@@ -66,6 +68,7 @@ def profile_case(args):
     import torch
     import synth
     import paper_1708_02574_gb300 as tpa
+    tpa.set_pattern(not args.valued_products)
     n = 1 << args.scale
     src, dst = synth.rmat_edges(args.scale, args.edge_factor)
     g = tpa.build_graph(n, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda())
@@ -278,6 +281,7 @@ def main(argv=None):
     import synth
     import paper_1708_02574_gb300 as tpa
 
+    tpa.set_pattern(not args.valued_products)
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -394,9 +398,11 @@ def main(argv=None):
         achieved = sp["alg_bytes"] / (sp["total_ms"] / 1000.0) / 1e9
         per_launch = sp["alg_bytes"] / max(1, sp["launches"])
         variant = names.get(tpa.get_variant(int(fam[len("spmm_kp"):])), "?")
+        products = "valued" if args.valued_products else "pattern"
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": ncu_traffic(variant, args.scale), "variant": variant,
-                "kernel": f"{fam}: merge-path SpMV/SpMM over CSR(A~^T), {variant}",
+                "traffic": ncu_traffic(f"{variant}+{products}", args.scale), "variant": variant,
+                "products": products,
+                "kernel": f"{fam}: merge-path SpMV/SpMM over CSR(A~^T), {variant}, {products} products",
                 "launches": sp["launches"], "avg_launch_ms": sp["total_ms"] / max(1, sp["launches"]),
                 "alg_bytes_per_launch": per_launch, "peak_source": f"{peak_kind} hbm_gbs (copy), burst",
                 "kernel_share_of_step": sp["total_ms"] / (1000.0 * t_rank)}
@@ -421,6 +427,7 @@ def main(argv=None):
                 "config": {"workload": WORKLOAD, "graph": f"R-MAT scale {args.scale} ef {args.edge_factor}",
                            "n": n, "m": m, "m_raw": int(src.size), "queries_per_rank": Q, "query_batch": batch,
                            "c": C, "S": S, "T": T, "eps": EPS, "parallelism": f"replicas x{world} (seed-sharded)",
+                           "products": "valued" if args.valued_products else "pattern-only",
                            "l2": "inputs larger than L2 (CSR 0.5 GB, scores 16.8 GB per step)"},
                 "roofline": roof, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk,

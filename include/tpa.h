@@ -224,6 +224,15 @@ int tpa_get_cpi_batch_width(void);
  * only by FP32 rounding order.  enable = 0 pulls every iteration. */
 tpa_status tpa_set_push(int enable);
 
+/* Pattern-only products (default on) for unweighted graphs: every edge out of
+ * node u carries the same value RN32(1/outdeg(u)), so the propagation gathers
+ * x_u * RN32(1/outdeg(u)), kept scaled in the iterate buffer, instead of
+ * reading the value array: 4 instead of 8 bytes per nonzero (Section III-A's
+ * row-normalised A~ is unchanged).  Results differ from the valued products
+ * only by FP32 rounding.  Weighted graphs always read their values.
+ * enable = 0 reads the value array everywhere. */
+tpa_status tpa_set_pattern(int enable);
+
 /* ---------------------------------------------------- batched serving ---
  * Algorithm 3 for a stream of request batches of uneven size, with the launch
  * sequence of each batch size captured once in a CUDA graph and replayed.
@@ -236,7 +245,7 @@ tpa_status tpa_set_push(int enable);
  * and graphs that point at it and at the graph's CSR: it must be freed before
  * the graph, and calls on one server must not overlap.  Results equal those
  * of tpa_query with the same settings bit for bit.  A change of a kernel
- * setting (tpa_set_variant, tpa_set_batch_width, tpa_set_push) makes the
+ * setting (tpa_set_variant, tpa_set_batch_width, tpa_set_push, tpa_set_pattern) makes the
  * server capture again, and so does a batch that needs more workspace than
  * any before it (its buffers are reallocated, and graphs captured over the
  * old ones are dropped, never replayed). */

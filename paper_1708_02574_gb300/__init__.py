@@ -37,6 +37,7 @@ from .tpa import (  # noqa: F401
     set_cpi_batch_width,
     get_cpi_batch_width,
     set_push,
+    set_pattern,
     get_batch_width,
     set_variant,
     get_variant,

@@ -169,7 +169,8 @@ void tpa_free_graph(tpa_graph *g)
     if (!g) return;
     cudaStream_t s = 0;
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&g->rp_t, &g->col_t, &g->val_t, &g->rp_a, &g->col_a, &g->val_a, &g->outdeg, &g->r_str,
+    DevBuf *bufs[] = {&g->rp_t, &g->col_t, &g->val_t, &g->rp_a, &g->col_a, &g->val_a, &g->outdeg, &g->inv_deg32,
+                      &g->r_str,
                       &g->perm_a2t, &g->w_a, &g->inv_d, &g->row_a, &g->ws.u, &g->ws.touched, &g->ws.x2,
                       &g->ws.x, &g->ws.y, &g->ws.r, &g->ws.carry, &g->ws.head, &g->ws.tl1, &g->ws.fix,
                       &g->ws.ctl, &g->ws.seeds, &g->ws.out, &g->ws.iters};

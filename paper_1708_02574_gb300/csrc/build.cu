@@ -332,6 +332,16 @@ __global__ void fill_vals_t_k(const int32_t *col, int64_t m, const int32_t *outd
         val[i] = 1.0f / (float)outdeg[col[i]];
 }
 
+// RN32(1/outdeg(u)) per node, the value every edge out of u carries in both
+// CSRs (same expression as the edge values, so bit-identical); 0 for deadends.
+__global__ void inv_deg_k(const int32_t *outdeg, int64_t n, float *inv)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = outdeg[i];
+        inv[i] = d > 0 ? 1.0f / (float)d : 0.0f;
+    }
+}
+
 __global__ void split_a_k(const uint64_t *key, int64_t m, const int32_t *outdeg, int32_t *col, float *val)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
@@ -430,6 +440,7 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
     for (DevBuf *b : {&g->col_t, &g->val_t, &g->col_a, &g->val_a})
         TPA_CUDA(cudaMemsetAsync(static_cast<char *>(b->p) + (size_t)m * 4, 0, (size_t)CSR_PAD * 4, s));
     g->outdeg.ensure((size_t)n * sizeof(int32_t), s);
+    g->inv_deg32.ensure((size_t)n * sizeof(float), s);
     cnt.ensure((size_t)n * sizeof(int32_t), s);
 
     // 5. CSR(A~^T) row pointers from run lengths of dst
@@ -469,6 +480,10 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
         fill_vals_t_k<<<grid_for(m, 256), 256, 0, s>>>(g->col_t.as<int32_t>(), m, g->outdeg.as<int32_t>(),
                                                        g->val_t.as<float>());
         note_launch("build", 2);
+    }
+    if (n > 0) {
+        inv_deg_k<<<grid_for(n, 256), 256, 0, s>>>(g->outdeg.as<int32_t>(), n, g->inv_deg32.as<float>());
+        note_launch("build");
     }
     TPA_CHECK_LAUNCH();
     // keep the payload of the source sort: for each CSR(A~) edge, its index in CSR(A~^T)

@@ -218,16 +218,21 @@ static int64_t launch_spmvp(const Params &p, cudaStream_t s)
 {
     constexpr size_t smem = WARPS * PipeSmem<G, V, ITEMS>::PER_WARP;
     static_assert(smem <= 227 * 1024, "shared memory per block");
+    // one instantiation per product mode, so the valued kernel carries no test of it
+    auto *const valued = spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB, false>;
+    auto *const pattern = spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB, true>;
     static int per_sm = 0;
     if (!per_sm) {
-        TPA_CUDA(cudaFuncSetAttribute(spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB>,
-                                                               WARPS * 32, smem));
-        per_sm = std::max(per_sm, 1);
+        TPA_CUDA(cudaFuncSetAttribute(valued, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TPA_CUDA(cudaFuncSetAttribute(pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int a = 0, b = 0;
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, valued, WARPS * 32, smem));
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pattern, WARPS * 32, smem));
+        per_sm = std::max(std::min(a, b), 1);
     }
     const int64_t grid = std::min<int64_t>((p.tiles + WARPS - 1) / WARPS, (int64_t)per_sm * num_sms());
-    spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB><<<(unsigned)grid, WARPS * 32, smem, s>>>(p);
+    if (p.inv_deg) pattern<<<(unsigned)grid, WARPS * 32, smem, s>>>(p);
+    else valued<<<(unsigned)grid, WARPS * 32, smem, s>>>(p);
     return grid * WARPS;
 }
 
@@ -419,6 +424,8 @@ constexpr int DEFAULT_CHUNK_QUERY = 8;
 constexpr int DEFAULT_CHUNK_CPI = 8;
 // Push path for the first two family iterations of a query (on by default).
 static bool g_push = true;
+// Pattern-only products for unweighted graphs (on by default; see Params::inv_deg).
+static bool g_pattern = true;
 constexpr int PUSH_MAX_OUTDEG = 256;   // seeds with more out-edges keep the pull path
 static_assert(PUSH_MAX_OUTDEG <= PUSH_THREADS, "push_x2_k takes one thread per out-edge of the seed");
 constexpr int PUSH_BLOCKS = 32;        // blocks per column in push_x2_k
@@ -426,15 +433,18 @@ constexpr int PUSH_MAX_KP = 16;        // widest query chunk with the push branc
 
 static void launch_convert(int KP, unsigned blocks, unsigned long long *U, uint32_t *touched, float *X, float *R,
                            int64_t n, int kc, float decay, double eps, double *part, void *ctl, int gate,
-                           cudaStream_t s)
+                           const float *inv_deg, cudaStream_t s)
 {
+#define TPA_CONVERT(W) \
+    convert_x2_k<W><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl, gate, inv_deg)
     switch (KP) {
-    case 1: convert_x2_k<1><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl, gate); break;
-    case 2: convert_x2_k<2><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl, gate); break;
-    case 4: convert_x2_k<4><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl, gate); break;
-    case 16: convert_x2_k<16><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl, gate); break;
-    default: convert_x2_k<8><<<blocks, 256, 0, s>>>(U, touched, X, R, n, kc, decay, eps, part, ctl, gate); break;
+    case 1: TPA_CONVERT(1); break;
+    case 2: TPA_CONVERT(2); break;
+    case 4: TPA_CONVERT(4); break;
+    case 16: TPA_CONVERT(16); break;
+    default: TPA_CONVERT(8); break;
     }
+#undef TPA_CONVERT
 }
 
 static void launch_clear_x2(int KP, uint32_t *touched, float *X, int64_t n, void *ctl, int gate, cudaStream_t s)
@@ -462,14 +472,15 @@ static const Variant &pick_variant(int KP)
 
 // ------------------------------------------------------------ CPI loop ---
 // Algorithmic bytes of one SpMV/SpMM launch over CSR(A~^T): row pointers
-// (int64), columns and values once, the iterate X[n][KP] read once and, in the
-// accumulate mode, Y[n][KP] written and r[n][k] read and written; in the
-// finalize mode r[n][k] and r~_stranger[n] read and out[n][k] written.
-static double spmm_bytes(int64_t n, int64_t m, int KP, int k, int mode, int accumulate)
+// (int64), columns and values once (columns only for pattern-only products),
+// the iterate X[n][KP] read once and, in the accumulate mode, Y[n][KP]
+// written (pattern-only: with inv_deg[n] read) and r[n][k] read and written;
+// in the finalize mode r[n][k] and r~_stranger[n] read and out[n][k] written.
+static double spmm_bytes(int64_t n, int64_t m, int KP, int k, int mode, int accumulate, bool pattern)
 {
-    double b = 8.0 * (double)(n + 1) + 8.0 * (double)m + 4.0 * (double)n * KP;
+    double b = 8.0 * (double)(n + 1) + (pattern ? 4.0 : 8.0) * (double)m + 4.0 * (double)n * KP;
     if (mode == MODE_ACC)
-        b += 4.0 * (double)n * KP + (accumulate ? 8.0 * (double)n * k : 0.0);
+        b += 4.0 * (double)n * KP + (accumulate ? 8.0 * (double)n * k : 0.0) + (pattern ? 4.0 * (double)n : 0.0);
     else
         b += 4.0 * (double)n * k + 4.0 * (double)n + 4.0 * (double)n * k;
     return b;
@@ -513,6 +524,8 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
 
     ctl_init_k<<<1, 256, 0, s>>>(W.ctl.p, kc);
     note_launch("init");
+    // pattern-only products: x is kept scaled by the inverse out-degree
+    const float *inv_deg = g_pattern && !g->weighted ? g->inv_deg32.as<float>() : nullptr;
     const float c_val = (float)a.c;
     const float pr_val = (float)(a.c * (1.0 / (double)n));
     float *r;
@@ -568,19 +581,19 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
                 g->rp_a.as<int64_t>(), g->col_a.as<int32_t>(), g->val_a.as<float>(), a.seeds + k0, KP, c_val,
                 decay_f, W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), r, W.ctl.p, gate_push);
             launch_convert(KP, cblocks, W.u.as<unsigned long long>(), W.touched.as<uint32_t>(), W.x2.as<float>(), r,
-                           n, kc, decay_f, a.eps, W.fix.as<double>(), W.ctl.p, gate_push, s);
+                           n, kc, decay_f, a.eps, W.fix.as<double>(), W.ctl.p, gate_push, inv_deg, s);
             note_launch("push", 3);
         }
         if (run_pull) {   // x0; iterations 1 and 2 are pulled below
             init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, a.seeds + k0, kc, c_val, pr_val, r,
-                                                         ldr, a.s_iter == 0 ? 1 : 0, W.ctl.p, gate_pull);
+                                                         ldr, a.s_iter == 0 ? 1 : 0, W.ctl.p, gate_pull, inv_deg);
             note_launch("init");
         }
         TPA_CHECK_LAUNCH();
     } else {
         init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, a.seeds ? a.seeds + k0 : nullptr, kc,
                                                      c_val, pr_val, r, ldr, a.s_iter == 0 ? 1 : 0, W.ctl.p,
-                                                     GATE_NONE);
+                                                     GATE_NONE, inv_deg);
         note_launch("init");
         TPA_CHECK_LAUNCH();
     }
@@ -622,6 +635,7 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     p.tl1 = W.tl1.as<float>();
     p.part = W.fix.as<double>();
     p.ctl = W.ctl.p;
+    p.inv_deg = inv_deg;
     if (var.binned) bind_bins(p, g, 0, KP, s);
 
     // x and y alternate; on a two-way chunk iteration 2 writes and iteration
@@ -656,7 +670,7 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
             p.mode = (a.tpa_final && i == last) ? MODE_FINAL : MODE_ACC;
             ProfMark pm = prof_begin(s);
             p.l1_slots = var.spmm(p, s);
-            prof_end(pm, spmm_family(KP), spmm_bytes(n, g->m, KP, kc, p.mode, p.accumulate), s);
+            prof_end(pm, spmm_family(KP), spmm_bytes(n, g->m, KP, kc, p.mode, p.accumulate, p.inv_deg != nullptr), s);
             ProfMark pf = prof_begin(s);
             var.fix(p, fix_blocks, s);
             prof_end(pf, "fixup", 0.0, s);
@@ -881,7 +895,7 @@ void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float
     if (var.binned) bind_bins(p, g, which, KP, s);
     ProfMark pm = prof_begin(s);
     p.l1_slots = var.spmm(p, s);
-    prof_end(pm, spmm_family(KP), spmm_bytes(g->n, g->m, KP, kc, MODE_ACC, 0), s);
+    prof_end(pm, spmm_family(KP), spmm_bytes(g->n, g->m, KP, kc, MODE_ACC, 0, false), s);
     var.fix(p, fix_blocks, s);
     note_launch("init");
     note_launch(spmm_family(KP));
@@ -987,6 +1001,13 @@ int tpa_get_cpi_batch_width(void) { return g_chunk_cpi ? g_chunk_cpi : DEFAULT_C
 tpa_status tpa_set_push(int enable)
 {
     g_push = enable != 0;
+    ++g_epoch;
+    return TPA_OK;
+}
+
+tpa_status tpa_set_pattern(int enable)
+{
+    g_pattern = enable != 0;
     ++g_epoch;
     return TPA_OK;
 }

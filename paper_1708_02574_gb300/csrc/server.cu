@@ -92,7 +92,8 @@ std::vector<uint64_t> identity(const tpa_graph *g)
                             &w.u, &w.touched, &w.x2, &w.cpart})
         addr(*b);
     v.push_back((uint64_t)(uintptr_t)w.hflag);
-    for (const DevBuf *b : {&g->rp_t, &g->col_t, &g->val_t, &g->rp_a, &g->col_a, &g->val_a, &g->outdeg, &g->perm_a2t,
+    for (const DevBuf *b : {&g->rp_t, &g->col_t, &g->val_t, &g->rp_a, &g->col_a, &g->val_a, &g->outdeg, &g->inv_deg32,
+                            &g->perm_a2t,
                             &g->w_a, &g->inv_d, &g->row_a, &g->r_str})
         addr(*b);
     for (const auto *plans : {&g->plans_t, &g->plans_a})

@@ -77,7 +77,7 @@ __device__ __forceinline__ void epilogue_col(const Params &p, int64_t row, int c
     const bool valid = c < p.k;
     const bool run = valid && alive_c;
     if (p.mode == MODE_ACC) {
-        p.y[row * KP + c] = y;
+        p.y[row * KP + c] = p.inv_deg ? y * __ldg(p.inv_deg + row) : y;   // the next product's x
         if (p.accumulate && run) atomicAdd(p.r + row * p.ldr + c, y);
     } else if (valid) {
         float fam = p.r[row * p.ldr + c];
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(BIN_WARPS * 32) bin_short_k(Params p)
 #pragma unroll 4
         for (int64_t e = e0 + sub; e < e1; e += LPR) {
             const int32_t c = __ldcs(p.col + e);
-            const float v = __ldcs(p.val + e);
+            const float v = p.inv_deg ? 1.0f : __ldcs(p.val + e);
             float xv[KP];
             ld_row<KP>(p.x + (int64_t)c * KP, xv);
 #pragma unroll
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(BIN_WARPS * 32) bin_warp_k(Params p)
 #pragma unroll 4
         for (int64_t e = e0 + lane; e < e1; e += 32) {
             const int32_t c = __ldcs(p.col + e);
-            const float v = __ldcs(p.val + e);
+            const float v = p.inv_deg ? 1.0f : __ldcs(p.val + e);
             float xv[KP];
             ld_row<KP>(p.x + (int64_t)c * KP, xv);
 #pragma unroll

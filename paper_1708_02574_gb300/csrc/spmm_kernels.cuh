@@ -91,6 +91,12 @@ struct Params {
     int64_t n_short, n_mid, n_long, n_empty, n_chunks;
     float *cpart;       // [n_chunks][KP] chunk sums
     int64_t slot0;      // first row of tl1 this launch writes its L1 partials to
+    // Pattern-only products over an unweighted CSR(A~^T), whose value at
+    // (v, u) is RN32(1/outdeg(u)) for every v: when inv_deg (that value per
+    // node u) is set, the value array is not read, x holds x_u * inv_deg[u],
+    // and the accumulate epilogue stores y_v * inv_deg[v] as the next x.
+    // r, the L1 norms and the outputs keep the unscaled iterate.
+    const float *inv_deg;
 };
 
 enum Gate : int { GATE_NONE = 0, GATE_PULL = 1, GATE_PUSH = 2 };
@@ -195,8 +201,30 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int V>
 __device__ __forceinline__ void cp_async_row(float *base, int elem, const float *src);
 
+// Product mode of a kernel: read from Params at run time, or fixed when the
+// kernel is compiled for one of them (valued: x_u and the value array;
+// pattern-only: x_u * inv_deg[u], see Params::inv_deg).
+enum ProductMode : int { PM_RUNTIME = 0, PM_VALUED = 1, PM_PATTERN = 2 };
+
+// Store one finished row of the iterate as the next product's x: scaled by
+// the row's inverse out-degree in pattern-only mode.
+template <int V, int PM = PM_RUNTIME>
+__device__ __forceinline__ void st_next_row(const Params &p, int64_t row, float *dst, const float (&y)[V])
+{
+    const bool pattern = PM == PM_PATTERN || (PM == PM_RUNTIME && p.inv_deg != nullptr);
+    if (pattern) {
+        const float w = __ldg(p.inv_deg + row);
+        float xs[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) xs[j] = y[j] * w;
+        st_row<V>(dst, xs);
+    } else {
+        st_row<V>(dst, y);
+    }
+}
+
 // Epilogue of Algorithm 1 for one finished row and V consecutive columns.
-template <int KP, int V>
+template <int KP, int V, int PM = PM_RUNTIME>
 __device__ __forceinline__ void epilogue(const Params &p, int64_t row, int col0, const float (&s)[V],
                                          const int (&alive)[V], float (&l1)[V])
 {
@@ -204,7 +232,7 @@ __device__ __forceinline__ void epilogue(const Params &p, int64_t row, int col0,
 #pragma unroll
     for (int j = 0; j < V; ++j) yv[j] = p.decay * s[j];
     if (p.mode == MODE_ACC) {
-        st_row<V>(p.y + row * KP + col0, yv);
+        st_next_row<V, PM>(p, row, p.y + row * KP + col0, yv);
         if (p.accumulate) {
             if (p.ldr == KP && V > 1) {
                 // whole padded row contiguous: vector read-modify-write
@@ -291,7 +319,7 @@ __global__ void __launch_bounds__(CTA) spmm_tile_k(Params p)
         if (threadIdx.x == 0) S.end[nrows] = 0x7fffffff;
         for (int i = threadIdx.x; i < nnz; i += CTA) {
             S.col[i] = __ldcs(p.col + y0 + i);
-            S.val[i] = __ldcs(p.val + y0 + i);
+            S.val[i] = p.inv_deg ? 1.0f : __ldcs(p.val + y0 + i);
         }
         __syncthreads();
 
@@ -545,7 +573,7 @@ spmvw_tile_k(Params p)
             for (int j = 0; j < ITEMS; ++j) {
                 const int i = lane + j * 32;
                 c[j] = i < nnz ? __ldcs(p.col + y0 + i) : 0;
-                v[j] = i < nnz ? __ldcs(p.val + y0 + i) : 0.0f;
+                v[j] = i < nnz ? (p.inv_deg ? 1.0f : __ldcs(p.val + y0 + i)) : 0.0f;
             }
             if constexpr (WT::ASYNC) {
                 // wide rows: gathers go straight to shared memory, all in flight at once
@@ -723,7 +751,7 @@ __global__ void __launch_bounds__(WARPS * 32) spmvg_tile_k(Params p)
         if (lane == 0) S.end[nrows] = 0x7fffffff;
         for (int i = lane; i < nnz; i += 32) {
             S.col[i] = __ldcs(p.col + y0 + i);
-            S.val[i] = __ldcs(p.val + y0 + i);
+            S.val[i] = p.inv_deg ? 1.0f : __ldcs(p.val + y0 + i);
         }
         __syncwarp();
 
@@ -870,7 +898,7 @@ __device__ __forceinline__ void red_row(float *p, const float (&v)[V])
 
 // Epilogue of Algorithm 1 for one finished row in accumulate mode without
 // loads: y stored, r += y by a vector atomic add.
-template <int KP, int V>
+template <int KP, int V, int PM = PM_RUNTIME>
 __device__ __forceinline__ void epilogue_red(const Params &p, int64_t row, int col0, const float (&s)[V],
                                              const int (&alive)[V], float (&l1)[V])
 {
@@ -878,7 +906,7 @@ __device__ __forceinline__ void epilogue_red(const Params &p, int64_t row, int c
 #pragma unroll
     for (int j = 0; j < V; ++j) yv[j] = p.decay * s[j];
     if (p.mode == MODE_ACC) {
-        st_row<V>(p.y + row * KP + col0, yv);
+        st_next_row<V, PM>(p, row, p.y + row * KP + col0, yv);
         if (p.accumulate) {
             if (p.ldr == KP) {
                 float add[V];
@@ -964,7 +992,7 @@ struct ChunkRegs {
     float4 v[RC > 0 ? RC : 1];
 };
 
-template <int RC>
+template <int RC, bool PAT>
 __device__ __forceinline__ void load_chunks(const Params &p, const TileMeta &m, ChunkRegs<RC> &r, int lane)
 {
     const int chunks = tile_chunks(m);
@@ -974,7 +1002,7 @@ __device__ __forceinline__ void load_chunks(const Params &p, const TileMeta &m, 
         const int q = lane + 32 * k;
         if (q < chunks) {
             r.c[k] = __ldcs(reinterpret_cast<const int4 *>(p.col + y0a) + q);
-            r.v[k] = __ldcs(reinterpret_cast<const float4 *>(p.val + y0a) + q);
+            if constexpr (!PAT) r.v[k] = __ldcs(reinterpret_cast<const float4 *>(p.val + y0a) + q);
         }
     }
 }
@@ -982,7 +1010,7 @@ __device__ __forceinline__ void load_chunks(const Params &p, const TileMeta &m, 
 // Store the register chunks of tile m interleaved as (column, value) pairs,
 // and issue the cp.async copies of its row ends and of the elements of chunks
 // past 32 * RC (a few per tile at most; the caller commits).
-template <int RC>
+template <int RC, bool PAT>
 __device__ __forceinline__ void stage_tile(const Params &p, const TileMeta &m, const ChunkRegs<RC> &r,
                                            int64_t *rp_s, int32_t *cv_s, int lane)
 {
@@ -993,7 +1021,7 @@ __device__ __forceinline__ void stage_tile(const Params &p, const TileMeta &m, c
         const int q = lane + 32 * k;
         if (q < chunks) {
             const int4 c = r.c[k];
-            const float4 v = r.v[k];
+            const float4 v = PAT ? make_float4(1.0f, 1.0f, 1.0f, 1.0f) : r.v[k];
             *reinterpret_cast<int4 *>(cv_s + 4 * chunk_slot(2 * q)) =
                 make_int4(c.x, __float_as_int(v.x), c.y, __float_as_int(v.y));
             *reinterpret_cast<int4 *>(cv_s + 4 * chunk_slot(2 * q + 1)) =
@@ -1002,14 +1030,15 @@ __device__ __forceinline__ void stage_tile(const Params &p, const TileMeta &m, c
     }
     for (int e = 128 * RC + lane; e < 4 * chunks; e += 32) {
         cp_async<4>(cv_s + pair_word(e), p.col + y0a + e);
-        cp_async<4>(cv_s + pair_word(e) + 1, p.val + y0a + e);
+        if constexpr (PAT) cv_s[pair_word(e) + 1] = __float_as_int(1.0f);
+        else cp_async<4>(cv_s + pair_word(e) + 1, p.val + y0a + e);
     }
     const int nrows = m.x1 - m.x0;
     for (int i = lane; i < nrows; i += 32) cp_async<8>(rp_s + i, p.rp + m.x0 + i + 1);
     if (lane == 0) rp_s[nrows] = m.y0 + 0x7fffffff;
 }
 
-template <int G, int V, int ITEMS, int PF>
+template <int G, int V, int ITEMS, int PF, bool PAT>
 __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, int64_t t, const int64_t *rp_s,
                                           const int32_t *cv_s, float *rs_s, int lane, const int (&alive)[V],
                                           float (&l1)[V])
@@ -1114,9 +1143,9 @@ __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, in
         float sv[V];
         ld_row_smem<V>(rs_s + r * KP + col0, sv);
         if (p.mode == MODE_ACC)
-            epilogue_red<KP, V>(p, (int64_t)(m.x0 + r), col0, sv, alive, l1);
+            epilogue_red<KP, V, PAT ? PM_PATTERN : PM_VALUED>(p, (int64_t)(m.x0 + r), col0, sv, alive, l1);
         else
-            epilogue<KP, V>(p, (int64_t)(m.x0 + r), col0, sv, alive, l1);
+            epilogue<KP, V, PAT ? PM_PATTERN : PM_VALUED>(p, (int64_t)(m.x0 + r), col0, sv, alive, l1);
     }
 }
 
@@ -1129,7 +1158,7 @@ struct PipeSmem {
 };
 
 // MINB: resident blocks per SM requested from the register allocator.
-template <int G, int V, int ITEMS, int PF, int WARPS, int MINB>
+template <int G, int V, int ITEMS, int PF, int WARPS, int MINB, bool PAT>
 __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
 {
     using PT = PipeTile<G, V, ITEMS>;
@@ -1159,21 +1188,21 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
     TileMeta cur = tile_meta(p, t);
     ChunkRegs<RC> rg;
     if (t < p.tiles) {
-        load_chunks<RC>(p, cur, rg, lane);   // the first tile waits for its loads
-        stage_tile<RC>(p, cur, rg, buf[0].rp, buf[0].cv, lane);
+        load_chunks<RC, PAT>(p, cur, rg, lane);   // the first tile waits for its loads
+        stage_tile<RC, PAT>(p, cur, rg, buf[0].rp, buf[0].cv, lane);
     }
     cp_async_commit();
     TileMeta nxt = tile_meta(p, t + stride);
-    load_chunks<RC>(p, nxt, rg, lane);
+    load_chunks<RC, PAT>(p, nxt, rg, lane);
     int b = 0;
     for (; t < p.tiles; t += stride) {
-        if (t + stride < p.tiles) stage_tile<RC>(p, nxt, rg, buf[b ^ 1].rp, buf[b ^ 1].cv, lane);
+        if (t + stride < p.tiles) stage_tile<RC, PAT>(p, nxt, rg, buf[b ^ 1].rp, buf[b ^ 1].cv, lane);
         cp_async_commit();
         const TileMeta after = tile_meta(p, t + 2 * stride);
-        load_chunks<RC>(p, after, rg, lane);   // in flight during this walk
+        load_chunks<RC, PAT>(p, after, rg, lane);   // in flight during this walk
         cp_async_wait_group<1>();              // this tile's copies have landed
         __syncwarp();
-        walk_tile<G, V, ITEMS, PF>(p, cur, t, buf[b].rp, buf[b].cv, rs_s, lane, alive, l1);
+        walk_tile<G, V, ITEMS, PF, PAT>(p, cur, t, buf[b].rp, buf[b].cv, rs_s, lane, alive, l1);
         __syncwarp();                          // buffers and row sums are rewritten next iteration
         cur = nxt;
         nxt = after;
@@ -1354,7 +1383,6 @@ __global__ void __launch_bounds__(256) fixup_small_k(Params p)
     const int32_t h = mine ? p.head_row[t] : -1;
     const int64_t first = mine ? (int64_t)p.head_first[t] : 0;
     float l1[V];
-#pragma unroll
     const bool has_l1 = mine && t < (p.l1_slots ? p.l1_slots : p.tiles);
 #pragma unroll
     for (int q = 0; q < V; ++q) l1[q] = has_l1 ? p.tl1[t * V + q] : 0.0f;
@@ -1441,8 +1469,10 @@ __global__ void __launch_bounds__(256) fixup_small_k(Params p)
 // ---------------------------------------------------------- init / misc ---
 // x0 = c q per column (one-hot at seeds[j], or c/n everywhere when seeds is null);
 // r = x0 when s_iter == 0, else 0.
+// With inv_deg (pattern-only products) x holds x0 scaled by the row's inverse
+// out-degree; r gets x0 itself.
 __global__ void init_k(float *x, int KP, int64_t n, const int32_t *seeds, int k, float c_val, float pr_val,
-                       float *r, int64_t ldr, int acc0, const void *ctl, int gate)
+                       float *r, int64_t ldr, int acc0, const void *ctl, int gate, const float *inv_deg)
 {
     if (gate_off(gate, ctl)) return;
     const int64_t total = n * KP;
@@ -1451,7 +1481,7 @@ __global__ void init_k(float *x, int KP, int64_t n, const int32_t *seeds, int k,
         const int j = (int)(i % KP);
         float x0 = 0.0f;
         if (j < k) x0 = seeds ? (seeds[j] == v ? c_val : 0.0f) : pr_val;
-        x[i] = x0;
+        x[i] = inv_deg ? x0 * __ldg(inv_deg + v) : x0;
         if (r && j < k) r[v * ldr + j] = acc0 ? x0 : 0.0f;
     }
 }
@@ -1611,7 +1641,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) push_x2_k(const int64_t *rp_a, c
 template <int KP>
 __global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, const uint32_t *touched, float *X,
                                                     float *R, int64_t n, int kc, float decay, double eps,
-                                                    double *part, void *ctl, int gate)
+                                                    double *part, void *ctl, int gate, const float *inv_deg)
 {
     if (gate_off(gate, ctl)) return;
     __shared__ float s_red[8][KP];
@@ -1644,7 +1674,15 @@ __global__ void __launch_bounds__(256) convert_x2_k(unsigned long long *U, const
                 }
                 nrm[j] += x[j];
             }
-            st_row<KP>(X + v * KP, x);
+            if (inv_deg) {   // pattern-only products gather x2 scaled by the inverse out-degree
+                const float w = __ldg(inv_deg + v);
+                float xs[KP];
+#pragma unroll
+                for (int j = 0; j < KP; ++j) xs[j] = x[j] * w;
+                st_row<KP>(X + v * KP, xs);
+            } else {
+                st_row<KP>(X + v * KP, x);
+            }
         }
     }
 #pragma unroll

@@ -121,6 +121,7 @@ struct tpa_graph {
     // CSR(A~): rows = sources
     tpa::DevBuf rp_a, col_a, val_a;
     tpa::DevBuf outdeg;
+    tpa::DevBuf inv_deg32;  // float[n] RN32(1/outdeg), 0 for deadends: the value of every edge out of a node
     tpa::DevBuf perm_a2t;   // uint32[m]: position in CSR(A~^T) of each CSR(A~) edge
     // weighted graphs (tpa_set_edge_weights)
     tpa::DevBuf w_a;        // float[m] edge weights, CSR(A~) order

@@ -70,6 +70,7 @@ def library():
         "tpa_set_cpi_batch_width": (i32, [i32]),
         "tpa_get_cpi_batch_width": (i32, []),
         "tpa_set_push": (i32, [i32]),
+        "tpa_set_pattern": (i32, [i32]),
         "tpa_profile_reset": (i32, [i32]),
         "tpa_profile_read": (i32, [P, i32, ctypes.POINTER(i32)]),
     }
@@ -344,6 +345,12 @@ def cpi_step_noalloc(n: int, m: int, row_ptr, col, val, c: float, x, y, r=None, 
 def set_push(enable: bool) -> None:
     """Push the sparse first family iterates of a query (default) or pull every iteration."""
     _check(library().tpa_set_push(1 if enable else 0))
+
+
+def set_pattern(enable: bool) -> None:
+    """Pattern-only products on unweighted graphs (default: x kept scaled by 1/outdeg, no value
+    array read) or products that read the value array."""
+    _check(library().tpa_set_pattern(1 if enable else 0))
 
 
 # ------------------------------------------------------------- gradients ---

@@ -249,3 +249,46 @@ def test_query_push_deterministic(rmat14, narrow_batches):
     a = tpa().query(rmat14["g"], seeds, S).cpu().numpy()
     b = tpa().query(rmat14["g"], seeds, S).cpu().numpy()
     assert np.array_equal(a, b)
+
+
+def test_pattern_only_products(rmat14):
+    """Pattern-only products (the default: the iterate kept scaled by
+    RN32(1/outdeg), the value array not read) and products that read the value
+    array give the same TPA scores up to FP32 rounding, each within the bars of
+    the oracle, for preprocessing and a query batch; on a weighted graph the
+    setting changes nothing."""
+    import torch
+    t = tpa()
+    seeds = synth.query_seeds(rmat14["cand"], 40, key=21)
+    seeds[0] = 0                                       # the biggest hub: a pulled chunk
+    res = {}
+    try:
+        for mode in (True, False):
+            t.set_pattern(mode)
+            t.preprocess(rmat14["g"], C, T, EPS)
+            r, it = t.get_stranger(rmat14["g"])
+            parity(r.cpu().numpy(), rmat14["rs"], f"r_stranger pattern={mode}")
+            assert abs(it - rmat14["it"]) <= 1
+            out = t.query(rmat14["g"], seeds, S).cpu().numpy()
+            for j in (0, 1, 8, 39):
+                ref = oracle.query(rmat14["og"], int(seeds[j]), C, S, T, rmat14["rs"], EPS)
+                parity(out[:, j], ref, f"pattern={mode} col {j}")
+            res[mode] = out
+        d = np.abs(res[True].astype(np.float64) - res[False])
+        assert d.sum(0).max() <= 1e-5 and d.max() <= 1e-7
+
+        n = 1 << 10
+        s, dst = synth.rmat_edges(10, 16)
+        g = t.build_graph(n, s, dst)
+        w = torch.from_numpy(synth.normal(g.m, key=4)).cuda().exp()
+        t.set_edge_weights(g, w)
+        sd = synth.query_seeds(synth.nodes_with_out_edge(n, s, dst), 8, key=22)
+        outs = []
+        for mode in (True, False):
+            t.set_pattern(mode)
+            t.preprocess(g, C, T, EPS)
+            outs.append(t.query(g, sd, S).clone())
+        assert torch.equal(outs[0], outs[1])
+    finally:
+        t.set_pattern(True)
+        t.preprocess(rmat14["g"], C, T, EPS)

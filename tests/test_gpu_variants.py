@@ -7,7 +7,9 @@ tiles with a ragged tail):
     a node without out-edges), and the same query pulled only;
   - Algorithm 1 with s_iter/t_iter into a caller buffer of kp - 1 columns (the
     accumulator's row stride differs from the padded width);
-  - preprocessing for the width-1 variants.
+  - preprocessing for the width-1 variants;
+each with pattern-only products (the default: x kept scaled by 1/outdeg, no
+value array read) and with products that read the value array.
 Bars as in the other parity tests: L1 <= 1e-5 and max-abs <= 1e-7 per result.
 """
 import numpy as np
@@ -67,12 +69,19 @@ def forced(request):
     t.set_push(True)
 
 
+@pytest.fixture(params=[True, False], ids=["pattern", "valued"])
+def pattern(request):
+    tpa().set_pattern(request.param)
+    yield request.param
+    tpa().set_pattern(True)
+
+
 def columns(k):
     return range(k) if k <= 16 else sorted({0, 1, 2, k // 2, k - 2, k - 1})
 
 
 @pytest.mark.parametrize("forced", variant_ids(), indirect=True)
-def test_variant_query(rmat12, forced):
+def test_variant_query(rmat12, forced, pattern):
     t = tpa()
     kp = forced["kp"]
     seeds = synth.query_seeds(rmat12["light"], kp, key=40 + kp)
@@ -98,7 +107,7 @@ def test_variant_query(rmat12, forced):
 
 
 @pytest.mark.parametrize("forced", variant_ids(), indirect=True)
-def test_variant_cpi_parts(rmat12, forced):
+def test_variant_cpi_parts(rmat12, forced, pattern):
     t = tpa()
     kp = forced["kp"]
     k = max(1, kp - 1)
@@ -114,7 +123,7 @@ def test_variant_cpi_parts(rmat12, forced):
 
 
 @pytest.mark.parametrize("forced", [v for v in variant_ids()], indirect=True)
-def test_variant_preprocess(rmat12, forced):
+def test_variant_preprocess(rmat12, forced, pattern):
     if forced["kp"] != 1:
         pytest.skip("preprocessing runs one column")
     t = tpa()
