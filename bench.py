@@ -50,12 +50,37 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--accuracy", type=int, default=0, metavar="SEEDS",
+                    help="run the accuracy study of TPA's approximations (S sweep at T=10, T sweep at S=5, "
+                         "recall@100/500) for SEEDS seeds on the GPU path, print one JSON line and exit")
     ap.add_argument("--valued-products", action="store_true",
                     help="products that read the value array instead of the default pattern-only products")
     ap.add_argument("--profile-case", choices=["preprocess", "query8"], default=None,
                     help="run one small case for an ncu capture and exit (no JSON line): preprocessing of the "
                          "graph, or two 8-seed queries of light seeds after it")
     return ap.parse_args(argv)
+
+
+def accuracy_study(args):
+    """Errors of the neighbor and stranger approximations and of r_TPA against
+    exact CPI (Table 3's quantities, the S and T sweeps of Section IV) on the
+    R-MAT graph, SEEDS seeds uniform over nodes with an out-edge (key 2)."""
+    import torch
+    import synth
+    import paper_1708_02574_gb300 as tpa
+    from paper_1708_02574_gb300 import accuracy
+    tpa.set_pattern(not args.valued_products)
+    n = 1 << args.scale
+    src, dst = synth.rmat_edges(args.scale, args.edge_factor)
+    g = tpa.build_graph(n, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda())
+    cand = synth.nodes_with_out_edge(n, src, dst)
+    seeds = torch.from_numpy(synth.query_seeds(cand, args.accuracy)).cuda()
+    t0 = time.perf_counter()
+    res = accuracy.sweep(g, seeds, C, EPS, S_fixed=S, T_fixed=T, ks=(100, 500))
+    print(json.dumps({"study": "tpa_accuracy", "data": "synthetic",
+                      "graph": f"R-MAT scale {args.scale} ef {args.edge_factor}", "n": n, "m": g.m,
+                      "c": C, "eps": EPS, "seeds": args.accuracy, "seconds": time.perf_counter() - t0, **res}))
+    return 0
 
 
 def profile_case(args):
@@ -270,6 +295,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.profile_case:
         return profile_case(args)
+    if args.accuracy:
+        return accuracy_study(args)
     rank, world, local = dist_env()
     if args.impl == "reference":
         if rank == 0:

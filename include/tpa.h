@@ -97,6 +97,21 @@ tpa_status tpa_get_stranger(const tpa_graph *g, float *out, int64_t *iters, void
 tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *out, void *stream);
 
 /*
+ * Algorithm 3 for nsets seed sets (personalised PageRank with the seed vector
+ * q_s = 1/|S| of Section II-C): column j starts from x0 = c q_j with
+ * q_j = 1/|S_j| on each member of set j, members[set_ptr[j] .. set_ptr[j+1])
+ * (a node listed twice counts twice), then r_TPA as for tpa_query.  By
+ * linearity each column equals the mean of its members' single-seed TPA
+ * vectors.  set_ptr: int64[nsets + 1], set_ptr[0] = 0, strictly increasing
+ * (no empty set); members: int32, 0 <= id < n; both host or device.  out:
+ * device float32[n * nsets], node-major.  The first two iterations are pulled
+ * (the push path starts from single seeds).
+ * Errors: TPA_ESTATE before tpa_preprocess; TPA_EINVAL.
+ */
+tpa_status tpa_query_sets(tpa_graph *g, const int64_t *set_ptr, const int32_t *members, int nsets, int S,
+                          float *out, void *stream);
+
+/*
  * Algorithm 1 (CPI) for k single-seed vectors q = e_{s_j}: returns
  * r_j = sum of x_i for s_iter <= i <= t_iter (t_iter < 0: no limit), each
  * column stopping after the first i with ||x_i||_1 < eps.  out is

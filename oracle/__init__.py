@@ -59,6 +59,8 @@ def _load():
         lib.orc_query.argtypes = [i64, P, P, P, f64, f64, i64, i64, ctypes.c_int32, P, P, P]
         lib.orc_cpi_exact.restype = i64
         lib.orc_cpi_exact.argtypes = [i64, P, P, P, f64, f64, ctypes.c_int32, P]
+        lib.orc_query_set.restype = i64
+        lib.orc_query_set.argtypes = [i64, P, P, P, f64, f64, i64, i64, i64, P, P, P]
         if hasattr(lib, "orc_adjoint_grad"):
             _bind_adjoint(lib)
         _lib = lib
@@ -156,6 +158,18 @@ def query(g: Graph, seed: int, c: float, S: int, T: int, r_stranger: np.ndarray,
     if it < 0:
         raise ValueError("orc_query")
     return (out, fam) if want_family else out
+
+
+def query_set(g: Graph, members, c: float, S: int, T: int, r_stranger: np.ndarray, eps: float = 1e-9):
+    """Algorithm 3 for a seed set: q = 1/|S| on each listed member (a repeated member counts again)."""
+    mem = np.ascontiguousarray(members, dtype=np.int32)
+    out = np.empty(g.n)
+    rs = np.ascontiguousarray(r_stranger, dtype=np.float64)
+    it = _load().orc_query_set(g.n, _p(g.rp_t), _p(g.col_t), _p(g.val_t), c, eps, S, T, mem.size, _p(mem),
+                               _p(rs), _p(out))
+    if it < 0:
+        raise ValueError("orc_query_set")
+    return out
 
 
 def cpi_exact(g: Graph, seed: int, c: float, eps: float = 1e-9):

@@ -222,6 +222,31 @@ int64_t orc_query(int64_t n, const int64_t *rp, const int32_t *col, const double
     return it;
 }
 
+/* Algorithm 3 for a seed set (the seed vector of Algorithm 1 with
+ * q_s = 1/|S| for s in S, Section II-C): members[0..len) lists the set, a
+ * node listed twice counting twice.  r_family from iterations 0..S-1 of CPI
+ * from that q, then r_TPA = r_family + alpha r_family + r~_stranger.
+ * Returns the CPI iteration count or -1. */
+int64_t orc_query_set(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                      double c, double eps, int64_t S, int64_t T, int64_t len, const int32_t *members,
+                      const double *r_stranger, double *out)
+{
+    if (len < 1 || S < 1 || T < S) return -1;
+    for (int64_t j = 0; j < len; ++j)
+        if (members[j] < 0 || members[j] >= n) return -1;
+    double *q = (double *)calloc((size_t)n, sizeof(double));
+    double *fam = (double *)malloc((size_t)n * sizeof(double));
+    if (!q || !fam) { free(q); free(fam); return -1; }
+    const double w = (g_fault == 9) ? 1.0 : 1.0 / (double)len;   /* planted: unnormalised q */
+    for (int64_t j = 0; j < len; ++j) q[members[j]] += w;
+    const int64_t it = orc_cpi(n, rp, col, val, q, c, eps, 0, S - 1, fam, NULL, 0);
+    const double alpha = orc_alpha(c, S, T);
+    for (int64_t v = 0; v < n; ++v) out[v] = fam[v] + alpha * fam[v] + r_stranger[v];
+    free(q);
+    free(fam);
+    return it;
+}
+
 /* Exact RWR by CPI (Algorithm 1 with s_iter = 0 and no terminal iteration). */
 int64_t orc_cpi_exact(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
                       double c, double eps, int32_t s, double *out)

@@ -32,6 +32,7 @@ from .tpa import (  # noqa: F401
     load_preprocessed,
     preprocess,
     query,
+    query_sets,
     save_preprocessed,
     set_batch_width,
     set_cpi_batch_width,

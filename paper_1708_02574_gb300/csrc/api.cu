@@ -173,7 +173,7 @@ void tpa_free_graph(tpa_graph *g)
                       &g->r_str,
                       &g->perm_a2t, &g->w_a, &g->inv_d, &g->row_a, &g->ws.u, &g->ws.touched, &g->ws.x2,
                       &g->ws.x, &g->ws.y, &g->ws.r, &g->ws.carry, &g->ws.head, &g->ws.tl1, &g->ws.fix,
-                      &g->ws.ctl, &g->ws.seeds, &g->ws.out, &g->ws.iters};
+                      &g->ws.ctl, &g->ws.seeds, &g->ws.sets, &g->ws.out, &g->ws.iters};
     for (DevBuf *b : bufs) b->release(s);
     g->ws.cpart.release(s);
     for (tpa::BinPlan *B : {&g->bins_t, &g->bins_a})
@@ -326,6 +326,67 @@ tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *ou
             TPA_CUDA(cudaMemcpyAsync(out, dout, (size_t)g->n * k * sizeof(float), cudaMemcpyDeviceToHost, s));
         TPA_CUDA(cudaStreamSynchronize(s));
     }
+    API_END
+}
+
+tpa_status tpa_query_sets(tpa_graph *g, const int64_t *set_ptr, const int32_t *members, int nsets, int S,
+                          float *out, void *stream)
+{
+    API_BEGIN
+    TPA_REQUIRE(g != nullptr, "tpa_query_sets: NULL graph");
+    if (!g->has_pre) {
+        set_error("tpa_query_sets: tpa_preprocess has not run");
+        return TPA_ESTATE;
+    }
+    TPA_REQUIRE(nsets >= 1, "tpa_query_sets: nsets = %d < 1", nsets);
+    TPA_REQUIRE(S >= 1 && S <= g->T, "tpa_query_sets: S = %d outside [1, T = %d]", S, g->T);
+    TPA_REQUIRE(set_ptr && members && out, "tpa_query_sets: NULL set_ptr, members or out");
+    TPA_REQUIRE(is_device_ptr(out), "tpa_query_sets: out must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int64_t> hp((size_t)nsets + 1);
+    if (is_device_ptr(set_ptr)) {
+        TPA_CUDA(cudaMemcpyAsync(hp.data(), set_ptr, hp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        TPA_CUDA(cudaStreamSynchronize(s));
+    } else {
+        memcpy(hp.data(), set_ptr, hp.size() * sizeof(int64_t));
+    }
+    TPA_REQUIRE(hp[0] == 0, "tpa_query_sets: set_ptr[0] = %lld, not 0", (long long)hp[0]);
+    for (int j = 0; j < nsets; ++j)
+        TPA_REQUIRE(hp[j + 1] > hp[j], "tpa_query_sets: seed set %d is empty or set_ptr decreases", j);
+    const int64_t total = hp[nsets];
+    TPA_REQUIRE(total <= ((int64_t)1 << 31) - 1, "tpa_query_sets: %lld members, more than 2^31 - 1",
+                (long long)total);
+    std::vector<int32_t> hm((size_t)total);
+    if (is_device_ptr(members)) {
+        TPA_CUDA(cudaMemcpyAsync(hm.data(), members, (size_t)total * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        TPA_CUDA(cudaStreamSynchronize(s));
+    } else {
+        memcpy(hm.data(), members, (size_t)total * sizeof(int32_t));
+    }
+    for (int64_t e = 0; e < total; ++e)
+        TPA_REQUIRE(hm[e] >= 0 && hm[e] < g->n, "member %d (index %lld) is outside [0, %lld)", hm[e], (long long)e,
+                    (long long)g->n);
+    g->ws.seeds.ensure((size_t)total * sizeof(int32_t), s);
+    g->ws.sets.ensure(hp.size() * sizeof(int64_t), s);
+    TPA_CUDA(cudaMemcpyAsync(g->ws.seeds.p, hm.data(), (size_t)total * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    TPA_CUDA(cudaMemcpyAsync(g->ws.sets.p, hp.data(), hp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CpiArgs a;
+    a.seeds = g->ws.seeds.as<int32_t>();
+    a.set_ptr = g->ws.sets.as<int64_t>();
+    a.k = nsets;
+    a.c = g->c;
+    a.eps = g->eps;
+    a.s_iter = 0;
+    a.t_iter = S - 1;
+    a.r_internal = true;
+    a.tpa_final = true;
+    a.alpha = alpha_of(g->c, S, g->T);
+    a.r_str = g->r_str.as<float>();
+    a.out = out;
+    a.ldo = nsets;
+    run_cpi(g, a, s);
+    // the host copies above read from pageable vectors: finish them before those go
+    TPA_CUDA(cudaStreamSynchronize(s));
     API_END
 }
 

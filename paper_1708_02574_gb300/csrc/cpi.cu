@@ -546,7 +546,8 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     // CUDA graph) the device chooses (push_decide_k) and the kernels of the
     // other branch return at once.  On both branches x2 ends in the x2
     // buffer, which iteration 3 reads.
-    const bool two_way = g_push && a.tpa_final && a.seeds && last >= 3 && KP <= PUSH_MAX_KP && a.r_internal;
+    const bool two_way =
+        g_push && a.tpa_final && a.seeds && !a.set_ptr && last >= 3 && KP <= PUSH_MAX_KP && a.r_internal;
     bool host_decided = false, host_push = false;
     if (two_way && a.seed_outdeg) {
         host_decided = true;
@@ -589,6 +590,13 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
                                                          ldr, a.s_iter == 0 ? 1 : 0, W.ctl.p, gate_pull, inv_deg);
             note_launch("init");
         }
+        TPA_CHECK_LAUNCH();
+    } else if (a.set_ptr) {   // seed sets: zero, then scatter c / |S_j| over each set's members
+        init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, nullptr, kc, c_val, 0.0f, r, ldr,
+                                                     a.s_iter == 0 ? 1 : 0, W.ctl.p, GATE_NONE, inv_deg);
+        scatter_sets_k<<<kc, 256, 0, s>>>(W.x.as<float>(), KP, a.set_ptr + k0, a.seeds, c_val, r, ldr,
+                                          a.s_iter == 0 ? 1 : 0, inv_deg);
+        note_launch("init", 2);
         TPA_CHECK_LAUNCH();
     } else {
         init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, a.seeds ? a.seeds + k0 : nullptr, kc,

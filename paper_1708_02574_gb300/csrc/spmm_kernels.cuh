@@ -1486,6 +1486,23 @@ __global__ void init_k(float *x, int KP, int64_t n, const int32_t *seeds, int k,
     }
 }
 
+// x0 of seed-set columns (x and r zeroed before): block j adds c / |S_j| for
+// each member of set j (scaled by inv_deg in x for pattern-only products;
+// unscaled into r when acc0).  Repeated members add equal values, so the
+// order of the atomics does not change the sums.
+__global__ void scatter_sets_k(float *x, int KP, const int64_t *set_ptr, const int32_t *members, float c_val,
+                               float *r, int64_t ldr, int acc0, const float *inv_deg)
+{
+    const int j = blockIdx.x;
+    const int64_t e0 = set_ptr[j], e1 = set_ptr[j + 1];
+    const float w = c_val / (float)(e1 - e0);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int64_t v = members[e];
+        atomicAdd(x + v * KP + j, inv_deg ? w * __ldg(inv_deg + v) : w);
+        if (r && acc0) atomicAdd(r + v * ldr + j, w);
+    }
+}
+
 __global__ void ctl_init_k(void *ctl, int k)
 {
     const CtlView cv = ctl_view(ctl);

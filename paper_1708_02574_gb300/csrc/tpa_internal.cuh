@@ -100,7 +100,8 @@ struct Workspace {
     DevBuf carry, head, tl1;   // per-tile carries, deferred heads, per-tile L1
     DevBuf fix;             // fixup partials
     DevBuf ctl;             // control block (see Ctl)
-    DevBuf seeds;           // int32 seeds
+    DevBuf seeds;           // int32 seeds (or seed-set members)
+    DevBuf sets;            // int64 seed-set offsets
     DevBuf out;             // device staging for host outputs
     DevBuf iters;           // int32 per-column iteration counts
     DevBuf u;               // push path: 64-bit fixed-point accumulator [n][KP]
@@ -193,6 +194,9 @@ struct CpiArgs {
     // host int32[k]: out-degrees of the seeds.  Given, query chunks choose
     // their push/pull branch on the host; absent (graph capture), on the device.
     const int32_t *seed_outdeg = nullptr;
+    // seed sets (device int64[k+1]): column j starts from q = 1/|S_j| on the
+    // members seeds[set_ptr[j] .. set_ptr[j+1]) instead of one seed
+    const int64_t *set_ptr = nullptr;
 };
 
 // adjoint.cu

@@ -43,6 +43,7 @@ def library():
         "tpa_preprocess": (i32, [P, f64, i32, f64, P]),
         "tpa_get_stranger": (i32, [P, P, ctypes.POINTER(i64), P]),
         "tpa_query": (i32, [P, P, i32, i32, P, P]),
+        "tpa_query_sets": (i32, [P, P, P, i32, i32, P, P]),
         "tpa_cpi": (i32, [P, P, i32, f64, f64, i32, i32, P, P, P]),
         "tpa_cpi_exact": (i32, [P, ctypes.c_int32, f64, f64, P, P, P]),
         "tpa_save_preprocessed": (i32, [P, ctypes.c_char_p]),
@@ -196,6 +197,22 @@ def query(g: Graph, seeds, S: int = 5, out=None):
     if out is None:
         out = torch.empty((n, k), dtype=torch.float32, device="cuda")
     _check(library().tpa_query(g.handle, _ptr(s), int(k), int(S), _ptr(out), _stream()))
+    return out
+
+
+def query_sets(g: Graph, sets, S: int = 5, out=None):
+    """tpa_query_sets (Algorithm 3 with q = 1/|S| over each seed set); ``sets`` is a
+    list of member lists.  Returns float32 [n, len(sets)]."""
+    torch = _torch()
+    sets = [list(x) for x in sets]
+    ptr = np.zeros(len(sets) + 1, dtype=np.int64)
+    ptr[1:] = np.cumsum([len(x) for x in sets])
+    mem = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.int64) for x in sets]) if sets else
+                               np.zeros(0), dtype=np.int32)
+    n, _ = graph_info(g)
+    if out is None:
+        out = torch.empty((n, len(sets)), dtype=torch.float32, device="cuda")
+    _check(library().tpa_query_sets(g.handle, _ptr(ptr), _ptr(mem), int(len(sets)), int(S), _ptr(out), _stream()))
     return out
 
 

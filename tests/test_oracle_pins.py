@@ -8,7 +8,8 @@ Each ``pin_*`` function raises AssertionError when the oracle disagrees with:
   * closed forms on the directed cycle and the bidirectional star,
   * the L1-mass identities of Lemma 2 and the iteration count of Lemma 4,
   * the error bounds of Lemma 1, Lemma 3 and Theorem 2,
-  * the bound constants printed in Table 3 (tests/golden/table3_bounds.txt).
+  * the bound constants printed in Table 3 (tests/golden/table3_bounds.txt),
+  * seed sets: matrix powers applied to q = 1/|S| and linearity in q.
 
 ``test_planted_mistakes_are_caught`` plants plausible mistakes in the oracle
 (on the CPU) and checks that at least one pin fails for each of them.
@@ -192,6 +193,28 @@ def pin_bounds():
                 assert np.abs(fam + nb + st - exact).sum() < 1e-12
 
 
+def pin_query_set():
+    """Seed sets (q_s = 1/|S|, Section II-C): r_TPA from the matrix powers of
+    P = (1-c) A~^T applied to that q, and the linearity of Algorithm 3 in q
+    (the mean of the members' single-seed vectors, a repeated member counting
+    twice)."""
+    for kind, n, s, d in graphs():
+        g = oracle.build_graph(n, s, d)
+        P = (1 - C) * dense_A(n, s, d).T
+        for S, T in ((5, 10), (2, 4)):
+            rs, _ = oracle.preprocess(g, C, T, eps=1e-15)
+            a = ((1 - C) ** S - (1 - C) ** T) / (1 - (1 - C) ** S)
+            for members in ([3], [0, n - 1, n // 2], [5, 5, n - 2]):
+                q = np.zeros(n)
+                for v in members:
+                    q[v] += 1.0 / len(members)
+                fam = sum(C * np.linalg.matrix_power(P, i) @ q for i in range(S))
+                got = oracle.query_set(g, members, C, S, T, rs, eps=1e-15)
+                assert np.abs(got - ((1 + a) * fam + rs)).sum() < 1e-12, (kind, S, T, members)
+                mean = sum(oracle.query(g, v, C, S, T, rs, eps=1e-15) for v in members) / len(members)
+                assert np.abs(got - mean).sum() < 1e-12, (kind, S, T, members)
+
+
 def read_table3():
     rows = []
     with open(GOLDEN) as f:
@@ -216,7 +239,7 @@ def pin_table3_constants():
 
 
 PINS = [pin_csr_bruteforce, pin_cpi_dense_solve, pin_tpa_matrix_powers, pin_cycle_closed_form,
-        pin_star_closed_form, pin_lemma2_mass, pin_bounds, pin_table3_constants]
+        pin_star_closed_form, pin_lemma2_mass, pin_bounds, pin_table3_constants, pin_query_set]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -227,7 +250,7 @@ def test_pin(pin):
 
 FAULTS = {1: "A~ instead of A~^T", 2: "x0 dropped from r", 3: "decay (1-c) dropped",
           4: "alpha sign flipped", 5: "t_iter exclusive", 6: "normalised by in-degree",
-          7: "norm tested before adding x_i", 8: "PageRank q unnormalised"}
+          7: "norm tested before adding x_i", 8: "PageRank q unnormalised", 9: "seed-set q unnormalised"}
 
 
 @pytest.mark.parametrize("fault", sorted(FAULTS), ids=[FAULTS[k] for k in sorted(FAULTS)])
