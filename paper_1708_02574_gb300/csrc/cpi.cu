@@ -216,23 +216,25 @@ static int64_t launch_spmvg(const Params &p, cudaStream_t s)
 template <int G, int V, int ITEMS, int PF, int WARPS, int MINB>
 static int64_t launch_spmvp(const Params &p, cudaStream_t s)
 {
-    constexpr size_t smem = WARPS * PipeSmem<G, V, ITEMS>::PER_WARP;
-    static_assert(smem <= 227 * 1024, "shared memory per block");
     // one instantiation per product mode, so the valued kernel carries no test of it
+    constexpr size_t smem_v = WARPS * PipeSmem<G, V, ITEMS, false>::PER_WARP;
+    constexpr size_t smem_p = WARPS * PipeSmem<G, V, ITEMS, true>::PER_WARP;
+    static_assert(smem_v <= 227 * 1024 && smem_p <= 227 * 1024, "shared memory per block");
     auto *const valued = spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB, false>;
     auto *const pattern = spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB, true>;
-    static int per_sm = 0;
-    if (!per_sm) {
-        TPA_CUDA(cudaFuncSetAttribute(valued, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        TPA_CUDA(cudaFuncSetAttribute(pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int a = 0, b = 0;
-        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, valued, WARPS * 32, smem));
-        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pattern, WARPS * 32, smem));
-        per_sm = std::max(std::min(a, b), 1);
+    static int per_sm_v = 0, per_sm_p = 0;
+    if (!per_sm_v) {
+        TPA_CUDA(cudaFuncSetAttribute(valued, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v));
+        TPA_CUDA(cudaFuncSetAttribute(pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_v, valued, WARPS * 32, smem_v));
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_p, pattern, WARPS * 32, smem_p));
+        per_sm_v = std::max(per_sm_v, 1);
+        per_sm_p = std::max(per_sm_p, 1);
     }
+    const int per_sm = p.inv_deg ? per_sm_p : per_sm_v;
     const int64_t grid = std::min<int64_t>((p.tiles + WARPS - 1) / WARPS, (int64_t)per_sm * num_sms());
-    if (p.inv_deg) pattern<<<(unsigned)grid, WARPS * 32, smem, s>>>(p);
-    else valued<<<(unsigned)grid, WARPS * 32, smem, s>>>(p);
+    if (p.inv_deg) pattern<<<(unsigned)grid, WARPS * 32, smem_p, s>>>(p);
+    else valued<<<(unsigned)grid, WARPS * 32, smem_v, s>>>(p);
     return grid * WARPS;
 }
 

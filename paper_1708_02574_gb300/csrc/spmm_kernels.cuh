@@ -209,11 +209,13 @@ enum ProductMode : int { PM_RUNTIME = 0, PM_VALUED = 1, PM_PATTERN = 2 };
 // Store one finished row of the iterate as the next product's x: scaled by
 // the row's inverse out-degree in pattern-only mode.
 template <int V, int PM = PM_RUNTIME>
-__device__ __forceinline__ void st_next_row(const Params &p, int64_t row, float *dst, const float (&y)[V])
+__device__ __forceinline__ void st_next_row(const Params &p, int64_t row, float *dst, const float (&y)[V],
+                                            float w_row)
 {
     const bool pattern = PM == PM_PATTERN || (PM == PM_RUNTIME && p.inv_deg != nullptr);
     if (pattern) {
-        const float w = __ldg(p.inv_deg + row);
+        // a kernel compiled for pattern-only products passes inv_deg[row] (staged)
+        const float w = PM == PM_PATTERN ? w_row : __ldg(p.inv_deg + row);
         float xs[V];
 #pragma unroll
         for (int j = 0; j < V; ++j) xs[j] = y[j] * w;
@@ -226,13 +228,13 @@ __device__ __forceinline__ void st_next_row(const Params &p, int64_t row, float 
 // Epilogue of Algorithm 1 for one finished row and V consecutive columns.
 template <int KP, int V, int PM = PM_RUNTIME>
 __device__ __forceinline__ void epilogue(const Params &p, int64_t row, int col0, const float (&s)[V],
-                                         const int (&alive)[V], float (&l1)[V])
+                                         const int (&alive)[V], float (&l1)[V], float w_row = 0.0f)
 {
     float yv[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) yv[j] = p.decay * s[j];
     if (p.mode == MODE_ACC) {
-        st_next_row<V, PM>(p, row, p.y + row * KP + col0, yv);
+        st_next_row<V, PM>(p, row, p.y + row * KP + col0, yv, w_row);
         if (p.accumulate) {
             if (p.ldr == KP && V > 1) {
                 // whole padded row contiguous: vector read-modify-write
@@ -900,13 +902,13 @@ __device__ __forceinline__ void red_row(float *p, const float (&v)[V])
 // loads: y stored, r += y by a vector atomic add.
 template <int KP, int V, int PM = PM_RUNTIME>
 __device__ __forceinline__ void epilogue_red(const Params &p, int64_t row, int col0, const float (&s)[V],
-                                             const int (&alive)[V], float (&l1)[V])
+                                             const int (&alive)[V], float (&l1)[V], float w_row = 0.0f)
 {
     float yv[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) yv[j] = p.decay * s[j];
     if (p.mode == MODE_ACC) {
-        st_next_row<V, PM>(p, row, p.y + row * KP + col0, yv);
+        st_next_row<V, PM>(p, row, p.y + row * KP + col0, yv, w_row);
         if (p.accumulate) {
             if (p.ldr == KP) {
                 float add[V];
@@ -924,17 +926,21 @@ __device__ __forceinline__ void epilogue_red(const Params &p, int64_t row, int c
     for (int j = 0; j < V; ++j) l1[j] += alive[j] ? fabsf(yv[j]) : 0.0f;
 }
 
-template <int G, int V, int ITEMS>
+template <int G, int V, int ITEMS, bool PAT>
 struct __align__(16) PipeTile {
     static constexpr int NW = 32 / G;
     static constexpr int L = NW * ITEMS;
     static constexpr int CH = (L + 6) / 4 + 1;      // 4-nonzero chunks a tile's nonzeros can span
     static constexpr int PCH = (2 * CH + 7) & ~7;   // 16-byte pair chunks, whole swizzle groups
+    static constexpr int CCH = (CH + 7) & ~7;       // 16-byte column chunks (pattern-only)
     int64_t rp[L + 2];   // row_ptr[x0+1 .. x1], then a sentinel y0 + INT_MAX
-    // (column, value bits) of nonzeros y0a .. y0a + 4 * chunks, y0a = y0
-    // rounded down to a multiple of 4; nonzero e of the slice is the pair at
-    // word pair_word(e): one 8-byte shared load per step
-    int32_t cv[4 * PCH];
+    // Valued products: (column, value bits) of nonzeros y0a .. y0a + 4 * chunks,
+    // y0a = y0 rounded down to a multiple of 4; nonzero e of the slice is the
+    // pair at word pair_word(e): one 8-byte shared load per step.
+    // Pattern-only products: the columns alone, nonzero e at col_word(e).
+    int32_t cv[PAT ? 4 * CCH : 4 * PCH];
+    // pattern-only: inv_deg of the tile's rows x0 .. x1-1
+    float inv[PAT ? ((L + 3) & ~3) : 4];
 };
 
 // Slot of 16-byte chunk q: an XOR swizzle inside each group of 8 chunks (one
@@ -942,6 +948,8 @@ struct __align__(16) PipeTile {
 __device__ __forceinline__ int chunk_slot(int q) { return (q & ~7) | ((q ^ (q >> 3)) & 7); }
 // First word of the (column, value) pair of nonzero e (two pairs per chunk).
 __device__ __forceinline__ int pair_word(int e) { return 4 * chunk_slot(e >> 1) + 2 * (e & 1); }
+// Word of the column of nonzero e when only columns are staged (four per chunk).
+__device__ __forceinline__ int col_word(int e) { return 4 * chunk_slot(e >> 2) + (e & 3); }
 
 struct TileMeta {
     int64_t y0, y1;
@@ -1012,7 +1020,7 @@ __device__ __forceinline__ void load_chunks(const Params &p, const TileMeta &m, 
 // past 32 * RC (a few per tile at most; the caller commits).
 template <int RC, bool PAT>
 __device__ __forceinline__ void stage_tile(const Params &p, const TileMeta &m, const ChunkRegs<RC> &r,
-                                           int64_t *rp_s, int32_t *cv_s, int lane)
+                                           int64_t *rp_s, int32_t *cv_s, float *inv_s, int lane)
 {
     const int chunks = tile_chunks(m);
     const int64_t y0a = m.y0 & ~(int64_t)3;
@@ -1021,27 +1029,36 @@ __device__ __forceinline__ void stage_tile(const Params &p, const TileMeta &m, c
         const int q = lane + 32 * k;
         if (q < chunks) {
             const int4 c = r.c[k];
-            const float4 v = PAT ? make_float4(1.0f, 1.0f, 1.0f, 1.0f) : r.v[k];
-            *reinterpret_cast<int4 *>(cv_s + 4 * chunk_slot(2 * q)) =
-                make_int4(c.x, __float_as_int(v.x), c.y, __float_as_int(v.y));
-            *reinterpret_cast<int4 *>(cv_s + 4 * chunk_slot(2 * q + 1)) =
-                make_int4(c.z, __float_as_int(v.z), c.w, __float_as_int(v.w));
+            if constexpr (PAT) {
+                *reinterpret_cast<int4 *>(cv_s + 4 * chunk_slot(q)) = c;
+            } else {
+                const float4 v = r.v[k];
+                *reinterpret_cast<int4 *>(cv_s + 4 * chunk_slot(2 * q)) =
+                    make_int4(c.x, __float_as_int(v.x), c.y, __float_as_int(v.y));
+                *reinterpret_cast<int4 *>(cv_s + 4 * chunk_slot(2 * q + 1)) =
+                    make_int4(c.z, __float_as_int(v.z), c.w, __float_as_int(v.w));
+            }
         }
     }
     for (int e = 128 * RC + lane; e < 4 * chunks; e += 32) {
-        cp_async<4>(cv_s + pair_word(e), p.col + y0a + e);
-        if constexpr (PAT) cv_s[pair_word(e) + 1] = __float_as_int(1.0f);
-        else cp_async<4>(cv_s + pair_word(e) + 1, p.val + y0a + e);
+        if constexpr (PAT) {
+            cp_async<4>(cv_s + col_word(e), p.col + y0a + e);
+        } else {
+            cp_async<4>(cv_s + pair_word(e), p.col + y0a + e);
+            cp_async<4>(cv_s + pair_word(e) + 1, p.val + y0a + e);
+        }
     }
     const int nrows = m.x1 - m.x0;
     for (int i = lane; i < nrows; i += 32) cp_async<8>(rp_s + i, p.rp + m.x0 + i + 1);
+    if constexpr (PAT)
+        for (int i = lane; i < nrows; i += 32) cp_async<4>(inv_s + i, p.inv_deg + m.x0 + i);
     if (lane == 0) rp_s[nrows] = m.y0 + 0x7fffffff;
 }
 
 template <int G, int V, int ITEMS, int PF, bool PAT>
 __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, int64_t t, const int64_t *rp_s,
-                                          const int32_t *cv_s, float *rs_s, int lane, const int (&alive)[V],
-                                          float (&l1)[V])
+                                          const int32_t *cv_s, const float *inv_s, float *rs_s, int lane,
+                                          const int (&alive)[V], float (&l1)[V])
 {
     constexpr int NW = 32 / G, KP = G * V;
     const int w = lane / G, col0 = (lane % G) * V;
@@ -1075,9 +1092,14 @@ __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, in
         for (int it = 0; it < PF; ++it) {
             if (c0 + it < avail) {
                 if (ys < row_end) {
-                    const int2 e = *reinterpret_cast<const int2 *>(cv_s + pair_word(off + ys));
-                    vv[it] = __int_as_float(e.y);
-                    ld_row<V>(p.x + (int64_t)e.x * KP + col0, xv[it]);
+                    if constexpr (PAT) {   // every value is folded into x
+                        vv[it] = 1.0f;
+                        ld_row<V>(p.x + (int64_t)cv_s[col_word(off + ys)] * KP + col0, xv[it]);
+                    } else {
+                        const int2 e = *reinterpret_cast<const int2 *>(cv_s + pair_word(off + ys));
+                        vv[it] = __int_as_float(e.y);
+                        ld_row<V>(p.x + (int64_t)e.x * KP + col0, xv[it]);
+                    }
                     nzmask |= 1u << it;
                     ++ys;
                 } else {
@@ -1143,16 +1165,17 @@ __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, in
         float sv[V];
         ld_row_smem<V>(rs_s + r * KP + col0, sv);
         if (p.mode == MODE_ACC)
-            epilogue_red<KP, V, PAT ? PM_PATTERN : PM_VALUED>(p, (int64_t)(m.x0 + r), col0, sv, alive, l1);
+            epilogue_red<KP, V, PAT ? PM_PATTERN : PM_VALUED>(p, (int64_t)(m.x0 + r), col0, sv, alive, l1,
+                                                              PAT ? inv_s[r] : 0.0f);
         else
             epilogue<KP, V, PAT ? PM_PATTERN : PM_VALUED>(p, (int64_t)(m.x0 + r), col0, sv, alive, l1);
     }
 }
 
 // Shared memory per warp: two tile buffers and the row sums of one tile.
-template <int G, int V, int ITEMS>
+template <int G, int V, int ITEMS, bool PAT>
 struct PipeSmem {
-    using PT = PipeTile<G, V, ITEMS>;
+    using PT = PipeTile<G, V, ITEMS, PAT>;
     static constexpr size_t RS = (size_t)PT::L * G * V * sizeof(float);
     static constexpr size_t PER_WARP = 2 * sizeof(PT) + RS;
 };
@@ -1161,8 +1184,8 @@ struct PipeSmem {
 template <int G, int V, int ITEMS, int PF, int WARPS, int MINB, bool PAT>
 __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
 {
-    using PT = PipeTile<G, V, ITEMS>;
-    using SM = PipeSmem<G, V, ITEMS>;
+    using PT = PipeTile<G, V, ITEMS, PAT>;
+    using SM = PipeSmem<G, V, ITEMS, PAT>;
     static_assert(ITEMS % PF == 0, "PF");
     static_assert(PF <= 32, "PF");
     static_assert(sizeof(PT) % 16 == 0 && offsetof(PT, cv) % 16 == 0, "layout");
@@ -1189,20 +1212,20 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
     ChunkRegs<RC> rg;
     if (t < p.tiles) {
         load_chunks<RC, PAT>(p, cur, rg, lane);   // the first tile waits for its loads
-        stage_tile<RC, PAT>(p, cur, rg, buf[0].rp, buf[0].cv, lane);
+        stage_tile<RC, PAT>(p, cur, rg, buf[0].rp, buf[0].cv, buf[0].inv, lane);
     }
     cp_async_commit();
     TileMeta nxt = tile_meta(p, t + stride);
     load_chunks<RC, PAT>(p, nxt, rg, lane);
     int b = 0;
     for (; t < p.tiles; t += stride) {
-        if (t + stride < p.tiles) stage_tile<RC, PAT>(p, nxt, rg, buf[b ^ 1].rp, buf[b ^ 1].cv, lane);
+        if (t + stride < p.tiles) stage_tile<RC, PAT>(p, nxt, rg, buf[b ^ 1].rp, buf[b ^ 1].cv, buf[b ^ 1].inv, lane);
         cp_async_commit();
         const TileMeta after = tile_meta(p, t + 2 * stride);
         load_chunks<RC, PAT>(p, after, rg, lane);   // in flight during this walk
         cp_async_wait_group<1>();              // this tile's copies have landed
         __syncwarp();
-        walk_tile<G, V, ITEMS, PF, PAT>(p, cur, t, buf[b].rp, buf[b].cv, rs_s, lane, alive, l1);
+        walk_tile<G, V, ITEMS, PF, PAT>(p, cur, t, buf[b].rp, buf[b].cv, buf[b].inv, rs_s, lane, alive, l1);
         __syncwarp();                          // buffers and row sums are rewritten next iteration
         cur = nxt;
         nxt = after;
