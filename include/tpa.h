@@ -91,7 +91,10 @@ tpa_status tpa_get_stranger(const tpa_graph *g, float *out, int64_t *iters, void
  *   r_TPA = (1 + alpha) r_family + r~_stranger,
  *   alpha = ((1-c)^S - (1-c)^T) / (1 - (1-c)^S)   (Section III-B),
  * using the c and T of tpa_preprocess.  out is float32[n * k], node-major.
- * Requires 1 <= S <= T, k >= 1, 0 <= seeds[j] < n.
+ * Seeds run in chunks (tpa_set_batch_width); seeds with more out-edges than
+ * the push branch takes (256) are moved into the last chunks of the query,
+ * so that the other chunks push x1 and x2; every column still lands at its
+ * seed's position.  Requires 1 <= S <= T, k >= 1, 0 <= seeds[j] < n.
  * Errors: TPA_ESTATE before tpa_preprocess; TPA_EINVAL.
  */
 tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *out, void *stream);
@@ -259,7 +262,11 @@ tpa_status tpa_set_pattern(int enable);
  * server keeps its own workspace (about 6 n * 8 floats for chunks of 8 seeds)
  * and graphs that point at it and at the graph's CSR: it must be freed before
  * the graph, and calls on one server must not overlap.  Results equal those
- * of tpa_query with the same settings bit for bit.  A change of a kernel
+ * of tpa_query with the same settings bit for bit when tpa_query moves no
+ * seed (a batch of one chunk, or without seeds of more than 256 out-edges);
+ * otherwise the columns whose chunk changed agree to FP32 rounding (the
+ * server keeps each seed in its chunk, its branches being chosen on the
+ * device).  A change of a kernel
  * setting (tpa_set_variant, tpa_set_batch_width, tpa_set_push, tpa_set_pattern) makes the
  * server capture again, and so does a batch that needs more workspace than
  * any before it (its buffers are reallocated, and graphs captured over the

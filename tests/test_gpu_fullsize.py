@@ -65,8 +65,9 @@ def test_fullsize_query_batch(full):
 
 def test_fullsize_server_growing_batches(full):
     """Batched serving on the full-size graph with batch sizes whose workspace
-    grows (width-1 chunks, then chunks of 8): every batch equals tpa_query bit
-    for bit, and graphs captured over reallocated buffers are never replayed."""
+    grows (width-1 chunks, then chunks of 8): every batch equals tpa_query (bit
+    for bit unless tpa_query regroups heavy seeds), and graphs captured over
+    reallocated buffers are never replayed."""
     tpa, torch = full["tpa"], full["torch"]
     seeds = full["seeds"]
     sizes = [1, 256, 1, 7, 256, 100, 1, 7]
@@ -76,7 +77,12 @@ def test_fullsize_server_growing_batches(full):
         sd = seeds[off:off + k]
         off += k
         got = srv.query(torch.from_numpy(sd).cuda()).clone()
-        assert torch.equal(got, tpa.query(full["g"], sd, S)), k
+        ref = tpa.query(full["g"], sd, S)
+        if k <= 8 or not (full["og"].outdeg[sd] > 256).any():
+            assert torch.equal(got, ref), k
+        else:                                   # tpa_query regrouped heavy seeds: FP32 rounding
+            d = (got.double() - ref.double()).abs()
+            assert float(d.sum(0).max()) <= 1e-5 and float(d.max()) <= 1e-7, k
     st = srv.stats()
     assert st["replays"] + st["captures"] == len(sizes) and st["replays"] >= 2
     j = 3

@@ -292,3 +292,34 @@ def test_pattern_only_products(rmat14):
     finally:
         t.set_pattern(True)
         t.preprocess(rmat14["g"], C, T, EPS)
+
+
+def test_heavy_seeds_grouped(rmat14):
+    """Seeds with more out-edges than the push branch takes are moved to the
+    last chunks of a query, so only those chunks pull x1 and x2: 40 seeds with
+    three heavy ones spread over three chunks take 12 SpMM launches instead of
+    16, and every column lands where its seed was (parity with the oracle)."""
+    t = tpa()
+    og = rmat14["og"]
+    cand = rmat14["cand"]
+    light = cand[og.outdeg[cand] <= 256]
+    heavy = cand[og.outdeg[cand] > 256]
+    assert heavy.size >= 3
+    seeds = synth.query_seeds(light, 40, key=23)
+    for pos, h in zip((2, 17, 30), heavy[:3]):
+        seeds[pos] = h
+    t.profile_reset(True)
+    out = t.query(rmat14["g"], seeds, S).cpu().numpy()
+    spmm = sum(v["launches"] for k2, v in t.profile_read().items() if k2.startswith("spmm"))
+    t.profile_reset(False)
+    assert spmm == 4 * 1 + 2 * 4, spmm
+    for j in (0, 2, 3, 17, 30, 36, 37, 38, 39):
+        ref = oracle.query(og, int(seeds[j]), C, S, T, rmat14["rs"], EPS)
+        parity(out[:, j], ref, f"grouped col {j} seed {seeds[j]}")
+    try:
+        t.set_push(False)                       # no push branch: nothing is regrouped
+        pulled = t.query(rmat14["g"], seeds, S).cpu().numpy()
+    finally:
+        t.set_push(True)
+    d = np.abs(out.astype(np.float64) - pulled)
+    assert d.sum(0).max() <= 1e-5 and d.max() <= 1e-7

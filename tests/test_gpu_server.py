@@ -4,8 +4,9 @@ R-MAT scale 14 (16,384 nodes, edge factor 16, key 1); request batches of
 uneven size drawn uniformly from {1, 7, 32, 100, 256} (key 3) with seeds
 uniform over nodes with an out-edge, the first batch of a size answered
 directly and captured, later ones replayed.  Each batch must equal tpa_query
-on the same seeds bit for bit (same kernels, same order), and sampled columns
-must be within L1 <= 1e-5 and max-abs <= 1e-7 of the oracle.
+on the same seeds bit for bit (same kernels, same order) unless tpa_query
+regroups seeds of more than 256 out-edges, and then to FP32 rounding; sampled
+columns must be within L1 <= 1e-5 and max-abs <= 1e-7 of the oracle.
 """
 import numpy as np
 import pytest
@@ -26,6 +27,18 @@ def tpa():
 def parity(gpu, ref, tag):
     diff = np.abs(np.asarray(gpu, np.float64) - ref)
     assert diff.sum() <= 1e-5 and diff.max() <= 1e-7, f"{tag}: L1 {diff.sum():.3e} max {diff.max():.3e}"
+
+
+def same_as_query(got, ref, seeds, outdeg, tag):
+    """Bit for bit when tpa_query keeps every seed in place (one chunk of the
+    default width, or no seed of more than 256 out-edges); otherwise the
+    regrouped columns agree to FP32 rounding."""
+    import torch
+    if len(seeds) <= 8 or not (outdeg[np.asarray(seeds)] > 256).any():
+        assert torch.equal(got, ref), tag
+    else:
+        d = (got.double() - ref.double()).abs()
+        assert float(d.sum(0).max()) <= 1e-5 and float(d.max()) <= 1e-7, tag
 
 
 @pytest.fixture(scope="module")
@@ -53,7 +66,7 @@ def test_server_uneven_batches(graph14):
         off += k
         got = srv.query(torch.from_numpy(sd).cuda() if b % 2 else sd).clone()
         ref = t.query(graph14["g"], sd, S)
-        assert torch.equal(got, ref), f"batch {b} (k={k}) differs from tpa_query"
+        same_as_query(got, ref, sd, graph14["og"].outdeg, f"batch {b} (k={k}) differs from tpa_query")
         if b < 6:
             for j in sorted({0, k // 2, k - 1}):
                 parity(got[:, j].cpu().numpy(),
@@ -84,7 +97,7 @@ def test_server_workspace_growth_recaptures(graph14):
               (256, dict(graphs=2, replays=2, captures=3))]
     for k, st in expect:
         got = srv.query(sd[:k]).clone()
-        assert torch.equal(got, t.query(graph14["g"], sd[:k], S)), k
+        same_as_query(got, t.query(graph14["g"], sd[:k], S), sd[:k], graph14["og"].outdeg, k)
         now = srv.stats(k)
         assert {key: now[key] for key in st} == st, (k, now)
     parity(got[:, 255].cpu().numpy(), oracle.query(graph14["og"], int(sd[255]), C, S, T, graph14["rs"], EPS), "k 256")
@@ -103,7 +116,7 @@ def test_server_recaptures_after_setting_change(graph14):
         t.set_batch_width(4)
         b = srv.query(seeds).clone()
         assert srv.stats()["graphs"] == 1            # the old graph was dropped, one new capture
-        assert torch.equal(b, t.query(graph14["g"], seeds, S))
+        same_as_query(b, t.query(graph14["g"], seeds, S), seeds, graph14["og"].outdeg, "width 4")
         for j in (0, 31):
             parity(b[:, j].cpu().numpy(),
                    oracle.query(graph14["og"], int(seeds[j]), C, S, T, graph14["rs"], EPS), f"width 4 col {j}")
