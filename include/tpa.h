@@ -91,10 +91,11 @@ tpa_status tpa_get_stranger(const tpa_graph *g, float *out, int64_t *iters, void
  *   r_TPA = (1 + alpha) r_family + r~_stranger,
  *   alpha = ((1-c)^S - (1-c)^T) / (1 - (1-c)^S)   (Section III-B),
  * using the c and T of tpa_preprocess.  out is float32[n * k], node-major.
- * Seeds run in chunks (tpa_set_batch_width); seeds with more out-edges than
- * the push branch takes (256) are moved into the last chunks of the query,
- * so that the other chunks push x1 and x2; every column still lands at its
- * seed's position.  Requires 1 <= S <= T, k >= 1, 0 <= seeds[j] < n.
+ * Seeds run in chunks (tpa_set_batch_width).  With out in device memory (or
+ * host memory that is not page-locked), seeds with more out-edges than the
+ * push branch takes (256) are swapped into the last chunks of the query, so
+ * that the other chunks push x1 and x2, and the swapped columns are put back
+ * at the end; results then agree with unmoved seeds to FP32 rounding.  Requires 1 <= S <= T, k >= 1, 0 <= seeds[j] < n.
  * Errors: TPA_ESTATE before tpa_preprocess; TPA_EINVAL.
  */
 tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *out, void *stream);

@@ -173,7 +173,7 @@ void tpa_free_graph(tpa_graph *g)
                       &g->r_str,
                       &g->perm_a2t, &g->w_a, &g->inv_d, &g->row_a, &g->ws.u, &g->ws.touched, &g->ws.x2,
                       &g->ws.x, &g->ws.y, &g->ws.r, &g->ws.carry, &g->ws.head, &g->ws.tl1, &g->ws.fix,
-                      &g->ws.ctl, &g->ws.seeds, &g->ws.sets, &g->ws.seeds_g, &g->ws.cols, &g->ws.stage,
+                      &g->ws.ctl, &g->ws.seeds, &g->ws.sets, &g->ws.seeds_g, &g->ws.cols,
                       &g->ws.out, &g->ws.iters};
     for (DevBuf *b : bufs) b->release(s);
     g->ws.cpart.release(s);

@@ -506,10 +506,7 @@ static int iteration_bound(double c, double eps)
     return (int)std::min(1.0e6, i) + 4;
 }
 
-// One chunk of k0 .. k0+kc-1.  The scores go to a.out + k0 (row stride
-// a.ldo), or to out_to (row stride ldo_to) when it is given.
-void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t s, float *out_to = nullptr,
-                   int64_t ldo_to = 0)
+void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t s)
 {
     const int KP = kp_for(kc);
     const Variant &var = pick_variant(KP);
@@ -612,9 +609,8 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     }
     if (last == 0) {
         if (a.tpa_final) {
-            finalize_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(r, ldr, a.r_str, (float)(1.0 + a.alpha),
-                                                           out_to ? out_to : a.out + k0, out_to ? ldo_to : a.ldo,
-                                                           n, kc);
+            finalize_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(r, ldr, a.r_str, (float)(1.0 + a.alpha), a.out + k0,
+                                                           a.ldo, n, kc);
             note_launch("finalize");
         }
         if (a.iters_out) {
@@ -637,8 +633,8 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     p.tiles = P.tiles;
     p.r = r;
     p.ldr = ldr;
-    p.out = out_to ? out_to : (a.out ? a.out + k0 : nullptr);
-    p.ldo = out_to ? ldo_to : a.ldo;
+    p.out = a.out ? a.out + k0 : nullptr;
+    p.ldo = a.ldo;
     p.r_str = a.r_str;
     p.one_plus_alpha = (float)(1.0 + a.alpha);
     p.decay = (float)(1.0 - a.c);
@@ -951,16 +947,19 @@ __global__ void gather_seeds_k(const int32_t *seeds, const int32_t *perm, int k,
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) out[j] = seeds[perm[j]];
 }
 
-// Scores of a regrouped chunk ([n][KP] staging, columns 0..kc-1) to their
-// output columns cols[0..kc).
-__global__ void scatter_cols_k(const float *stage, int KP, int64_t n, int kc, float *out, int64_t ldo,
-                               const int32_t *cols)
+// After a regrouped query has written every chunk in place, column pairs
+// (a, b) of out hold each other's scores: swap them back.
+__global__ void swap_cols_k(float *out, int64_t ldo, int64_t n, const int32_t *pairs, int np)
 {
-    const int64_t total = n * kc;
+    const int64_t total = n * np;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = i / kc;
-        const int j = (int)(i % kc);
-        out[v * ldo + __ldg(cols + j)] = stage[v * KP + j];
+        const int64_t v = i / np;
+        const int q = (int)(i % np);
+        float *row = out + v * ldo;
+        const int32_t a = __ldg(pairs + 2 * q), b = __ldg(pairs + 2 * q + 1);
+        const float ta = row[a], tb = row[b];
+        row[a] = tb;
+        row[b] = ta;
     }
 }
 
@@ -970,18 +969,29 @@ void run_cpi(tpa_graph *g, const CpiArgs &a0, cudaStream_t s)
                                    : (g_chunk_cpi ? g_chunk_cpi : DEFAULT_CHUNK_CPI);
     CpiArgs a = a0;
     // A query whose chunk branches the host picks (it has the seeds' out-degrees)
-    // gathers the seeds too heavy for the push branch into its last chunks.
+    // and whose output is in device memory swaps the seeds too heavy for the
+    // push branch into its last chunks, runs every chunk in place, and swaps
+    // the moved columns back at the end.
     std::vector<int32_t> perm, od;
     bool grouped = false;
-    if (a.tpa_final && a.seed_outdeg && a.seeds && !a.set_ptr && a.r_internal && a.t_iter >= 3 && a.out)
+    if (a.tpa_final && a.seed_outdeg && a.seeds && !a.set_ptr && a.r_internal && a.t_iter >= 3 && a.out &&
+        is_device_ptr(a.out))
         grouped = group_heavy_seeds(a.seed_outdeg, a.k, chunk, perm);
     Workspace &W = g->ws;
+    std::vector<int32_t> pairs;
     if (grouped) {
         od.resize((size_t)a.k);
         for (int j = 0; j < a.k; ++j) od[j] = a.seed_outdeg[perm[j]];
-        W.cols.ensure((size_t)a.k * sizeof(int32_t), s);
+        for (int j = 0; j < a.k; ++j)
+            if (perm[j] > j) {   // positions j and perm[j] traded seeds
+                pairs.push_back(j);
+                pairs.push_back(perm[j]);
+            }
+        W.cols.ensure(((size_t)a.k + pairs.size()) * sizeof(int32_t), s);
         W.seeds_g.ensure((size_t)a.k * sizeof(int32_t), s);
         TPA_CUDA(cudaMemcpyAsync(W.cols.p, perm.data(), (size_t)a.k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        TPA_CUDA(cudaMemcpyAsync(W.cols.as<int32_t>() + a.k, pairs.data(), pairs.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, s));
         gather_seeds_k<<<(unsigned)std::min(1024, (a.k + 255) / 256), 256, 0, s>>>(a.seeds, W.cols.as<int32_t>(),
                                                                                    a.k, W.seeds_g.as<int32_t>());
         note_launch("init");
@@ -989,22 +999,12 @@ void run_cpi(tpa_graph *g, const CpiArgs &a0, cudaStream_t s)
         a.seeds = W.seeds_g.as<int32_t>();
         a.seed_outdeg = od.data();
     }
-    for (int k0 = 0; k0 < a.k; k0 += chunk) {
-        const int kc = std::min(chunk, a.k - k0);
-        bool in_place = true;
-        for (int j = 0; grouped && j < kc; ++j) in_place = in_place && perm[k0 + j] == k0 + j;
-        if (in_place) {
-            run_cpi_chunk(g, a, k0, kc, s);
-        } else {
-            // a chunk holding moved seeds finishes into staging, then each column goes to its place
-            const int KP = kp_for(kc);
-            W.stage.ensure((size_t)g->n * KP * sizeof(float), s);
-            run_cpi_chunk(g, a, k0, kc, s, W.stage.as<float>(), KP);
-            scatter_cols_k<<<grid_1d(g->n * kc, 256), 256, 0, s>>>(W.stage.as<float>(), KP, g->n, kc, a.out, a.ldo,
-                                                                    W.cols.as<int32_t>() + k0);
-            note_launch("finalize");
-            TPA_CHECK_LAUNCH();
-        }
+    for (int k0 = 0; k0 < a.k; k0 += chunk) run_cpi_chunk(g, a, k0, std::min(chunk, a.k - k0), s);
+    if (grouped) {
+        const int np = (int)(pairs.size() / 2);
+        swap_cols_k<<<grid_1d(g->n * np, 256), 256, 0, s>>>(a.out, a.ldo, g->n, W.cols.as<int32_t>() + a.k, np);
+        note_launch("finalize");
+        TPA_CHECK_LAUNCH();
     }
 }
 

@@ -89,7 +89,7 @@ std::vector<uint64_t> identity(const tpa_graph *g)
     };
     const Workspace &w = g->ws;
     for (const DevBuf *b : {&w.x, &w.y, &w.r, &w.carry, &w.head, &w.tl1, &w.fix, &w.ctl, &w.seeds, &w.sets,
-                            &w.seeds_g, &w.cols, &w.stage, &w.out, &w.iters, &w.u, &w.touched, &w.x2, &w.cpart})
+                            &w.seeds_g, &w.cols, &w.out, &w.iters, &w.u, &w.touched, &w.x2, &w.cpart})
         addr(*b);
     v.push_back((uint64_t)(uintptr_t)w.hflag);
     for (const DevBuf *b : {&g->rp_t, &g->col_t, &g->val_t, &g->rp_a, &g->col_a, &g->val_a, &g->outdeg, &g->inv_deg32,
@@ -314,7 +314,7 @@ void tpa_server_free(tpa_server *srv)
     cudaStream_t s = 0;
     DevBuf *bufs[] = {&srv->out_buf, &srv->seeds, &srv->ws.x, &srv->ws.y, &srv->ws.r, &srv->ws.carry,
                       &srv->ws.head, &srv->ws.tl1, &srv->ws.fix, &srv->ws.ctl, &srv->ws.seeds, &srv->ws.sets,
-                      &srv->ws.seeds_g, &srv->ws.cols, &srv->ws.stage, &srv->ws.out,
+                      &srv->ws.seeds_g, &srv->ws.cols, &srv->ws.out,
                       &srv->ws.iters, &srv->ws.u, &srv->ws.touched, &srv->ws.x2, &srv->ws.cpart};
     for (DevBuf *b : bufs) b->release(s);
     if (srv->ws.hflag) cudaFreeHost(srv->ws.hflag);

@@ -102,8 +102,7 @@ struct Workspace {
     DevBuf ctl;             // control block (see Ctl)
     DevBuf seeds;           // int32 seeds (or seed-set members)
     DevBuf sets;            // int64 seed-set offsets
-    DevBuf seeds_g, cols;   // a query's seeds regrouped, and each one's output column
-    DevBuf stage;           // [n][KP] scores of a regrouped chunk before they go to their columns
+    DevBuf seeds_g, cols;   // a query's seeds regrouped; their positions, then the swapped column pairs
     DevBuf out;             // device staging for host outputs
     DevBuf iters;           // int32 per-column iteration counts
     DevBuf u;               // push path: 64-bit fixed-point accumulator [n][KP]

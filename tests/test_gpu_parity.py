@@ -163,14 +163,21 @@ def test_host_buffers_through_c_abi(rmat14):
 
 @pytest.mark.parametrize("k", [13, 150])
 def test_pinned_host_output(rmat14, k):
-    """Page-locked host output: the kernels write the scores straight into it."""
+    """Page-locked host output: the kernels write the scores straight into it
+    (every seed in its chunk)."""
     import torch
     t = tpa()
     seeds = synth.query_seeds(rmat14["cand"], k, key=14)
     out = torch.full((rmat14["n"], k), -1.0, dtype=torch.float32).pin_memory()
     t.query(rmat14["g"], seeds, S, out=out)
     dev = t.query(rmat14["g"], seeds, S).cpu()
-    assert torch.equal(out, dev)
+    if k <= 8 or not (rmat14["og"].outdeg[seeds] > 256).any():
+        assert torch.equal(out, dev)
+    else:   # into device memory tpa_query regroups seeds too heavy to push: FP32 rounding
+        d = (out.double() - dev.double()).abs()
+        assert float(d.sum(0).max()) <= 1e-5 and float(d.max()) <= 1e-7
+    for j in (0, k // 2, k - 1):
+        parity(out[:, j].numpy(), oracle.query(rmat14["og"], int(seeds[j]), C, S, T, rmat14["rs"], EPS), f"col {j}")
 
 
 def test_deterministic(rmat14):
