@@ -20,7 +20,7 @@
  *     r_TPA = r_family + alpha r_family + r~_stranger,
  *     alpha = ((1-c)^S - (1-c)^T) / (1 - (1-c)^S).
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - Graph: self-loops are dropped and duplicate edges are kept once.
  *     Nodes without out-edges (deadends) keep an all-zero row of A~, so mass
  *     leaks there.
