@@ -33,7 +33,10 @@ if ROOT not in sys.path:
 
 METRIC = "TPA seeds/s and SpMV HBM GB/s vs peak, batched vs per-seed CPI at L1≤1e-5"
 C, S, T, EPS = 0.15, 5, 10, 1e-9
-WORKLOAD = "TPA preprocessing + 1000 single-seed queries on R-MAT scale 22 (ef 16), c=0.15 S=5 T=10 eps=1e-9"
+def workload(args) -> str:
+    """The configuration a line measures, by what it is and its sizes."""
+    return (f"TPA preprocessing + {args.queries} single-seed queries on R-MAT scale {args.scale} "
+            f"(ef {args.edge_factor}), c={C} S={S} T={T} eps={EPS:.0e}".replace("e-0", "e-"))
 
 
 def parse_args(argv=None):
@@ -259,7 +262,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n": n, "m": og.m, "queries": args.queries},
+            "data": "synthetic", "config": {"workload": workload(args), "n": n, "m": og.m, "queries": args.queries},
             "cpu_baseline": {"value": value, "unit": "seeds/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "seeds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -451,11 +454,12 @@ def main(argv=None):
         line = {"metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "graph": f"R-MAT scale {args.scale} ef {args.edge_factor}",
+                "config": {"workload": workload(args), "graph": f"R-MAT scale {args.scale} ef {args.edge_factor}",
                            "n": n, "m": m, "m_raw": int(src.size), "queries_per_rank": Q, "query_batch": batch,
                            "c": C, "S": S, "T": T, "eps": EPS, "parallelism": f"replicas x{world} (seed-sharded)",
                            "products": "valued" if args.valued_products else "pattern-only",
-                           "l2": "inputs larger than L2 (CSR 0.5 GB, scores 16.8 GB per step)"},
+                           "l2": f"inputs larger than L2 (CSR {8 * m / 1e9:.1f} GB with values, "
+                                 f"scores {4 * n * Q / 1e9:.1f} GB per step)"},
                 "roofline": roof, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk,
                 "phases_ms": phases, "preprocess_iters": pre_iters,
