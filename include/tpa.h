@@ -252,6 +252,16 @@ tpa_status tpa_set_push(int enable);
  * enable = 0 reads the value array everywhere. */
 tpa_status tpa_set_pattern(int enable);
 
+/* The order in which tpa_query runs the k seeds of one call (with its output
+ * in device memory), from their out-degrees outdeg[0..k) (host int32) and the
+ * settings in effect: perm[j] (host int32[k]) is the position of the seed
+ * run at place j.  Seeds with more than 256 out-edges are swapped into the
+ * last places, each with a light seed from there, when some chunk can push
+ * (push on, S >= 4, chunks of at most 16, more than one chunk); otherwise
+ * perm is the identity.  Host only: no GPU work.  TPA_EINVAL for NULL
+ * arguments or k < 1. */
+tpa_status tpa_seed_order(const int32_t *outdeg, int k, int S, int32_t *perm);
+
 /* ---------------------------------------------------- batched serving ---
  * Algorithm 3 for a stream of request batches of uneven size, with the launch
  * sequence of each batch size captured once in a CUDA graph and replayed.

@@ -39,6 +39,7 @@ from .tpa import (  # noqa: F401
     get_cpi_batch_width,
     set_push,
     set_pattern,
+    seed_order,
     get_batch_width,
     set_variant,
     get_variant,

@@ -35,6 +35,7 @@
 #include <atomic>
 #include <cstddef>
 #include <cmath>
+#include <numeric>
 #include <vector>
 
 #include "tpa_internal.cuh"
@@ -1097,6 +1098,20 @@ tpa_status tpa_set_push(int enable)
 {
     g_push = enable != 0;
     ++g_epoch;
+    return TPA_OK;
+}
+
+tpa_status tpa_seed_order(const int32_t *outdeg, int k, int S, int32_t *perm)
+{
+    if (!outdeg || !perm || k < 1) {
+        set_error("tpa_seed_order: NULL argument or k < 1");
+        return TPA_EINVAL;
+    }
+    std::vector<int32_t> p((size_t)k);
+    std::iota(p.begin(), p.end(), 0);
+    const int chunk = g_chunk_query ? g_chunk_query : DEFAULT_CHUNK_QUERY;
+    if (S - 1 >= 3) group_heavy_seeds(outdeg, k, chunk, p);   // the push branch exists from S = 4
+    std::copy(p.begin(), p.end(), perm);
     return TPA_OK;
 }
 

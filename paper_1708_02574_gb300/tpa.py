@@ -72,6 +72,7 @@ def library():
         "tpa_get_cpi_batch_width": (i32, []),
         "tpa_set_push": (i32, [i32]),
         "tpa_set_pattern": (i32, [i32]),
+        "tpa_seed_order": (i32, [P, i32, i32, P]),
         "tpa_profile_reset": (i32, [i32]),
         "tpa_profile_read": (i32, [P, i32, ctypes.POINTER(i32)]),
     }
@@ -362,6 +363,14 @@ def cpi_step_noalloc(n: int, m: int, row_ptr, col, val, c: float, x, y, r=None, 
 def set_push(enable: bool) -> None:
     """Push the sparse first family iterates of a query (default) or pull every iteration."""
     _check(library().tpa_set_push(1 if enable else 0))
+
+
+def seed_order(outdeg, S: int = 5) -> np.ndarray:
+    """tpa_seed_order: the order tpa_query runs seeds with these out-degrees in (host only)."""
+    od = np.ascontiguousarray(outdeg, dtype=np.int32)
+    perm = np.empty(od.size, dtype=np.int32)
+    _check(library().tpa_seed_order(_ptr(od), int(od.size), int(S), _ptr(perm)))
+    return perm
 
 
 def set_pattern(enable: bool) -> None:
