@@ -56,6 +56,9 @@ def parse_args(argv=None):
     ap.add_argument("--accuracy", type=int, default=0, metavar="SEEDS",
                     help="run the accuracy study of TPA's approximations (S sweep at T=10, T sweep at S=5, "
                          "recall@100/500) for SEEDS seeds on the GPU path, print one JSON line and exit")
+    ap.add_argument("--graph", default="rmat", metavar="rmat|planted:BLOCKS:P_IN",
+                    help="graph of the accuracy study: R-MAT (default) or a planted-partition graph with "
+                         "BLOCKS equal communities and a share P_IN of edges inside them")
     ap.add_argument("--valued-products", action="store_true",
                     help="products that read the value array instead of the default pattern-only products")
     ap.add_argument("--profile-case", choices=["preprocess", "query8"], default=None,
@@ -74,14 +77,20 @@ def accuracy_study(args):
     from paper_1708_02574_gb300 import accuracy
     tpa.set_pattern(not args.valued_products)
     n = 1 << args.scale
-    src, dst = synth.rmat_edges(args.scale, args.edge_factor)
+    if args.graph == "rmat":
+        src, dst = synth.rmat_edges(args.scale, args.edge_factor)
+        name = f"R-MAT scale {args.scale} ef {args.edge_factor}"
+    else:
+        kind, blocks, p_in = args.graph.split(":")
+        assert kind == "planted", args.graph
+        src, dst = synth.planted_edges(n, args.edge_factor, int(blocks), float(p_in))
+        name = f"planted partition 2^{args.scale} nodes ef {args.edge_factor}, {blocks} blocks, p_in {p_in}"
     g = tpa.build_graph(n, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda())
     cand = synth.nodes_with_out_edge(n, src, dst)
     seeds = torch.from_numpy(synth.query_seeds(cand, args.accuracy)).cuda()
     t0 = time.perf_counter()
     res = accuracy.sweep(g, seeds, C, EPS, S_fixed=S, T_fixed=T, ks=(100, 500))
-    print(json.dumps({"study": "tpa_accuracy", "data": "synthetic",
-                      "graph": f"R-MAT scale {args.scale} ef {args.edge_factor}", "n": n, "m": g.m,
+    print(json.dumps({"study": "tpa_accuracy", "data": "synthetic", "graph": name, "n": n, "m": g.m,
                       "c": C, "eps": EPS, "seeds": args.accuracy, "seconds": time.perf_counter() - t0, **res}))
     return 0
 

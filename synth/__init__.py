@@ -15,6 +15,8 @@ Recipes (the workloads stand in for the KONECT graphs of the paper's Table 2):
 * ``edge_features``: N(0, 1) float32 per edge and feature (stream key 4).
 * ``theta``: N(0, 0.1^2) float32 (stream key 5).
 * ``triples``: (seed, positive out-neighbour, uniform negative) (stream key 6).
+* ``planted_edges(n, edge_factor, blocks, p_in)``: a planted-partition graph with
+  communities, for the accuracy study (stream key 7).
 """
 from __future__ import annotations
 
@@ -54,6 +56,8 @@ def _load():
         lib.synth_rmat.restype = ctypes.c_int
         lib.synth_rmat.argtypes = [ctypes.c_int, i64, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, u64, i32p, i32p, ctypes.c_int]
+        lib.synth_planted.restype = ctypes.c_int
+        lib.synth_planted.argtypes = [i64, i64, i64, ctypes.c_double, u64, i32p, i32p]
         lib.synth_has_out_edge.restype = None
         lib.synth_has_out_edge.argtypes = [i64, i64, i32p, i32p, i32p]
         lib.synth_pick_uniform.restype = None
@@ -88,6 +92,17 @@ def rmat_edges(scale: int, edge_factor: int = 16, a: float = A, b: float = B, c:
     rc = _load().synth_rmat(int(scale), m, a, b, c, key, _ptr(src), _ptr(dst), nt)
     if rc != 0:
         raise ValueError("synth_rmat rejected its arguments")
+    return src, dst
+
+
+def planted_edges(n: int, edge_factor: int, blocks: int, p_in: float, key: int = 7):
+    """Planted-partition graph (communities): ``edge_factor * n`` edges, uniform sources,
+    destinations inside the source's block with probability ``p_in``, else uniform."""
+    m = int(edge_factor) * int(n)
+    src = np.empty(m, dtype=np.int32)
+    dst = np.empty(m, dtype=np.int32)
+    if _load().synth_planted(n, m, blocks, p_in, key, _ptr(src), _ptr(dst)) != 0:
+        raise ValueError("synth_planted rejected its arguments")
     return src, dst
 
 

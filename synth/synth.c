@@ -103,6 +103,37 @@ int synth_rmat(int scale, int64_t m, double a, double b, double c, uint64_t key,
     return 0;
 }
 
+/* Planted-partition graph: n nodes in `blocks` equal contiguous blocks
+ * (block of v = v * blocks / n), m directed edges.  Edge e draws its source
+ * uniformly over all nodes and, with probability p_in, its destination
+ * uniformly inside the source's block, else uniformly over all nodes.
+ * Counter-based: edge e uses counters 3e, 3e+1, 3e+2 of `key`.
+ * Returns -1 on bad arguments. */
+int synth_planted(int64_t n, int64_t m, int64_t blocks, double p_in, uint64_t key, int32_t *src, int32_t *dst)
+{
+    if (n < 1 || n > ((int64_t)1 << 31) - 1 || m < 0 || blocks < 1 || blocks > n || !(p_in >= 0.0 && p_in <= 1.0) ||
+        !src || !dst)
+        return -1;
+    for (int64_t e = 0; e < m; ++e) {
+        const uint64_t c = 3 * (uint64_t)e;
+        int64_t s = (int64_t)(u01(key, c) * (double)n);
+        if (s >= n) s = n - 1;
+        int64_t d;
+        if (u01(key, c + 1) < p_in) {
+            const int64_t b = s * blocks / n;
+            const int64_t lo = (b * n + blocks - 1) / blocks, hi = ((b + 1) * n + blocks - 1) / blocks;
+            d = lo + (int64_t)(u01(key, c + 2) * (double)(hi - lo));
+            if (d >= hi) d = hi - 1;
+        } else {
+            d = (int64_t)(u01(key, c + 2) * (double)n);
+            if (d >= n) d = n - 1;
+        }
+        src[e] = (int32_t)s;
+        dst[e] = (int32_t)d;
+    }
+    return 0;
+}
+
 /* Mark nodes with at least one out-edge to another node (not a self-loop).
  * flag must hold n bytes; it is overwritten. */
 void synth_has_out_edge(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, uint8_t *flag)

@@ -58,3 +58,19 @@ def test_seed_picks_and_sizes():
     edges = set(zip(s.tolist(), d.tolist()))
     assert all((a, b) in edges and a != b for a, b in zip(sd.tolist(), p.tolist()))
     assert ng.min() >= 0 and ng.max() < n
+
+
+def test_planted_partition_edges():
+    """Planted-partition graph: ids in range, the share of edges inside the
+    source's block close to p_in plus the uniform draws that land there, and
+    the same edges for the same key."""
+    n, blocks, p_in = 1 << 12, 64, 0.8
+    s, d = synth.planted_edges(n, 16, blocks, p_in)
+    assert s.size == d.size == 16 * n
+    assert s.min() >= 0 and s.max() < n and d.min() >= 0 and d.max() < n
+    inside = (s * blocks // n == d * blocks // n).mean()
+    assert abs(inside - (p_in + (1 - p_in) / blocks)) < 0.01
+    s2, d2 = synth.planted_edges(n, 16, blocks, p_in)
+    assert np.array_equal(s, s2) and np.array_equal(d, d2)
+    s3, _ = synth.planted_edges(n, 16, blocks, p_in, key=8)
+    assert not np.array_equal(s, s3)
