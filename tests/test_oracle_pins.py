@@ -171,8 +171,14 @@ def pin_lemma2_mass():
 
 
 def pin_bounds():
-    """Lemma 1, Lemma 3 and Theorem 2 on graphs with and without deadends."""
-    for kind, n, s, d in graphs():
+    """Lemma 1, Lemma 3 and Theorem 2 on graphs with and without deadends, and on
+    planted-partition graphs (communities)."""
+    planted = []
+    for blocks, p_in in ((4, 0.9), (12, 0.6)):
+        n = 96
+        s, d = synth.planted_edges(n, 3, blocks, p_in, key=60 + blocks)
+        planted.append((f"planted{blocks}", n, s, d))
+    for kind, n, s, d in graphs() + planted:
         g = oracle.build_graph(n, s, d)
         for S, T in ((5, 10), (2, 4), (4, 6), (3, 3)):
             rs, _ = oracle.preprocess(g, C, T, eps=1e-13)
