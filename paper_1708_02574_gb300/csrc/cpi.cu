@@ -1,33 +1,28 @@
-// Cumulative power iteration (Algorithm 1) on the GPU.
+// Cumulative power iteration (Algorithm 1) on the GPU: the host side that
+// plans and launches it.  The kernels are in spmm_kernels.cuh (merge path)
+// and spmm_binned.cuh (rows binned by length).
 //
-// One iteration computes x_i = (1-c) A~^T x_{i-1} for k independent columns
-// (node-major X[n][KP], KP = padded k) with a merge-path SpMM over CSR(A~^T)
-// (Merrill and Garland's merge-based decomposition: the path interleaves the
-// n row-end markers with the m nonzeros, and every CTA takes an equal slice
-// of it, so hub rows with huge in-degree cost no load imbalance).
+// One iteration computes x_i = (1-c) A~^T x_{i-1} for a chunk of k columns
+// (node-major X[n][KP], KP = k padded to a power of two) with a merge-path
+// SpMM over CSR(A~^T): the path interleaves the n row ends with the m
+// nonzeros and is cut into equal tiles, so rows of hubs cost no imbalance.
+// Several kernel variants exist per KP (warp walker, pipelined group walker,
+// CTA walker, binned rows); the first of each width in kVariants is the
+// default, and the autotuner or tpa_set_variant may pick another.  Each
+// SpMM launch fuses the epilogue of Algorithm 1 (y stored, r += y for
+// running columns, FP32 L1 partials of y) or, on the last family iteration
+// of Algorithm 3, the finalize out = (1+alpha)(r + y) + r~_stranger.  A
+// fixup kernel then finishes the rows split across tiles, adds the L1
+// partials in a fixed order (FP64 across blocks) and applies the break test
+// ||x_i||_1 < eps per column.  Tile orders are static, so results are
+// deterministic run to run.
 //
-// spmm_tile_k, tiles of L = NVT * ITEMS path steps, taken round-robin by
-// persistent CTAs:
-//   1. stage the tile's row ends and (col, val) into shared memory with
-//      evict-first loads, so the CSR stream does not push the iterates out
-//      of L2;
-//   2. each virtual thread (G lanes, V columns per lane) finds its own
-//      diagonal by a merge-path search in shared memory, issues the
-//      gathers x[col] for a chunk of steps, then walks the chunk, emitting
-//      finished rows;
-//   3. a segmented scan over the virtual threads' carries finishes rows
-//      that straddle virtual threads; the row straddling the tile's start
-//      is deferred to the fixup kernel, and the tile's last partial row is
-//      written out as the tile carry;
-//   4. the epilogue of Algorithm 1 is fused: y = (1-c) sum, r += y for
-//      columns still running when i >= s_iter, per-column L1 of y in FP64;
-//      or, on the last family iteration of Algorithm 3, the finalize
-//      out = (1+alpha)(r + y) + r~_stranger.
-// fixup_k, warps over tiles: adds the carries of earlier tiles to each
-// deferred row in a fixed order, applies the epilogue, reduces the per-tile
-// L1 partials in a fixed order, and the last block applies the break test
-// ||x_i||_1 < eps per column.  Both kernels run persistent grids with a static
-// tile order, so results are deterministic run to run.
+// Around the SpMM: query chunks of light seeds push x1 and x2 along CSR(A~)
+// instead of pulling them (the host or, in captured launch sequences, the
+// device picks the branch); unweighted graphs use pattern-only products
+// (the iterate is kept scaled by 1/outdeg and the value array is not read);
+// and a query whose scores go to device memory moves its seeds too heavy to
+// push into its last chunks, swapping their columns back at the end.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
