@@ -22,6 +22,27 @@ from . import tpa
 TIE = 0.03   # relative margin within which a default wins
 
 
+def pick_fastest(times: dict, default, tie: float = TIE):
+    """Key of the smallest time in `times`, except that `default` (when timed)
+    wins if it is within a factor (1 + tie) of that smallest time."""
+    best = min(times, key=lambda k: times[k])
+    if default in times and times[default] <= times[best] * (1.0 + tie):
+        return default
+    return best
+
+
+def pick_query(results: list, defaults: dict, default_width: int, tie: float = TIE) -> dict:
+    """The query setting with the highest throughput in `results` (dicts with
+    width, variant, seeds_per_s), except that within a factor (1 + tie) of it
+    the default variant of the best width wins, then the default width's
+    default variant."""
+    best = max(results, key=lambda r: r["seeds_per_s"])
+    for cand in ([r for r in results if r["width"] == best["width"] and r["variant"] == defaults[best["width"]]] +
+                 [r for r in results if r["width"] == default_width and r["variant"] == defaults[default_width]]):
+        if cand["seeds_per_s"] >= best["seeds_per_s"] / (1.0 + tie):
+            return cand
+    return best
+
 
 def _time(fn, reps: int) -> float:
     import torch
@@ -47,12 +68,10 @@ def tune_preprocess(g: tpa.Graph, c: float, T: int, eps: float, reps: int = 1) -
             continue
         tpa.set_variant(1, v["index"])
         times[v["index"]] = _time(lambda: tpa.preprocess(g, c, T, eps), reps)
-    best = min(times.items(), key=lambda kv: kv[1])
-    if times[default] <= best[1] * (1.0 + TIE):
-        best = (default, times[default])
-    tpa.set_variant(1, best[0])
+    best = pick_fastest(times, default)
+    tpa.set_variant(1, best)
     tpa.preprocess(g, c, T, eps)
-    return {"variant": best[0], "seconds": best[1]}
+    return {"variant": best, "seconds": times[best]}
 
 
 def tune_query(g: tpa.Graph, seeds, S: int, widths=(1, 2, 4, 8, 16, 32, 64, 128, 256), reps: int = 2,
@@ -79,14 +98,7 @@ def tune_query(g: tpa.Graph, seeds, S: int, widths=(1, 2, 4, 8, 16, 32, 64, 128,
             t = _time(lambda: tpa.query(g, sd, S, out=out), reps)
             results.append({"width": w, "variant": v["index"], "seeds_per_s": q / t})
         tpa.set_variant(w, -1)
-    best = max(results, key=lambda r: r["seeds_per_s"])
-    # prefer the default variant of the best width, then the default width's
-    # default variant, when within TIE of the fastest
-    for cand in ([r for r in results if r["width"] == best["width"] and r["variant"] == defaults[best["width"]]] +
-                 [r for r in results if r["width"] == default_width and r["variant"] == defaults[default_width]]):
-        if cand["seeds_per_s"] >= best["seeds_per_s"] / (1.0 + TIE):
-            best = cand
-            break
+    best = pick_query(results, defaults, default_width)
     tpa.set_batch_width(best["width"])
     tpa.set_variant(best["width"], best["variant"])
     return {"best": best, "all": results}
