@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -27,12 +28,68 @@ void set_error(const char *fmt, ...)
 
 void clear_error() { g_err[0] = '\0'; }
 
+// The library's stream-ordered memory pool on the current device.  Its release
+// threshold is unlimited, so a freed block stays mapped (and is reused by the
+// next allocation) until trim_pool() hands unused memory back to the driver;
+// that happens only after a device-wide synchronisation (end of graph build,
+// tpa_free_graph, tpa_server_free).  The default pool would unmap freed
+// blocks at every synchronisation of any stream.
+static cudaMemPool_t lib_pool()
+{
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDevices];
+    int dev = 0;
+    TPA_CUDA(cudaGetDevice(&dev));
+    TPA_REQUIRE(dev >= 0 && dev < kMaxDevices, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        TPA_CUDA(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = UINT64_MAX;
+        TPA_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
+void trim_pool() noexcept
+{
+    try {
+        cudaMemPoolTrimTo(lib_pool(), 0);
+    } catch (...) {
+        cudaGetLastError();
+    }
+}
+
+// Growth of a buffer that exists frees the old block, which a captured graph,
+// another stream or an earlier call may still be reading: wait for the whole
+// device first (growth happens a few times per workspace, not per call).  No
+// allocation may happen while a stream is being captured: the address would
+// belong to the graph, not to the library.
 void DevBuf::ensure(size_t b, cudaStream_t s)
 {
     if (b <= bytes && p) return;
-    release(s);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusNone;
+    }
+    if (cs != cudaStreamCaptureStatusNone) {
+        set_error("a %zu-byte device buffer would be allocated while the stream is captured", b);
+        throw Fail{TPA_ECUDA};
+    }
+    if (p) {
+        TPA_CUDA(cudaDeviceSynchronize());
+        release(s);
+    }
     void *q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, b ? b : 16, s);
+    cudaError_t e = cudaMallocFromPoolAsync(&q, b ? b : 16, lib_pool(), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("device allocation of %zu bytes failed: %s", b, cudaGetErrorString(e));
@@ -47,6 +104,14 @@ void DevBuf::release(cudaStream_t s)
     if (p) cudaFreeAsync(p, s);
     p = nullptr;
     bytes = 0;
+}
+
+void need(const DevBuf &b, size_t bytes, const char *what)
+{
+    if (!b.p || b.bytes < bytes) {
+        set_error("internal: %s holds %zu bytes, a launch indexes %zu", what, b.p ? b.bytes : (size_t)0, bytes);
+        throw Fail{TPA_ECUDA};
+    }
 }
 
 bool is_device_ptr(const void *p)
@@ -156,6 +221,9 @@ tpa_status tpa_build_graph(int64_t n, int64_t m_edges, const int32_t *src, const
         build_csr(g, ps, pd, m_edges, s);
         dsrc.release(s);
         ddst.release(s);
+        // the sort buffers of the build go back to the driver
+        TPA_CUDA(cudaStreamSynchronize(s));
+        trim_pool();
     } catch (...) {
         tpa_free_graph(g);
         throw;
@@ -190,6 +258,7 @@ void tpa_free_graph(tpa_graph *g)
         }
     if (g->ws.hflag) cudaFreeHost(g->ws.hflag);
     cudaStreamSynchronize(s);
+    trim_pool();
     delete g;
 }
 

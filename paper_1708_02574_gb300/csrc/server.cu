@@ -322,6 +322,7 @@ void tpa_server_free(tpa_server *srv)
     if (srv->staged) cudaEventDestroy(srv->staged);
     if (srv->cap) cudaStreamDestroy(srv->cap);
     cudaDeviceSynchronize();
+    trim_pool();
     delete srv;
 }
 

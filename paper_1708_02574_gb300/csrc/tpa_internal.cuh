@@ -63,6 +63,14 @@ struct DevBuf {
 
 bool is_device_ptr(const void *p);
 
+// Check before a launch that a buffer holds the bytes the launch indexes
+// (TPA_ECUDA with a message otherwise).
+void need(const DevBuf &b, size_t bytes, const char *what);
+
+// Hand unused blocks of the library's memory pool back to the driver (call
+// after a device or stream synchronisation that retired the frees).
+void trim_pool() noexcept;
+
 // Copy `bytes` from a host or device pointer into device memory (stream-ordered).
 void copy_in(void *dst_dev, const void *src_any, size_t bytes, cudaStream_t s);
 
@@ -89,6 +97,23 @@ struct BinPlan {
     DevBuf chunk_e0;      // int64[n_chunks]
 };
 
+// The segmented flag walk (spmm_seg.cuh) over one CSR: a copy of the column
+// ids with bit 31 set on the first nonzero of every row (zero-padded to whole
+// tiles of the widest tile), the rows with and without nonzeros, and the
+// exclusive prefix of the nonempty-row flags (int64[n + 1]).
+struct SegRows {
+    bool built = false;
+    int64_t n_nz = 0, n_empty = 0, padded = 0;
+    DevBuf colf, nz_rows, empty_rows, nzpos;
+};
+// Tiles of tn nonzeros: crow0[t] (int32[tiles + 1]) is the number of rows
+// that start before tile t.
+struct SegTiles {
+    int64_t tn = 0, tiles = 0;
+    DevBuf crow0;
+};
+constexpr int64_t SEG_MAX_TN = 1024;   // the padding of the column copy covers tiles up to this size
+
 // ---------------------------------------------------------------- graph ---
 // The column and value arrays of both CSRs hold CSR_PAD extra zero elements
 // after the m real ones, so kernels may stage a tile's nonzeros in 16-byte
@@ -109,7 +134,11 @@ struct Workspace {
     DevBuf touched;         // push path: one bit per row reached by the push
     DevBuf x2;              // push path: x2 [n][KP <= 16], zero outside the marked rows
     DevBuf cpart;           // binned-row kernels: chunk sums of long rows [chunks][KP]
+    DevBuf agg;             // segmented kernel: tagged carry-out words [tiles][KP] (zeroed when allocated)
     bool u_clean = false;   // u, touched and x2 are known to be all zero
+    // rows of x without in-edges may hold nonzeros (x0 written there): 0 no,
+    // 1 only the current chunk's seeds, 2 any of them
+    int x_dirty = 2;
     int32_t *hflag = nullptr;   // pinned host mirror of the done flag (2 slots)
 };
 
@@ -139,6 +168,8 @@ struct tpa_graph {
     std::map<int, tpa::Plan> plans_t;   // merge-path plans over CSR(A~^T) keyed by L
     std::map<int, tpa::Plan> plans_a;   // merge-path plans over CSR(A~) keyed by L
     tpa::BinPlan bins_t, bins_a;        // row bins of CSR(A~^T) and CSR(A~)
+    tpa::SegRows seg_t, seg_a;          // flag-walk data of CSR(A~^T) and CSR(A~)
+    std::map<int, tpa::SegTiles> segt_t, segt_a;   // flag-walk tiles keyed by tile size
     tpa::Workspace ws;
 };
 
@@ -150,6 +181,9 @@ struct Ctl {
     int32_t ticket;         // last-block-done counter for the fixup reduction
     int32_t iter;           // current iteration index (written by the host-side schedule)
     int32_t push;           // 1: this query chunk takes the push path for x1, x2 (decided on the device)
+    uint32_t epoch;         // launches of the segmented SpMM so far (tags its carry-out words; never reset)
+    int32_t error;          // 1: a bounded device wait gave up (kept until the host reads and clears it)
+    int32_t pad_[2];
 };
 // Per-column state follows the Ctl header in the control buffer:
 //   int32 alive[kpad], int32 iters[kpad], double norm[kpad]
