@@ -125,6 +125,16 @@ tpa_status tpa_query_sets(tpa_graph *g, const int64_t *set_ptr, const int32_t *m
 tpa_status tpa_cpi(tpa_graph *g, const int32_t *seeds, int k, double c, double eps, int s_iter,
                    int t_iter, float *out, int32_t *iters, void *stream);
 
+/*
+ * Wait for the graph's work on `stream` and report whether a bounded device
+ * wait of its kernels gave up since the last check (TPA_ETIMEOUT; the
+ * results of those calls are not valid).  The SpMV/SpMM of a CPI iteration
+ * finishes rows that span tiles by waiting, with a limit of about a second,
+ * for the partial sums of earlier tiles; calls that synchronise anyway
+ * (host outputs, tpa_preprocess) check by themselves.
+ */
+tpa_status tpa_sync(tpa_graph *g, void *stream);
+
 /* Exact RWR by CPI for one seed (Algorithm 1 with s_iter = 0, t_iter = inf). */
 tpa_status tpa_cpi_exact(tpa_graph *g, int32_t seed, double c, double eps, float *out,
                          int32_t *iters, void *stream);
@@ -149,11 +159,16 @@ tpa_status tpa_load_preprocessed(tpa_graph *g, const char *path, void *stream);
  * col int32[m], val float32[m]; rows = destinations), adds y into r when r is
  * not NULL, and writes ||y||_1 (FP64) to l1[0] when l1 is not NULL.  Every
  * array must be device memory; the call is stream-ordered on `stream`.
+ * The CSR is not validated on the device: row_ptr[0] = 0, row_ptr[n] = m,
+ * row_ptr non-decreasing and 0 <= col[e] < n are the caller's to guarantee
+ * (an id out of range makes the step read out of bounds).  x, y and r must
+ * be three distinct arrays (TPA_EINVAL otherwise): the step is not in place.
  *
  * Scratch lives in a file-scope device array of TPA_NOALLOC_SCRATCH_BYTES
- * (16 MiB) that every GPU loading the library holds until the process exits;
- * it fits graphs with n + m up to about 119 million (TPA_EINVAL beyond, with
- * the needed size in tpa_last_error).  The first call on each device looks up
+ * (16 MiB) that every GPU loading the library holds until the process exits.
+ * Its layout takes 32 bytes per merge-path tile of 256 steps plus about
+ * 10 KB, so it fits graphs with n + m up to about 134 million (TPA_EINVAL
+ * beyond, with the needed size in tpa_last_error).  The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress); make that first call
  * before any stream capture.  All calls share the one array, so calls whose
  * GPU work overlaps (other streams, other threads) race and give wrong
@@ -180,6 +195,15 @@ tpa_status tpa_set_edge_weights(tpa_graph *g, const float *w, void *stream);
 tpa_status tpa_edge_weights(const float *feat, const float *theta, int d, int64_t m, float *w, void *stream);
 
 /*
+ * Bytes of stranger-chain iterates the reverse sweep of tpa_loss_grad keeps
+ * (default 16 GiB).  When the K+1 iterates of n floats need more, only every
+ * C-th one is kept, C = ceil(sqrt(K+1)), and each segment of C iterates is
+ * recomputed from its checkpoint when the sweep reaches it (about 2 sqrt(K)
+ * vectors instead of K+1, for K more SpMVs); the gradient is bit-identical.
+ */
+tpa_status tpa_set_adjoint_budget(uint64_t bytes);
+
+/*
  * L = sum over ntrip triples (s, p, q) of softplus(r[q] - r[p]), where
  * r = (1+alpha) r_family(s) + r~_stranger follows Algorithms 2-3 on the
  * current weights with the stranger chain run for exactly K >= T iterations
@@ -188,7 +212,8 @@ tpa_status tpa_edge_weights(const float *feat, const float *theta, int d, int64_
  * dL/dw (float32[m], CSR(A~) order, device or host) to grad_w, computed by the
  * adjoint recursions l_i = (1+alpha) g + P^T l_{i+1} (family, S-1 steps) and
  * m_i = [i >= T] G + P^T m_{i+1} (stranger, K steps) with P^T = (1-c) A~ and
- * the row-normalisation Jacobian.  Unweighted graphs use unit weights.
+ * the row-normalisation Jacobian.  grad_w = NULL computes the loss alone (no
+ * reverse sweep, no stored iterates).  Unweighted graphs use unit weights.
  */
 tpa_status tpa_loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const int32_t *neg, int ntrip,
                          double c, int S, int T, int K, double *loss, float *grad_w, void *stream);
@@ -307,6 +332,10 @@ tpa_status tpa_server_result(const tpa_server *srv, float **out, int64_t *ldo);
  * a replay or a direct run followed by a capture).  NULL outputs are skipped. */
 tpa_status tpa_server_stats(const tpa_server *srv, int k, int64_t *graphs, int64_t *replays,
                             int64_t *launches_per_replay, int64_t *captures);
+
+/* Wait for the server's work on `stream`; TPA_ETIMEOUT when a bounded
+ * device wait of its kernels gave up since the last check (see tpa_sync). */
+tpa_status tpa_server_sync(tpa_server *srv, void *stream);
 
 /* Release the server (waits for its work). */
 void tpa_server_free(tpa_server *srv);

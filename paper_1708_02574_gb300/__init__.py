@@ -20,7 +20,9 @@ from .tpa import (  # noqa: F401
     cpi_step_noalloc,
     edge_weights,
     loss_grad,
+    set_adjoint_budget,
     set_edge_weights,
+    sync,
     theta_grad,
     get_csr,
     get_stranger,

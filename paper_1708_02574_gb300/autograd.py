@@ -3,9 +3,10 @@
 Edge weights w_e = exp(theta . f_e) parameterise A~ = w / rowsum.  The loss is
 L = sum over triples (s, p, q) of softplus(r_TPA^(s)[q] - r_TPA^(s)[p]), with
 r_TPA from Algorithms 2-3 (the stranger chain run for exactly K iterations).
-The forward pass already runs the adjoint kernels (tpa_loss_grad), because the
-backward recursions need the forward iterates; backward scales the stored
-dL/dtheta by the incoming gradient.
+When theta requires a gradient, the forward pass already runs the adjoint
+kernels (tpa_loss_grad), because the backward recursions need the forward
+iterates, and backward scales the stored dL/dtheta by the incoming gradient;
+otherwise the forward pass computes the loss alone.
 """
 from __future__ import annotations
 
@@ -23,8 +24,9 @@ class TPALinkLoss(torch.autograd.Function):
             # the iteration count of preprocessing on these weights (Algorithm 2's break)
             tpa.preprocess(g, c, T, eps)
             K = max(int(tpa.get_stranger(g)[1]), T)
-        loss, gw = tpa.loss_grad(g, seeds, pos, neg, c, S, T, K)
-        gtheta = tpa.theta_grad(feat, w, gw)
+        want = bool(ctx.needs_input_grad[0])
+        loss, gw = tpa.loss_grad(g, seeds, pos, neg, c, S, T, K, want_grad=want)
+        gtheta = tpa.theta_grad(feat, w, gw) if want else torch.zeros_like(theta, dtype=torch.float64)
         ctx.save_for_backward(gtheta)
         ctx.theta_dtype = theta.dtype
         ctx.K = K

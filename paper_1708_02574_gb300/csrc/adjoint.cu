@@ -270,34 +270,128 @@ void theta_grad(const float *feat, const float *w, const float *gw, int d, int64
     tick.release(s);
 }
 
-// Loss and dL/dw (device float[m], CSR(A~) order).  seeds/pos/neg are device arrays.
+// Iterates x'_0 .. x'_{K-1} of the stranger chain as the reverse sweep asks
+// for them (in decreasing order).  Either all are kept (K+1 vectors of n), or
+// only every C-th one is, C = ceil(sqrt(K+1)), and the C iterates of a segment
+// are recomputed from its checkpoint when the sweep enters it: about
+// 2 sqrt(K) vectors instead of K+1, for K extra SpMVs.  The recomputation runs
+// the same deterministic kernel on the same input, so the iterates, and the
+// gradient, are bit-identical either way.
+struct StrangerIterates {
+    tpa_graph *g = nullptr;
+    int64_t n = 0;
+    int K = 0, C = 0;           // C = 0: every iterate is kept
+    float decay = 0.0f;
+    DevBuf all, ck, seg;
+    int seg_base = -1;
+
+    // Bytes of device memory each way keeps.
+    static size_t full_bytes(int64_t n, int K) { return (size_t)(K + 1) * n * sizeof(float); }
+    static int stride(int K) { return (int)std::ceil(std::sqrt((double)(K + 1))); }
+    static size_t checkpoint_bytes(int64_t n, int K)
+    {
+        const int C = stride(K);
+        return ((size_t)(K / C + 1) + (size_t)C) * n * sizeof(float);
+    }
+
+    void init(tpa_graph *g_, int K_, float decay_, bool checkpoint, cudaStream_t s)
+    {
+        g = g_;
+        n = g->n;
+        K = K_;
+        decay = decay_;
+        if (checkpoint) {
+            C = stride(K);
+            ck.ensure((size_t)(K / C + 1) * n * sizeof(float), s);
+            seg.ensure((size_t)C * n * sizeof(float), s);
+        } else {
+            all.ensure(full_bytes(n, K), s);
+        }
+    }
+    // Buffer the forward sweep writes x'_i into (a segment slot when checkpointing).
+    float *fwd_slot(int i)
+    {
+        if (!C) return all.as<float>() + (int64_t)i * n;
+        return seg.as<float>() + (int64_t)(i % C) * n;
+    }
+    // After x'_i is written: keep it when it is a checkpoint.
+    void fwd_done(int i, cudaStream_t s)
+    {
+        if (C && i % C == 0)
+            TPA_CUDA(cudaMemcpyAsync(ck.as<float>() + (int64_t)(i / C) * n, fwd_slot(i), (size_t)n * sizeof(float),
+                                     cudaMemcpyDeviceToDevice, s));
+    }
+    const float *get(int i, cudaStream_t s)
+    {
+        if (!C) return all.as<float>() + (int64_t)i * n;
+        const int base = (i / C) * C;
+        if (base != seg_base) {
+            float *S0 = seg.as<float>();
+            TPA_CUDA(cudaMemcpyAsync(S0, ck.as<float>() + (int64_t)(base / C) * n, (size_t)n * sizeof(float),
+                                     cudaMemcpyDeviceToDevice, s));
+            for (int t = 1; t < C && base + t <= K - 1; ++t)
+                spmv_apply(g, 0, S0 + (int64_t)(t - 1) * n, S0 + (int64_t)t * n, 1, decay, s);
+            seg_base = base;
+        }
+        return seg.as<float>() + (int64_t)(i - base) * n;
+    }
+    void release(cudaStream_t s)
+    {
+        all.release(s);
+        ck.release(s);
+        seg.release(s);
+    }
+};
+
+size_t g_adjoint_budget = (size_t)16 << 30;   // iterate bytes kept before checkpointing starts
+
+// Loss and dL/dw (device float[m], CSR(A~) order; grad_w = nullptr: the loss
+// only, without the reverse sweep or stored iterates).  seeds/pos/neg are
+// device arrays.
 double loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const int32_t *neg, int ntrip, double c,
                  int S, int T, int K, float *grad_w, cudaStream_t s)
 {
     const int64_t n = g->n, m = g->m;
     const float decay = (float)(1.0 - c);
     const float opa = (float)(1.0 + alpha_of(c, S, T));
+    const bool want_grad = grad_w != nullptr;
     ensure_row_ids(g, s);
-    DevBuf xs, rs, F, lamA, lamB, GE, loss, sg, gacc, Gs;
-    xs.ensure((size_t)(K + 1) * n * sizeof(float), s);
+    DevBuf rs, F, lamA, lamB, GE, loss, sg, gacc, Gs, two;
+    StrangerIterates X;
     rs.ensure((size_t)n * sizeof(float), s);
     F.ensure((size_t)S * n * KB * sizeof(float), s);
     lamA.ensure((size_t)n * KB * sizeof(float), s);
     lamB.ensure((size_t)n * KB * sizeof(float), s);
-    GE.ensure((size_t)std::max<int64_t>(m, 1) * sizeof(float), s);
     loss.ensure((size_t)ntrip * sizeof(double), s);
     sg.ensure((size_t)ntrip * sizeof(double), s);
     gacc.ensure((size_t)n * sizeof(unsigned long long), s);
-    Gs.ensure((size_t)n * sizeof(float), s);
-    TPA_CUDA(cudaMemsetAsync(GE.p, 0, GE.bytes, s));
     TPA_CUDA(cudaMemsetAsync(gacc.p, 0, gacc.bytes, s));
-    float *X = xs.as<float>();
+    TPA_CUDA(cudaMemsetAsync(rs.p, 0, rs.bytes, s));
+    if (want_grad) {
+        X.init(g, K, decay, StrangerIterates::full_bytes(n, K) > g_adjoint_budget, s);
+        GE.ensure((size_t)std::max<int64_t>(m, 1) * sizeof(float), s);
+        Gs.ensure((size_t)n * sizeof(float), s);
+        TPA_CUDA(cudaMemsetAsync(GE.p, 0, GE.bytes, s));
+    } else {
+        two.ensure((size_t)2 * n * sizeof(float), s);
+    }
 
-    // stranger chain, K fixed
-    fill_k<<<grid_for(n), 256, 0, s>>>(X, n, (float)(c * (1.0 / (double)n)));
-    for (int i = 1; i <= K; ++i) spmv_apply(g, 0, X + (int64_t)(i - 1) * n, X + (int64_t)i * n, 1, decay, s);
-    stranger_sum_k<<<grid_for(n), 256, 0, s>>>(X, n, T, K, rs.as<float>());
-    note_launch("adjoint", 2);
+    // stranger chain, K fixed: r~_stranger = x'_T + ... + x'_K, added in
+    // iteration order (the same FP32 sums whether or not iterates are kept)
+    auto slot = [&](int i) { return want_grad ? X.fwd_slot(i) : two.as<float>() + (int64_t)(i & 1) * n; };
+    fill_k<<<grid_for(n), 256, 0, s>>>(slot(0), n, (float)(c * (1.0 / (double)n)));
+    note_launch("adjoint");
+    TPA_CHECK_LAUNCH();
+    if (want_grad) X.fwd_done(0, s);
+    if (T == 0) axpy_k<<<grid_for(n), 256, 0, s>>>(rs.as<float>(), slot(0), n);
+    for (int i = 1; i <= K; ++i) {
+        spmv_apply(g, 0, slot(i - 1), slot(i), 1, decay, s);
+        if (want_grad) X.fwd_done(i, s);
+        if (i >= T) {
+            axpy_k<<<grid_for(n), 256, 0, s>>>(rs.as<float>(), slot(i), n);
+            note_launch("adjoint");
+        }
+    }
     TPA_CHECK_LAUNCH();
 
     // family chains in batches of KB triples: forward, scores, backward
@@ -310,6 +404,8 @@ double loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const i
         for (int i = 1; i < S; ++i) spmv_apply(g, 0, Fp + (int64_t)(i - 1) * n * KB, Fp + (int64_t)i * n * KB, KB, decay, s);
         pair_k<<<1, 32, 0, s>>>(Fp, n, S, pos + t0, neg + t0, kb, opa, rs.as<float>(), loss.as<double>() + t0,
                                 sg.as<double>() + t0, gacc.as<unsigned long long>());
+        note_launch("adjoint", 2);
+        if (!want_grad) continue;
         float *lam = lamA.as<float>(), *nxt = lamB.as<float>();
         TPA_CUDA(cudaMemsetAsync(lam, 0, (size_t)n * KB * sizeof(float), s));
         scatter_g_k<<<1, 32, 0, s>>>(lam, pos + t0, neg + t0, sg.as<double>() + t0, kb, opa);
@@ -322,28 +418,30 @@ double loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const i
                 scatter_g_k<<<1, 32, 0, s>>>(lam, pos + t0, neg + t0, sg.as<double>() + t0, kb, opa);
             }
         }
-        note_launch("adjoint", 3 + 2 * (S - 1));
+        note_launch("adjoint", 1 + 2 * (S - 1));
         TPA_CHECK_LAUNCH();
     }
 
-    // stranger backward: m_K = G, m_i = [i >= T] G + P^T m_{i+1}
-    gacc_to_float_k<<<grid_for(n), 256, 0, s>>>(gacc.as<unsigned long long>(), n, Gs.as<float>());
-    float *mu = lamA.as<float>(), *mn = lamB.as<float>();   // [n] vectors now
-    TPA_CUDA(cudaMemcpyAsync(mu, Gs.p, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    for (int i = K; i >= 1; --i) {
-        sddmm_k<1><<<grid_for(m), 256, 0, s>>>(g->row_a.as<int32_t>(), g->col_a.as<int32_t>(), m, mu,
-                                               X + (int64_t)(i - 1) * n, 1, decay, GE.as<float>());
-        if (i > 1) {
-            spmv_apply(g, 1, mu, mn, 1, decay, s);
-            std::swap(mu, mn);
-            if (i - 1 >= T) axpy_k<<<grid_for(n), 256, 0, s>>>(mu, Gs.as<float>(), n);
+    if (want_grad) {
+        // stranger backward: m_K = G, m_i = [i >= T] G + P^T m_{i+1}
+        gacc_to_float_k<<<grid_for(n), 256, 0, s>>>(gacc.as<unsigned long long>(), n, Gs.as<float>());
+        float *mu = lamA.as<float>(), *mn = lamB.as<float>();   // [n] vectors now
+        TPA_CUDA(cudaMemcpyAsync(mu, Gs.p, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        for (int i = K; i >= 1; --i) {
+            sddmm_k<1><<<grid_for(m), 256, 0, s>>>(g->row_a.as<int32_t>(), g->col_a.as<int32_t>(), m, mu,
+                                                   X.get(i - 1, s), 1, decay, GE.as<float>());
+            if (i > 1) {
+                spmv_apply(g, 1, mu, mn, 1, decay, s);
+                std::swap(mu, mn);
+                if (i - 1 >= T) axpy_k<<<grid_for(n), 256, 0, s>>>(mu, Gs.as<float>(), n);
+            }
         }
+        note_launch("adjoint", 1 + 2 * K);
+        jacobian_k<<<grid_for(n * 32), 256, 0, s>>>(g->rp_a.as<int64_t>(), GE.as<float>(), g->val_a.as<float>(),
+                                                   g->inv_d.as<double>(), n, grad_w);
+        note_launch("adjoint");
+        TPA_CHECK_LAUNCH();
     }
-    note_launch("adjoint", 1 + 2 * K);
-    jacobian_k<<<grid_for(n * 32), 256, 0, s>>>(g->rp_a.as<int64_t>(), GE.as<float>(), g->val_a.as<float>(),
-                                               g->inv_d.as<double>(), n, grad_w);
-    note_launch("adjoint");
-    TPA_CHECK_LAUNCH();
 
     loss_sum_k<<<1, 1, 0, s>>>(loss.as<double>(), ntrip, sg.as<double>());
     note_launch("adjoint");
@@ -351,8 +449,9 @@ double loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const i
     double L = 0.0;
     TPA_CUDA(cudaMemcpyAsync(&L, sg.p, sizeof(double), cudaMemcpyDeviceToHost, s));
     TPA_CUDA(cudaStreamSynchronize(s));
-    xs.release(s); rs.release(s); F.release(s); lamA.release(s); lamB.release(s); GE.release(s);
-    loss.release(s); sg.release(s); gacc.release(s); Gs.release(s);
+    X.release(s);
+    rs.release(s); F.release(s); lamA.release(s); lamB.release(s); GE.release(s);
+    loss.release(s); sg.release(s); gacc.release(s); Gs.release(s); two.release(s);
     return L;
 }
 

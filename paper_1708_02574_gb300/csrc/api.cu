@@ -166,6 +166,24 @@ static std::vector<int32_t> read_seeds(const int32_t *seeds, int k, int64_t n, c
     return h;
 }
 
+// Raise TPA_ETIMEOUT when a bounded device wait of the graph's kernels gave
+// up since the last check (the flag lives in the control block and is
+// cleared here).  Called where a call synchronises anyway.
+static void check_waits(tpa_graph *g, cudaStream_t s)
+{
+    if (!g->ws.ctl.p) return;
+    int32_t *flag = &static_cast<Ctl *>(g->ws.ctl.p)->error;
+    int32_t e = 0;
+    TPA_CUDA(cudaMemcpyAsync(&e, flag, sizeof e, cudaMemcpyDeviceToHost, s));
+    TPA_CUDA(cudaStreamSynchronize(s));
+    if (e) {
+        TPA_CUDA(cudaMemsetAsync(flag, 0, sizeof e, s));
+        TPA_CUDA(cudaStreamSynchronize(s));
+        set_error("a bounded device wait gave up: the results of the calls since the last check are not valid");
+        throw Fail{TPA_ETIMEOUT};
+    }
+}
+
 }  // namespace tpa
 
 using namespace tpa;
@@ -245,6 +263,11 @@ void tpa_free_graph(tpa_graph *g)
                       &g->ws.out, &g->ws.iters};
     for (DevBuf *b : bufs) b->release(s);
     g->ws.cpart.release(s);
+    g->ws.agg.release(s);
+    for (tpa::SegRows *R : {&g->seg_t, &g->seg_a})
+        for (DevBuf *b : {&R->colf, &R->nz_rows, &R->empty_rows, &R->nzpos}) b->release(s);
+    for (auto *tiles : {&g->segt_t, &g->segt_a})
+        for (auto &kv : *tiles) kv.second.crow0.release(s);
     for (tpa::BinPlan *B : {&g->bins_t, &g->bins_a})
         for (DevBuf *b : {&B->rows_short, &B->rows_mid, &B->rows_long, &B->rows_empty, &B->long_first,
                           &B->chunk_row, &B->chunk_e0})
@@ -322,6 +345,7 @@ tpa_status tpa_preprocess(tpa_graph *g, double c, int T, double eps, void *strea
     int32_t it = 0;
     TPA_CUDA(cudaMemcpyAsync(&it, a.iters_out, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     TPA_CUDA(cudaStreamSynchronize(s));
+    check_waits(g, s);
     g->pre_iters = it;
     g->c = c;
     g->T = T;
@@ -395,6 +419,7 @@ tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *ou
         if (!mapped)
             TPA_CUDA(cudaMemcpyAsync(out, dout, (size_t)g->n * k * sizeof(float), cudaMemcpyDeviceToHost, s));
         TPA_CUDA(cudaStreamSynchronize(s));
+        check_waits(g, s);
     }
     API_END
 }
@@ -499,6 +524,7 @@ tpa_status tpa_cpi(tpa_graph *g, const int32_t *seeds, int k, double c, double e
     if (host_out) {
         TPA_CUDA(cudaMemcpyAsync(out, dout, (size_t)g->n * k * sizeof(float), cudaMemcpyDeviceToHost, s));
         TPA_CUDA(cudaStreamSynchronize(s));
+        check_waits(g, s);
     }
     API_END
 }
@@ -527,11 +553,25 @@ tpa_status tpa_edge_weights(const float *feat, const float *theta, int d, int64_
     API_END
 }
 
+tpa_status tpa_sync(tpa_graph *g, void *stream)
+{
+    API_BEGIN
+    TPA_REQUIRE(g != nullptr, "tpa_sync: NULL graph");
+    check_waits(g, (cudaStream_t)stream);
+    API_END
+}
+
+tpa_status tpa_set_adjoint_budget(uint64_t bytes)
+{
+    g_adjoint_budget = (size_t)bytes;
+    return TPA_OK;
+}
+
 tpa_status tpa_loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const int32_t *neg, int ntrip,
                          double c, int S, int T, int K, double *loss, float *grad_w, void *stream)
 {
     API_BEGIN
-    TPA_REQUIRE(g && seeds && pos && neg && loss && grad_w, "tpa_loss_grad: NULL argument");
+    TPA_REQUIRE(g && seeds && pos && neg && loss, "tpa_loss_grad: NULL argument");
     TPA_REQUIRE(ntrip >= 1, "tpa_loss_grad: ntrip = %d < 1", ntrip);
     TPA_REQUIRE(c > 0.0 && c < 1.0, "tpa_loss_grad: c = %g outside (0, 1)", c);
     TPA_REQUIRE(S >= 1 && S <= T && T <= K && K <= 100000, "tpa_loss_grad: need 1 <= S <= T <= K");
@@ -553,7 +593,7 @@ tpa_status tpa_loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos,
     TPA_CUDA(cudaMemcpyAsync(trip.as<int32_t>(), hs.data(), (size_t)ntrip * 4, cudaMemcpyHostToDevice, s));
     TPA_CUDA(cudaMemcpyAsync(trip.as<int32_t>() + ntrip, hp.data(), (size_t)ntrip * 4, cudaMemcpyHostToDevice, s));
     TPA_CUDA(cudaMemcpyAsync(trip.as<int32_t>() + 2 * ntrip, hq.data(), (size_t)ntrip * 4, cudaMemcpyHostToDevice, s));
-    const bool host_out = !is_device_ptr(grad_w);
+    const bool host_out = grad_w && !is_device_ptr(grad_w);
     DevBuf gw;
     float *dgw = grad_w;
     if (host_out) {

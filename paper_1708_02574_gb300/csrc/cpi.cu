@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstddef>
+#include <cstring>
 #include <cmath>
 #include <numeric>
 #include <vector>
@@ -37,6 +38,7 @@
 
 #include "spmm_kernels.cuh"
 #include "spmm_binned.cuh"
+#include "spmm_seg.cuh"
 
 namespace tpa {
 
@@ -122,6 +124,94 @@ static const BinPlan &get_bin_plan(tpa_graph *g, int which, cudaStream_t s)
     cnt.release(s);
     B.built = true;
     return B;
+}
+
+// Flag-walk data of CSR(A~^T) (which = 0) or CSR(A~), built once per graph.
+static const SegRows &get_seg_rows(tpa_graph *g, int which, cudaStream_t s)
+{
+    SegRows &R = which ? g->seg_a : g->seg_t;
+    if (R.built) return R;
+    const int64_t n = g->n, m = g->m;
+    const int64_t *rp = which ? g->rp_a.as<int64_t>() : g->rp_t.as<int64_t>();
+    const int32_t *col = which ? g->col_a.as<int32_t>() : g->col_t.as<int32_t>();
+    DevBuf nzf, ef, epos, tmp;
+    nzf.ensure((size_t)n * sizeof(int32_t), s);
+    ef.ensure((size_t)n * sizeof(int32_t), s);
+    R.nzpos.ensure((size_t)(n + 1) * sizeof(int64_t), s);
+    epos.ensure((size_t)(n + 1) * sizeof(int64_t), s);
+    seg_row_flags_k<<<grid_1d(n, 256), 256, 0, s>>>(rp, n, nzf.as<int32_t>(), ef.as<int32_t>());
+    TPA_CHECK_LAUNCH();
+    exclusive_scan_i32_i64(nzf.as<int32_t>(), R.nzpos.as<int64_t>(), n, tmp, s);
+    exclusive_scan_i32_i64(ef.as<int32_t>(), epos.as<int64_t>(), n, tmp, s);
+    int64_t cnt[2];
+    TPA_CUDA(cudaMemcpyAsync(&cnt[0], R.nzpos.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TPA_CUDA(cudaMemcpyAsync(&cnt[1], epos.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TPA_CUDA(cudaStreamSynchronize(s));
+    R.n_nz = cnt[0];
+    R.n_empty = cnt[1];
+    R.nz_rows.ensure((size_t)std::max<int64_t>(1, R.n_nz) * sizeof(int32_t), s);
+    R.empty_rows.ensure((size_t)std::max<int64_t>(1, R.n_empty) * sizeof(int32_t), s);
+    seg_scatter_rows_k<<<grid_1d(n, 256), 256, 0, s>>>(rp, n, R.nzpos.as<int64_t>(), epos.as<int64_t>(),
+                                                       R.nz_rows.as<int32_t>(), R.empty_rows.as<int32_t>());
+    TPA_CHECK_LAUNCH();
+    R.padded = (m + SEG_MAX_TN - 1) / SEG_MAX_TN * SEG_MAX_TN + SEG_MAX_TN;
+    R.colf.ensure((size_t)R.padded * sizeof(uint32_t), s);
+    seg_copy_cols_k<<<grid_1d(R.padded, 256), 256, 0, s>>>(col, m, R.padded, R.colf.as<uint32_t>());
+    seg_mark_k<<<grid_1d(n, 256), 256, 0, s>>>(rp, n, R.colf.as<uint32_t>());
+    note_launch("plan", 5);
+    TPA_CHECK_LAUNCH();
+    TPA_CUDA(cudaStreamSynchronize(s));
+    nzf.release(s);
+    ef.release(s);
+    epos.release(s);
+    tmp.release(s);
+    R.built = true;
+    return R;
+}
+
+// Tiles of tn nonzeros over CSR(A~^T) (which = 0) or CSR(A~).
+static const SegTiles &get_seg_tiles(tpa_graph *g, int which, int64_t tn, cudaStream_t s)
+{
+    TPA_REQUIRE(tn >= 32 && tn <= SEG_MAX_TN, "segmented walk: tile of %lld nonzeros", (long long)tn);
+    std::map<int, SegTiles> &M = which ? g->segt_a : g->segt_t;
+    auto it = M.find((int)tn);
+    if (it != M.end()) return it->second;
+    const SegRows &R = get_seg_rows(g, which, s);
+    const int64_t *rp = which ? g->rp_a.as<int64_t>() : g->rp_t.as<int64_t>();
+    SegTiles &T = M[(int)tn];
+    T.tn = tn;
+    T.tiles = (g->m + tn - 1) / tn;
+    TPA_REQUIRE(T.tiles * tn <= R.padded, "segmented walk: column copy too short");
+    T.crow0.ensure((size_t)(T.tiles + 1) * sizeof(int32_t), s);
+    seg_tiles_k<<<grid_1d(T.tiles + 1, 256), 256, 0, s>>>(rp, g->n, g->m, R.nzpos.as<int64_t>(), tn, T.tiles,
+                                                          T.crow0.as<int32_t>());
+    note_launch("plan");
+    TPA_CHECK_LAUNCH();
+    return T;
+}
+
+// Point the flag-walk fields of p at the data of a CSR; sizes the carry-out
+// words of the workspace for kp columns (zeroed whenever allocated).
+static void bind_seg(Params &p, tpa_graph *g, int which, int64_t tn, int kp, cudaStream_t s)
+{
+    const SegRows &R = get_seg_rows(g, which, s);
+    const SegTiles &T = get_seg_tiles(g, which, tn, s);
+    Workspace &W = g->ws;
+    const size_t agg_bytes = (size_t)std::max<int64_t>(1, T.tiles) * kp * sizeof(unsigned long long);
+    if (!W.agg.p || W.agg.bytes < agg_bytes) {
+        W.agg.ensure(agg_bytes, s);
+        TPA_CUDA(cudaMemsetAsync(W.agg.p, 0, W.agg.bytes, s));
+    }
+    need(W.agg, (size_t)T.tiles * kp * sizeof(unsigned long long), "carry-out words");
+    need(R.colf, (size_t)T.tiles * tn * sizeof(uint32_t), "flagged columns");
+    p.colf = R.colf.as<uint32_t>();
+    p.nz_rows = R.nz_rows.as<int32_t>();
+    p.empty_rows = R.empty_rows.as<int32_t>();
+    p.n_empty = R.n_empty;
+    p.tile_crow0 = T.crow0.as<int32_t>();
+    p.seg_tiles = T.tiles;
+    p.m = g->m;
+    p.agg = W.agg.as<unsigned long long>();
 }
 
 // Point the binned-row fields of p at the bins of a CSR (and the chunk sums).
@@ -234,6 +324,55 @@ static int64_t launch_spmvp(const Params &p, cudaStream_t s)
     return grid * WARPS;
 }
 
+// Segmented flag walk (spmm_seg.cuh): persistent grid of at most the
+// kernel's occupancy times the SM count (its waits need every CTA resident);
+// returns the CTAs launched (rows of the L1 partial buffer).
+template <int V, int R, int PF>
+static int64_t launch_seg(const Params &p, cudaStream_t s)
+{
+    constexpr size_t smem = seg_smem_bytes<V, R>();
+    static_assert(smem <= 227 * 1024, "shared memory per block");
+    auto *const valued = spmm_seg_k<V, R, PF, false>;
+    auto *const pattern = spmm_seg_k<V, R, PF, true>;
+    static int per_sm_v = 0, per_sm_p = 0;
+    if (!per_sm_v) {
+        for (auto *fn : {valued, pattern}) {
+            TPA_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            TPA_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
+        }
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_v, valued, SEG_WARPS * 32, smem));
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_p, pattern, SEG_WARPS * 32, smem));
+        TPA_REQUIRE(per_sm_v >= 1 && per_sm_p >= 1, "segmented walk: the kernel does not fit on an SM");
+    }
+    const int per_sm = p.inv_deg ? per_sm_p : per_sm_v;
+    int64_t grid =
+        std::max<int64_t>(1, std::min<int64_t>((p.seg_tiles + SEG_WARPS - 1) / SEG_WARPS, (int64_t)per_sm * num_sms()));
+    // a cooperative launch: the driver starts every CTA at once or refuses
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.blockDim = dim3(SEG_WARPS * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    for (;;) {
+        cfg.gridDim = dim3((unsigned)grid);
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, p.inv_deg ? pattern : valued, p);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorCooperativeLaunchTooLarge || grid == 1) TPA_CUDA(e);
+        cudaGetLastError();
+        grid = (grid + 1) / 2;
+    }
+    return grid;
+}
+
+// Upper bound of the CTAs of any persistent grid (32 resident blocks per SM at most).
+static int64_t seg_grid_bound() { return (int64_t)32 * num_sms(); }
+
 // Binned-row kernels (spmm_binned.cuh): short, medium, chunks of long rows,
 // long-row combine, empty rows; returns the rows of tl1 written.
 template <int KP>
@@ -318,6 +457,7 @@ struct Variant {
     void (*fix)(const Params &, unsigned, cudaStream_t);
     const char *name;
     bool binned = false;   // binned-row kernels (need the row bins bound to Params)
+    bool seg = false;      // segmented flag walk: no fixup; tiles of cfg.L() nonzeros
 };
 
 #define TPA_VARIANT(G, V, I, PF) \
@@ -327,6 +467,8 @@ struct Variant {
 #define TPA_VARIANTG(G, V, I, PF) \
     {{G, V, I, PF, 32}, launch_spmvg<G, V, I, PF, 8>, launch_fix<G * V>, "walker<" #G "," #V "," #I "," #PF ">"}
 #define TPA_VARIANTB(KP) {{1, KP, 4, 4, 32}, launch_binned<KP>, launch_bin_finish<KP>, "bins<" #KP ">", true}
+#define TPA_VARIANTS(V, R, PF) \
+    {{1, V, R, PF, 32}, launch_seg<V, R, PF>, nullptr, "seg<" #V "," #R "," #PF ">", false, true}
 #define TPA_VARIANTP(G, V, I, PF, W, MB)                                 \
     {{G, V, I, PF, 32}, launch_spmvp<G, V, I, PF, W, MB>, launch_fix<G * V>, \
      "pipe<" #G "," #V "," #I "," #PF "," #W "," #MB ">"}
@@ -338,6 +480,17 @@ static const Variant kVariants[] = {
     TPA_VARIANTP(1, 4, 4, 4, 8, 1),
     TPA_VARIANTP(2, 4, 8, 8, 4, 5),
     TPA_VARIANTP(4, 4, 8, 8, 4, 1),
+    TPA_VARIANTS(1, 16, 16),
+    TPA_VARIANTS(2, 8, 8),
+    TPA_VARIANTS(4, 8, 8),
+    TPA_VARIANTS(8, 8, 8),
+    TPA_VARIANTS(1, 32, 16),
+    TPA_VARIANTS(1, 8, 8),
+    TPA_VARIANTS(2, 16, 8),
+    TPA_VARIANTS(4, 4, 4),
+    TPA_VARIANTS(4, 16, 8),
+    TPA_VARIANTS(8, 8, 4),
+    TPA_VARIANTS(8, 4, 4),
     TPA_VARIANT(8, 4, 16, 8),
     TPA_VARIANT(16, 4, 16, 8),
     TPA_VARIANT(32, 4, 32, 8),
@@ -396,6 +549,7 @@ static const Variant kVariants[] = {
 #undef TPA_VARIANTG
 #undef TPA_VARIANTP
 #undef TPA_VARIANTB
+#undef TPA_VARIANTS
 
 // Padded width: the smallest power of two >= k (every power of two up to
 // KP_MAX has at least one kernel variant).
@@ -502,23 +656,84 @@ static int iteration_bound(double c, double eps)
     return (int)std::min(1.0e6, i) + 4;
 }
 
+// Sizes the workspace buffers that one SpMV/SpMM launch of variant var at
+// padded width KP over CSR(A~^T) (which = 0) or CSR(A~) indexes, and checks
+// them against what the launch indexes; fills the plan fields of p.  The
+// control block is zeroed when first allocated (its launch counter must
+// start below every tag in the carry-out words).  Returns the blocks of the
+// fixup grid (0 for the segmented walk, which has no fixup).
+static unsigned size_for_variant(tpa_graph *g, const Variant &var, int which, int KP, Params &p, cudaStream_t s)
+{
+    Workspace &W = g->ws;
+    const bool fresh_ctl = !W.ctl.p;
+    W.ctl.ensure(CTL_BYTES, s);
+    if (fresh_ctl) TPA_CUDA(cudaMemsetAsync(W.ctl.p, 0, CTL_BYTES, s));
+    if (var.seg) {
+        const size_t fix_bytes = (size_t)seg_grid_bound() * KP * sizeof(double);
+        W.fix.ensure(fix_bytes, s);
+        need(W.fix, fix_bytes, "L1 partials");
+        bind_seg(p, g, which, var.cfg.L(), KP, s);
+        p.tiles = 0;
+        return 0;
+    }
+    const Plan &P = get_plan(g, var.cfg.L(), s, which);
+    const size_t tile_bytes = (size_t)P.tiles * KP * sizeof(float);
+    W.carry.ensure(tile_bytes, s);
+    W.head.ensure(tile_bytes, s);
+    int64_t tl1_rows = P.tiles + 8;   // per tile, or per warp of a grid
+    if (var.binned) tl1_rows = std::max(tl1_rows, binned_slots_bound(get_bin_plan(g, which, s).n_long, KP));
+    W.tl1.ensure((size_t)tl1_rows * KP * sizeof(float), s);
+    const unsigned fix_blocks = fix_grid(KP, P.tiles);
+    W.fix.ensure((size_t)fix_blocks * KP * sizeof(double), s);
+    need(W.carry, tile_bytes, "tile carries");
+    need(W.head, tile_bytes, "deferred heads");
+    need(W.tl1, (size_t)tl1_rows * KP * sizeof(float), "tile L1 partials");
+    need(W.fix, (size_t)fix_blocks * KP * sizeof(double), "fixup partials");
+    p.tile_x = P.tile_x.as<int32_t>();
+    p.tile_y = P.tile_y.as<int64_t>();
+    p.head_row = P.head_row.as<int32_t>();
+    p.head_first = P.head_first.as<int32_t>();
+    p.tiles = P.tiles;
+    p.carry = W.carry.as<float>();
+    p.head = W.head.as<float>();
+    p.tl1 = W.tl1.as<float>();
+    if (var.binned) bind_bins(p, g, which, KP, s);
+    return fix_blocks;
+}
+
+// Iterate buffers of n rows of KP floats: y is zeroed when allocated (the
+// segmented walk writes only rows with in-edges); a new x has unknown rows.
+static void size_iterates(tpa_graph *g, int KP, cudaStream_t s)
+{
+    Workspace &W = g->ws;
+    const size_t bytes = (size_t)g->n * KP * sizeof(float);
+    if (!W.x.p || W.x.bytes < bytes) {
+        W.x.ensure(bytes, s);
+        W.x_zkp = 0;
+        W.x_seeds = false;
+    }
+    if (!W.y.p || W.y.bytes < bytes) {
+        W.y.ensure(bytes, s);
+        TPA_CUDA(cudaMemsetAsync(W.y.p, 0, W.y.bytes, s));
+        W.y_zkp = -1;
+    }
+    need(W.x, bytes, "iterate x");
+    need(W.y, bytes, "iterate y");
+}
+
 void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t s)
 {
     const int KP = kp_for(kc);
     const Variant &var = pick_variant(KP);
-    const Plan &P = get_plan(g, var.cfg.L(), s);
     const int64_t n = g->n;
     Workspace &W = g->ws;
-    W.x.ensure((size_t)n * KP * sizeof(float), s);
-    W.y.ensure((size_t)n * KP * sizeof(float), s);
-    W.carry.ensure((size_t)P.tiles * KP * sizeof(float), s);
-    W.head.ensure((size_t)P.tiles * KP * sizeof(float), s);
-    int64_t tl1_rows = P.tiles + 8;   // per tile, or per warp of a grid
-    if (var.binned) tl1_rows = std::max(tl1_rows, binned_slots_bound(get_bin_plan(g, 0, s).n_long, KP));
-    W.tl1.ensure((size_t)tl1_rows * KP * sizeof(float), s);
-    const unsigned fix_blocks = fix_grid(KP, P.tiles);
-    W.fix.ensure((size_t)fix_blocks * KP * sizeof(double), s);
-    W.ctl.ensure(CTL_BYTES, s);
+    Params p{};
+    size_iterates(g, KP, s);
+    const unsigned fix_blocks = size_for_variant(g, var, 0, KP, p, s);
+    if (W.x_seeds) {   // the seeds were another chunk's
+        W.x_zkp = 0;
+        W.x_seeds = false;
+    }
 
     ctl_init_k<<<1, 256, 0, s>>>(W.ctl.p, kc);
     note_launch("init");
@@ -530,6 +745,7 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     int64_t ldr;
     if (a.r_internal) {
         W.r.ensure((size_t)n * KP * sizeof(float), s);
+        need(W.r, (size_t)n * KP * sizeof(float), "accumulator r");
         r = W.r.as<float>();
         ldr = KP;
     } else {
@@ -568,6 +784,10 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
             TPA_CUDA(cudaMemsetAsync(W.touched.p, 0, W.touched.bytes, s));
             TPA_CUDA(cudaMemsetAsync(W.x2.p, 0, W.x2.bytes, s));
         }
+        need(W.u, (size_t)n * KP * sizeof(unsigned long long), "push accumulator");
+        need(W.touched, (size_t)((n + 31) / 32) * sizeof(uint32_t), "push row marks");
+        need(W.x2, (size_t)n * KP * sizeof(float), "x2 buffer");
+        need(W.fix, (size_t)cblocks * KP * sizeof(double), "conversion partials");
         W.u_clean = false;
         if (!host_decided) {
             push_decide_k<<<1, 32, 0, s>>>(a.seeds + k0, kc, g->outdeg.as<int32_t>(), PUSH_MAX_OUTDEG, W.ctl.p);
@@ -587,6 +807,10 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
             init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, a.seeds + k0, kc, c_val, pr_val, r,
                                                          ldr, a.s_iter == 0 ? 1 : 0, W.ctl.p, gate_pull, inv_deg);
             note_launch("init");
+            // x0 at the seeds, zero elsewhere; a gated launch may not run, then x keeps its state
+            const bool was_clean = W.x_zkp == KP || W.x_zkp == -1;
+            W.x_zkp = host_decided || was_clean ? KP : 0;
+            W.x_seeds = W.x_zkp == KP;
         }
         TPA_CHECK_LAUNCH();
     } else if (a.set_ptr) {   // seed sets: zero, then scatter c / |S_j| over each set's members
@@ -595,6 +819,8 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
         scatter_sets_k<<<kc, 256, 0, s>>>(W.x.as<float>(), KP, a.set_ptr + k0, a.seeds, c_val, r, ldr,
                                           a.s_iter == 0 ? 1 : 0, inv_deg);
         note_launch("init", 2);
+        W.x_zkp = 0;   // the members' x0 may sit on rows without in-edges
+        W.x_seeds = false;
         TPA_CHECK_LAUNCH();
     } else {
         init_k<<<grid_1d(n * KP, 256), 256, 0, s>>>(W.x.as<float>(), KP, n, a.seeds ? a.seeds + k0 : nullptr, kc,
@@ -602,6 +828,8 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
                                                      GATE_NONE, inv_deg);
         note_launch("init");
         TPA_CHECK_LAUNCH();
+        W.x_zkp = a.seeds ? KP : 0;   // PageRank's x0 is c/n on every row
+        W.x_seeds = a.seeds != nullptr;
     }
     if (last == 0) {
         if (a.tpa_final) {
@@ -617,16 +845,10 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
         return;
     }
 
-    Params p{};
     p.rp = g->rp_t.as<int64_t>();
     p.col = g->col_t.as<int32_t>();
     p.val = g->val_t.as<float>();
     p.n = n;
-    p.tile_x = P.tile_x.as<int32_t>();
-    p.tile_y = P.tile_y.as<int64_t>();
-    p.head_row = P.head_row.as<int32_t>();
-    p.head_first = P.head_first.as<int32_t>();
-    p.tiles = P.tiles;
     p.r = r;
     p.ldr = ldr;
     p.out = a.out ? a.out + k0 : nullptr;
@@ -636,13 +858,9 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
     p.decay = (float)(1.0 - a.c);
     p.k = kc;
     p.eps = a.eps;
-    p.carry = W.carry.as<float>();
-    p.head = W.head.as<float>();
-    p.tl1 = W.tl1.as<float>();
     p.part = W.fix.as<double>();
     p.ctl = W.ctl.p;
     p.inv_deg = inv_deg;
-    if (var.binned) bind_bins(p, g, 0, KP, s);
 
     // x and y alternate; on a two-way chunk iteration 2 writes and iteration
     // 3 reads the x2 buffer
@@ -674,17 +892,42 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
             p.iter = i;
             p.accumulate = i >= a.s_iter ? 1 : 0;
             p.mode = (a.tpa_final && i == last) ? MODE_FINAL : MODE_ACC;
+            // the segmented walk writes only rows with in-edges: clear the
+            // others in a buffer that held x0 (the seeds' rows, or every row)
+            p.zero_mode = 0;
+            const bool out_x = p.y == W.x.as<float>(), out_y = p.y == W.y.as<float>();
+            if (p.mode == MODE_ACC && (out_x || out_y)) {
+                int &zkp = out_x ? W.x_zkp : W.y_zkp;
+                const bool clean = zkp == KP || zkp == -1;
+                if (var.seg) {
+                    p.zero_mode = !clean ? 2 : (out_x && W.x_seeds) ? 1 : 0;
+                    p.zseeds = a.seeds ? a.seeds + k0 : nullptr;
+                    p.zk = kc;
+                    if (p.zero_mode == 1 && !p.zseeds) p.zero_mode = 2;
+                }
+                if (p.gate == GATE_NONE) {   // a gated launch may not run: the state stays
+                    zkp = KP;
+                    if (out_x) W.x_seeds = false;
+                }
+            }
             ProfMark pm = prof_begin(s);
             p.l1_slots = var.spmm(p, s);
             prof_end(pm, spmm_family(KP), spmm_bytes(n, g->m, KP, kc, p.mode, p.accumulate, p.inv_deg != nullptr), s);
-            ProfMark pf = prof_begin(s);
-            var.fix(p, fix_blocks, s);
-            prof_end(pf, "fixup", 0.0, s);
             note_launch(spmm_family(KP));
-            note_launch("fixup");
+            if (var.fix) {
+                ProfMark pf = prof_begin(s);
+                var.fix(p, fix_blocks, s);
+                prof_end(pf, "fixup", 0.0, s);
+                note_launch("fixup");
+            }
             if (p.mode == MODE_FINAL) {
-                finalize_if_done_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(W.ctl.p, r, ldr, a.r_str, p.one_plus_alpha,
-                                                                        p.out, p.ldo, n, kc);
+                if (var.seg)
+                    finalize_seg_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(W.ctl.p, p.empty_rows, p.n_empty, r, ldr,
+                                                                        a.r_str, p.one_plus_alpha, p.out, p.ldo, n,
+                                                                        kc);
+                else
+                    finalize_if_done_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(W.ctl.p, r, ldr, a.r_str,
+                                                                            p.one_plus_alpha, p.out, p.ldo, n, kc);
                 note_launch("finalize");
             }
             TPA_CHECK_LAUNCH();
@@ -864,27 +1107,14 @@ void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float
     TPA_REQUIRE(kc >= 1 && kc <= 8, "spmv_apply: %d columns (at most 8)", kc);
     const int KP = kp_for(kc);
     const Variant &var = pick_variant(KP);
-    const Plan &P = get_plan(g, var.cfg.L(), s, which);
     Workspace &W = g->ws;
-    W.carry.ensure((size_t)P.tiles * KP * sizeof(float), s);
-    W.head.ensure((size_t)P.tiles * KP * sizeof(float), s);
-    int64_t tl1_rows = P.tiles + 8;   // per tile, or per warp of a grid
-    if (var.binned) tl1_rows = std::max(tl1_rows, binned_slots_bound(get_bin_plan(g, which, s).n_long, KP));
-    W.tl1.ensure((size_t)tl1_rows * KP * sizeof(float), s);
-    const unsigned fix_blocks = fix_grid(KP, P.tiles);
-    W.fix.ensure((size_t)fix_blocks * KP * sizeof(double), s);
-    W.ctl.ensure(CTL_BYTES, s);
-    ctl_init_k<<<1, 256, 0, s>>>(W.ctl.p, kc);
     Params p{};
+    const unsigned fix_blocks = size_for_variant(g, var, which, KP, p, s);
+    ctl_init_k<<<1, 256, 0, s>>>(W.ctl.p, kc);
     p.rp = which ? g->rp_a.as<int64_t>() : g->rp_t.as<int64_t>();
     p.col = which ? g->col_a.as<int32_t>() : g->col_t.as<int32_t>();
     p.val = which ? g->val_a.as<float>() : g->val_t.as<float>();
     p.n = g->n;
-    p.tile_x = P.tile_x.as<int32_t>();
-    p.tile_y = P.tile_y.as<int64_t>();
-    p.head_row = P.head_row.as<int32_t>();
-    p.head_first = P.head_first.as<int32_t>();
-    p.tiles = P.tiles;
     p.x = x;
     p.y = y;
     p.decay = decay;
@@ -893,19 +1123,18 @@ void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float
     p.accumulate = 0;
     p.iter = 1;
     p.eps = 0.0;   // no break test: every column stays alive
-    p.carry = W.carry.as<float>();
-    p.head = W.head.as<float>();
-    p.tl1 = W.tl1.as<float>();
     p.part = W.fix.as<double>();
     p.ctl = W.ctl.p;
-    if (var.binned) bind_bins(p, g, which, KP, s);
+    p.zero_mode = var.seg ? 2 : 0;   // y is the caller's: its rows without nonzeros are cleared
     ProfMark pm = prof_begin(s);
     p.l1_slots = var.spmm(p, s);
     prof_end(pm, spmm_family(KP), spmm_bytes(g->n, g->m, KP, kc, MODE_ACC, 0, false), s);
-    var.fix(p, fix_blocks, s);
     note_launch("init");
     note_launch(spmm_family(KP));
-    note_launch("fixup");
+    if (var.fix) {
+        var.fix(p, fix_blocks, s);
+        note_launch("fixup");
+    }
     TPA_CHECK_LAUNCH();
 }
 
@@ -964,6 +1193,11 @@ void run_cpi(tpa_graph *g, const CpiArgs &a0, cudaStream_t s)
     const int chunk = a0.tpa_final ? (g_chunk_query ? g_chunk_query : DEFAULT_CHUNK_QUERY)
                                    : (g_chunk_cpi ? g_chunk_cpi : DEFAULT_CHUNK_CPI);
     CpiArgs a = a0;
+    // what x holds is not known across calls (graph replays run the sequence
+    // captured here on whatever a previous call left)
+    g->ws.x_zkp = 0;
+    g->ws.y_zkp = 0;
+    g->ws.x_seeds = false;
     // A query whose chunk branches the host picks (it has the seeds' out-degrees)
     // and whose output is in device memory swaps the seeds too heavy for the
     // push branch into its last chunks, runs every chunk in place, and swaps

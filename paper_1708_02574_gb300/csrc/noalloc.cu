@@ -56,6 +56,12 @@ extern "C" tpa_status tpa_cpi_step_noalloc(int64_t n, int64_t m, const int64_t *
                                            double *l1, void *stream)
 {
     clear_error();
+    // the walk gathers x while other tiles store y and add into r: an output
+    // that is also an input would be read half-updated
+    if ((x && (x == y || x == r)) || (y && y == r)) {
+        set_error("tpa_cpi_step_noalloc: x, y and r must be distinct arrays (in-place steps are not supported)");
+        return TPA_EINVAL;
+    }
     if (n < 1 || n >= ((int64_t)1 << 31) || m < 0 || m >= ((int64_t)1 << 31)) {
         set_error("tpa_cpi_step_noalloc: n = %lld or m = %lld out of range", (long long)n, (long long)m);
         return TPA_EINVAL;

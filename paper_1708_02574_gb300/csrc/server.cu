@@ -89,7 +89,7 @@ std::vector<uint64_t> identity(const tpa_graph *g)
     };
     const Workspace &w = g->ws;
     for (const DevBuf *b : {&w.x, &w.y, &w.r, &w.carry, &w.head, &w.tl1, &w.fix, &w.ctl, &w.seeds, &w.sets,
-                            &w.seeds_g, &w.cols, &w.out, &w.iters, &w.u, &w.touched, &w.x2, &w.cpart})
+                            &w.seeds_g, &w.cols, &w.out, &w.iters, &w.u, &w.touched, &w.x2, &w.cpart, &w.agg})
         addr(*b);
     v.push_back((uint64_t)(uintptr_t)w.hflag);
     for (const DevBuf *b : {&g->rp_t, &g->col_t, &g->val_t, &g->rp_a, &g->col_a, &g->val_a, &g->outdeg, &g->inv_deg32,
@@ -101,6 +101,13 @@ std::vector<uint64_t> identity(const tpa_graph *g)
             v.push_back((uint64_t)kv.first);
             for (const DevBuf *b : {&kv.second.tile_x, &kv.second.tile_y, &kv.second.head_row, &kv.second.head_first})
                 addr(*b);
+        }
+    for (const SegRows *R : {&g->seg_t, &g->seg_a})
+        for (const DevBuf *b : {&R->colf, &R->nz_rows, &R->empty_rows, &R->nzpos}) addr(*b);
+    for (const auto *tiles : {&g->segt_t, &g->segt_a})
+        for (const auto &kv : *tiles) {
+            v.push_back((uint64_t)kv.first);
+            addr(kv.second.crow0);
         }
     for (const BinPlan *B : {&g->bins_t, &g->bins_a})
         for (const DevBuf *b : {&B->rows_short, &B->rows_mid, &B->rows_long, &B->rows_empty, &B->long_first,
@@ -291,6 +298,27 @@ tpa_status tpa_server_result(const tpa_server *srv, float **out, int64_t *ldo)
     SRV_END
 }
 
+tpa_status tpa_server_sync(tpa_server *srv, void *stream)
+{
+    SRV_BEGIN
+    TPA_REQUIRE(srv != nullptr, "tpa_server_sync: NULL server");
+    cudaStream_t s = (cudaStream_t)stream;
+    TPA_CUDA(cudaStreamSynchronize(s));
+    if (srv->ws.ctl.p) {
+        int32_t *flag = &static_cast<Ctl *>(srv->ws.ctl.p)->error;
+        int32_t e = 0;
+        TPA_CUDA(cudaMemcpyAsync(&e, flag, sizeof e, cudaMemcpyDeviceToHost, s));
+        TPA_CUDA(cudaStreamSynchronize(s));
+        if (e) {
+            TPA_CUDA(cudaMemsetAsync(flag, 0, sizeof e, s));
+            TPA_CUDA(cudaStreamSynchronize(s));
+            set_error("a bounded device wait gave up: the batches since the last check are not valid");
+            throw Fail{TPA_ETIMEOUT};
+        }
+    }
+    SRV_END
+}
+
 tpa_status tpa_server_stats(const tpa_server *srv, int k, int64_t *graphs, int64_t *replays,
                             int64_t *launches_per_replay, int64_t *captures)
 {
@@ -315,7 +343,7 @@ void tpa_server_free(tpa_server *srv)
     DevBuf *bufs[] = {&srv->out_buf, &srv->seeds, &srv->ws.x, &srv->ws.y, &srv->ws.r, &srv->ws.carry,
                       &srv->ws.head, &srv->ws.tl1, &srv->ws.fix, &srv->ws.ctl, &srv->ws.seeds, &srv->ws.sets,
                       &srv->ws.seeds_g, &srv->ws.cols, &srv->ws.out,
-                      &srv->ws.iters, &srv->ws.u, &srv->ws.touched, &srv->ws.x2, &srv->ws.cpart};
+                      &srv->ws.iters, &srv->ws.u, &srv->ws.touched, &srv->ws.x2, &srv->ws.cpart, &srv->ws.agg};
     for (DevBuf *b : bufs) b->release(s);
     if (srv->ws.hflag) cudaFreeHost(srv->ws.hflag);
     if (srv->h_seeds) cudaFreeHost(srv->h_seeds);

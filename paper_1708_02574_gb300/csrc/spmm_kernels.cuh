@@ -97,6 +97,23 @@ struct Params {
     // and the accumulate epilogue stores y_v * inv_deg[v] as the next x.
     // r, the L1 norms and the outputs keep the unscaled iterate.
     const float *inv_deg;
+    // Segmented flag walk (spmm_seg.cuh): the columns of the CSR with bit 31
+    // set on the first nonzero of every row, the nonempty rows in order, the
+    // number of row starts before each tile of seg_tn nonzeros, and one
+    // tagged carry-out word per tile and column.
+    const uint32_t *colf;
+    const int32_t *nz_rows;
+    const int32_t *tile_crow0;
+    const int32_t *empty_rows;   // n_empty of them (the field the binned kernels use too)
+    int64_t m;
+    int64_t seg_tiles;
+    unsigned long long *agg;
+    // rows of y to clear before the walk (the walk writes nonempty rows only):
+    // 0 none, 1 those of the zk seeds zseeds[] that have no in-edge, 2 every
+    // empty row
+    int zero_mode;
+    int zk;
+    const int32_t *zseeds;
 };
 
 enum Gate : int { GATE_NONE = 0, GATE_PULL = 1, GATE_PUSH = 2 };

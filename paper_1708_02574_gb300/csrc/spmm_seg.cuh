@@ -1,0 +1,526 @@
+// Segmented flag walk: the SpMV/SpMM of one CPI iteration (Algorithm 1,
+// x_i = (1-c) A~^T x_{i-1}) with its epilogue, L1 norm and break test in a
+// single launch.  Included once, by cpi.cu, after spmm_kernels.cuh.
+//
+// The nonzeros of CSR(A~^T) are cut into tiles of TN = 32 * R consecutive
+// nonzeros, one warp per tile in a static strided order (tile t on warp
+// t mod W, so the warps in flight work on one band of rows and their gathers
+// share L2).  Lane l of a tile owns nonzeros [t*TN + R*l, t*TN + R*l + R):
+//   1. its R column ids come in two or four 16-byte streaming loads of a copy
+//      of the column array whose bit 31 marks the first nonzero of a row, so
+//      no row pointer is read and nothing is staged in shared memory;
+//   2. it gathers the R rows X[col][0..V) (V = padded batch width, one lane
+//      holds a whole row: one 32-byte load at V = 8) and walks them in order,
+//      closing a row sum at every row start;
+//   3. a shuffle segmented scan over the lanes adds the partials of rows that
+//      span lanes; rows that start and end in the tile are parked in shared
+//      memory and finished by one coalesced pass (lane per row: y stored,
+//      r += y by a vector atomic, or the TPA finalize in the last family
+//      iteration);
+//   4. a row that spans tiles is finished by the tile where it ends: each tile
+//      publishes its carry-out (the sum after its last row start, or of the
+//      whole tile when no row starts in it) as 64-bit words that pair the
+//      value with a launch tag, so a reader needs no fence: it waits (bounded)
+//      until the word carries this launch's tag, then adds the carry-outs of
+//      the tiles before it, nearest first, back to the tile where the row
+//      started.  The fixed order keeps results identical run to run.
+// The per-warp L1 partials are reduced by the last CTA to finish (one fence
+// and one ticket per CTA), which applies the break test ||x_i||_1 < eps.
+// Rows without nonzeros are never visited: their y stays zero (the rows a
+// launch must clear are listed in Params::zero_mode), and the TPA finalize
+// of those rows runs in finalize_seg_k.
+//
+// The waits assume every CTA of the grid is resident at once: the grid is at
+// most the occupancy of the kernel times the SM count.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tpa {
+
+constexpr int SEG_WARPS = 8;                 // 256 threads: block_sum_partials runs on them
+constexpr uint32_t SEG_ROW_START = 0x80000000u;
+constexpr long long SEG_SPIN_LIMIT = 1ll << 22;   // polls of one carry-out word (about a second)
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long seg_pack(float v, uint32_t tag)
+{
+    return ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v);
+}
+
+// Streaming 16-byte load of four column words (read once per launch).
+__device__ __forceinline__ uint4 ld_cols4(const uint32_t *p)
+{
+    uint4 r;
+    asm volatile("ld.global.cs.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ float4 ld_vals4(const float *p)
+{
+    float4 r;
+    asm volatile("ld.global.cs.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+// Wait (bounded) for the carry-out word w of the current launch (tag `want`
+// in bits 33.., row-start flag in bit 32); returns the word, or a zero value
+// with the error flag raised when the wait gives up.  Once any wait of the
+// launch has given up, every other wait returns at once, so a launch ends
+// within about one wait limit whatever happens.
+__device__ __forceinline__ unsigned long long seg_wait(const unsigned long long *w, uint32_t want, Ctl *hdr)
+{
+    unsigned long long v = ld_relaxed_u64(w);
+    long long spins = 0;
+    unsigned ns = 32;
+    while ((uint32_t)(v >> 33) != want) {
+        if (++spins > SEG_SPIN_LIMIT || *(volatile int32_t *)&hdr->error) {
+            atomicOr(&hdr->error, 1);
+            return 0ull;
+        }
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        v = ld_relaxed_u64(w);
+    }
+    return v;
+}
+
+// Sum of the carry-outs of tiles t-1, t-2, ... back to and including the
+// nearest one in which a row starts (all of them down to tile 0 if none),
+// nearest first.  Warp-cooperative: tile t-1 first (lane j reads its word j),
+// which ends the search in the common case of a row that started one tile
+// back; then 32 tiles per round (lane l reads tile base - l), lanes past the
+// first tile with a row start contributing zero, lanes added in a fixed
+// shuffle tree.  Every lane returns the same sums.
+template <int V>
+__device__ __forceinline__ void seg_lookback(const Params &p, int64_t t, uint32_t want, Ctl *hdr, int lane,
+                                             float (&sum)[V])
+{
+    const unsigned FULL = 0xffffffffu;
+    float v1 = 0.0f;
+    int st1 = 0;
+    if (lane < V) {
+        const unsigned long long w = seg_wait(p.agg + (t - 1) * V + lane, want, hdr);
+        v1 = __uint_as_float((uint32_t)w);
+        st1 = (int)((w >> 32) & 1ull);
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) sum[j] = __shfl_sync(FULL, v1, j);
+    if (__shfl_sync(FULL, st1, 0)) return;
+    for (int64_t base = t - 2; base >= 0; base -= 32) {
+        const int64_t u = base - lane;
+        float v[V];
+        bool start = false;
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[j] = 0.0f;
+        if (u >= 0) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const unsigned long long w = seg_wait(p.agg + u * V + j, want, hdr);
+                v[j] = __uint_as_float((uint32_t)w);
+                start = (w >> 32) & 1ull;
+            }
+        }
+        const unsigned starts = __ballot_sync(FULL, start);
+        const int stop = starts ? __ffs(starts) - 1 : 31;   // last lane that contributes
+        if (lane > stop) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) v[j] = 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            float a = v[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(FULL, a, o);
+            sum[j] += a;
+        }
+        if (starts) break;
+    }
+}
+
+// Epilogue of one finished row for the segmented kernel (lane holds the row).
+template <int V, bool PAT>
+__device__ __forceinline__ void seg_emit(const Params &p, int64_t v, const float (&sv)[V], const int (&alive)[V],
+                                         float (&l1)[V])
+{
+    if (p.mode == MODE_ACC)
+        epilogue_red<V, V, PAT ? PM_PATTERN : PM_VALUED>(p, v, 0, sv, alive, l1, PAT ? __ldg(p.inv_deg + v) : 0.0f);
+    else
+        epilogue<V, V, PAT ? PM_PATTERN : PM_VALUED>(p, v, 0, sv, alive, l1);
+}
+
+// Finish row `row`, whose part in tile t is `part`, with the carry-outs of
+// the tiles before t (warp-cooperative; lane 0 runs the epilogue).
+template <int V, bool PAT>
+__device__ __forceinline__ void seg_finish(const Params &p, int64_t t, int32_t row, const float (&part)[V],
+                                           uint32_t want, Ctl *hdr, int lane, const int (&alive)[V], float (&l1)[V])
+{
+    float back[V];
+    seg_lookback<V>(p, t, want, hdr, lane, back);
+    if (lane == 0) {
+        float tot[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) tot[j] = part[j] + back[j];
+        seg_emit<V, PAT>(p, (int64_t)row, tot, alive, l1);
+    }
+}
+
+// Dynamic shared memory of the segmented kernel: per warp, the sums of the
+// rows that start and end in its tile (at most TN - 1 of V floats).
+template <int V, int R>
+constexpr size_t seg_smem_bytes()
+{
+    return (size_t)SEG_WARPS * 32 * R * V * sizeof(float);
+}
+
+template <int V, int R, int PF, bool PAT>
+__global__ void __launch_bounds__(SEG_WARPS * 32) spmm_seg_k(Params p)
+{
+    static_assert(R % 4 == 0 && R % PF == 0 && R <= 32, "R");
+    static_assert(V == 1 || V == 2 || V == 4 || V == 8, "V");
+    constexpr int TN = 32 * R;
+    extern __shared__ __align__(16) float seg_smem[];
+    __shared__ double s_fin[256];
+    __shared__ float s_l1[SEG_WARPS][V];
+    __shared__ int s_last;
+    const CtlView cv = ctl_view(p.ctl);
+    if (gate_off(p.gate, p.ctl) || *(volatile int32_t *)&cv.hdr->done) return;
+    const uint32_t ep_raw = *(volatile uint32_t *)&cv.hdr->epoch;
+    const uint32_t ep = (ep_raw + 1u) & 0x7fffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *rs = seg_smem + (size_t)warp * TN * V;
+    const unsigned FULL = 0xffffffffu;
+
+    // rows of y that the walk never writes but that must read as zero
+    if (p.zero_mode == 1) {
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p.zk; j += gridDim.x * blockDim.x) {
+            const int64_t s = p.zseeds[j];
+            if (p.rp[s + 1] == p.rp[s]) {
+                float z[V];
+#pragma unroll
+                for (int q = 0; q < V; ++q) z[q] = 0.0f;
+                st_row<V>(p.y + s * V, z);
+            }
+        }
+    } else if (p.zero_mode == 2) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n_empty;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            float z[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) z[q] = 0.0f;
+            st_row<V>(p.y + (int64_t)p.empty_rows[i] * V, z);
+        }
+    }
+
+    int alive[V];
+    float l1[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        alive[j] = cv.alive[j];
+        l1[j] = 0.0f;
+    }
+    // the row a tile finishes through the carry-outs of earlier tiles, held
+    // until the warp's next tile is done
+    bool pend = false;
+    int64_t pend_t = 0;
+    int32_t pend_row = 0;
+    float pend_part[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) pend_part[j] = 0.0f;
+    const int64_t nw = (int64_t)gridDim.x * SEG_WARPS;
+    for (int64_t t = (int64_t)blockIdx.x * SEG_WARPS + warp; t < p.seg_tiles; t += nw) {
+        const int64_t e0 = t * TN + (int64_t)lane * R;
+        // 1. column words (the copy is padded to whole tiles) and row starts
+        uint32_t cw[R];
+#pragma unroll
+        for (int q = 0; q < R / 4; ++q) {
+            const uint4 c = ld_cols4(p.colf + e0 + 4 * q);
+            cw[4 * q] = c.x;
+            cw[4 * q + 1] = c.y;
+            cw[4 * q + 2] = c.z;
+            cw[4 * q + 3] = c.w;
+        }
+        float vv[PAT ? 1 : R];
+        if constexpr (!PAT) {
+            if (e0 + R <= p.m) {
+#pragma unroll
+                for (int q = 0; q < R / 4; ++q) {
+                    const float4 v4 = ld_vals4(p.val + e0 + 4 * q);
+                    vv[4 * q] = v4.x;
+                    vv[4 * q + 1] = v4.y;
+                    vv[4 * q + 2] = v4.z;
+                    vv[4 * q + 3] = v4.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) vv[i] = e0 + i < p.m ? __ldg(p.val + e0 + i) : 0.0f;
+            }
+        }
+        const int64_t left = p.m - e0;
+        const unsigned vm = left >= R ? (R == 32 ? FULL : (1u << R) - 1u) : left > 0 ? (1u << left) - 1u : 0u;
+        unsigned fm = 0;
+#pragma unroll
+        for (int i = 0; i < R; ++i) fm |= (cw[i] >> 31) << i;
+        fm &= vm;
+        const int nf = __popc(fm);
+        int incl = nf;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - nf;
+        const int q = __shfl_sync(FULL, incl, 31);
+
+        // 2. gathers and the walk: a row sum closes at every row start
+        float acc[V], head[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            acc[j] = 0.0f;
+            head[j] = 0.0f;
+        }
+        int seen = 0;
+#pragma unroll
+        for (int c0 = 0; c0 < R; c0 += PF) {
+            float xv[PF][V];
+#pragma unroll
+            for (int it = 0; it < PF; ++it) {
+                const int i = c0 + it;
+                if ((vm >> i) & 1u) {
+                    ld_row<V>(p.x + (int64_t)(cw[i] & ~SEG_ROW_START) * V, xv[it]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) xv[it][j] = 0.0f;
+                }
+            }
+#pragma unroll
+            for (int it = 0; it < PF; ++it) {
+                const int i = c0 + it;
+                if ((fm >> i) & 1u) {
+                    if (seen == 0) {
+#pragma unroll
+                        for (int j = 0; j < V; ++j) head[j] = acc[j];
+                    } else {
+                        st_row<V>(rs + (excl + seen - 1) * V, acc);
+                    }
+#pragma unroll
+                    for (int j = 0; j < V; ++j) acc[j] = 0.0f;
+                    ++seen;
+                }
+                if constexpr (PAT) {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) acc[j] += xv[it][j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) acc[j] = fmaf(vv[i], xv[it][j], acc[j]);
+                }
+            }
+        }
+
+        // 3. segmented scan of the lanes' trailing sums, restarting at lanes in
+        //    which a row starts; inc of lane l is the sum from the last row start
+        //    at or before lane l through the end of lane l
+        float inc[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) inc[j] = acc[j];
+        int key = nf > 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            float up[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) up[j] = __shfl_up_sync(FULL, inc[j], o);
+            const int kup = __shfl_up_sync(FULL, key, o);
+            if (lane >= o) {
+                if (!key) {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) inc[j] += up[j];
+                }
+                key |= kup;
+            }
+        }
+        // the row that ends just before this lane's first row start
+        float first_tot[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const float cin = __shfl_up_sync(FULL, inc[j], 1);
+            first_tot[j] = (lane > 0 ? cin : 0.0f) + head[j];
+        }
+        if (nf > 0 && excl > 0) st_row<V>(rs + (excl - 1) * V, first_tot);
+        // carry-out of the tile, tagged with this launch and whether a row starts in it
+        if (lane == 31) {
+            const uint32_t tag = (ep << 1) | (q > 0 ? 1u : 0u);
+#pragma unroll
+            for (int j = 0; j < V; ++j) st_relaxed_u64(p.agg + t * V + j, seg_pack(inc[j], tag));
+        }
+        __syncwarp();
+
+        // 4. rows that start and end in the tile: lane per row, coalesced
+        const int64_t crow0 = p.tile_crow0[t];
+        for (int k = lane; k < q - 1; k += 32) {
+            const int64_t v = p.nz_rows[crow0 + k];
+            float sv[V];
+            ld_row_smem<V>(rs + k * V, sv);
+            seg_emit<V, PAT>(p, v, sv, alive, l1);
+        }
+
+        // 5. the row that ends in this tile after starting in an earlier one (or
+        //    runs to the end of the matrix from an earlier tile) needs the
+        //    carry-outs of the tiles before; it is finished one tile of this
+        //    warp later, when those were published long ago
+        if (pend) {
+            seg_finish<V, PAT>(p, pend_t, pend_row, pend_part, ep, cv.hdr, lane, alive, l1);
+            pend = false;
+        }
+        const bool last = t == p.seg_tiles - 1;
+        if ((q > 0 && t > 0) || (q == 0 && last)) {
+            if (q > 0) {
+                const int f0 = __ffs(__ballot_sync(FULL, nf > 0)) - 1;
+#pragma unroll
+                for (int j = 0; j < V; ++j) pend_part[j] = __shfl_sync(FULL, first_tot[j], f0);
+            } else {
+#pragma unroll
+                for (int j = 0; j < V; ++j) pend_part[j] = __shfl_sync(FULL, inc[j], 31);
+            }
+            pend = true;
+            pend_t = t;
+            pend_row = p.nz_rows[crow0 - 1];
+        }
+        // 6. the last row that starts in the last tile ends with the matrix
+        if (last && q > 0 && lane == 31) seg_emit<V, PAT>(p, (int64_t)p.nz_rows[crow0 + q - 1], inc, alive, l1);
+        __syncwarp();   // rs is rewritten by the next tile
+    }
+    if (pend) seg_finish<V, PAT>(p, pend_t, pend_row, pend_part, ep, cv.hdr, lane, alive, l1);
+
+    // L1 partial of the CTA; the last CTA to finish sums the partials in a fixed
+    // order and applies the break test of Algorithm 1 per column
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        float a = l1[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(FULL, a, o);
+        if (lane == 0) s_l1[warp][j] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < V) {
+        float a = 0.0f;
+#pragma unroll
+        for (int w = 0; w < SEG_WARPS; ++w) a += s_l1[w][threadIdx.x];
+        p.part[(int64_t)blockIdx.x * V + threadIdx.x] = (double)a;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&cv.hdr->ticket, 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    block_sum_partials<V>(p.part, gridDim.x, s_fin);
+    if (threadIdx.x < V) {
+        const int c = threadIdx.x;
+        const double a = s_fin[c];
+        if (c < p.k && cv.alive[c]) {
+            cv.norm[c] = a;
+            cv.iters[c] = p.iter;
+            if (a < p.eps && p.mode == MODE_ACC) cv.alive[c] = 0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int c = 0; c < p.k && c < V; ++c) any |= cv.alive[c];
+        cv.hdr->done = any ? 0 : 1;
+        cv.hdr->ticket = 0;
+        cv.hdr->epoch = ep_raw + 1u;
+    }
+}
+
+// The TPA finalize r_TPA = (1+alpha) r_family + r~_stranger for the rows the
+// segmented kernel does not visit: the rows without nonzeros, or every row
+// when all columns stopped before the last family iteration (that launch
+// then returned at once).
+__global__ void finalize_seg_k(const void *ctl, const int32_t *empty_rows, int64_t n_empty, const float *r,
+                               int64_t ldr, const float *r_str, float opa, float *out, int64_t ldo, int64_t n, int k)
+{
+    const CtlView cv = ctl_view(const_cast<void *>(ctl));
+    const bool all = *(volatile int32_t *)&cv.hdr->done != 0;
+    const int64_t rows = all ? n : n_empty;
+    const int64_t total = rows * k;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t rr = i / k;
+        const int j = (int)(i % k);
+        const int64_t v = all ? rr : (int64_t)empty_rows[rr];
+        out[v * ldo + j] = fmaf(opa, r[v * ldr + j], r_str[v]);
+    }
+}
+
+// ---------------------------------------------------- plan of the walk ---
+// nzf[v] = 1 when row v has a nonzero, ef[v] = 1 when it has none.
+__global__ void seg_row_flags_k(const int64_t *rp, int64_t n, int32_t *nzf, int32_t *ef)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int nz = rp[v + 1] > rp[v] ? 1 : 0;
+        nzf[v] = nz;
+        ef[v] = 1 - nz;
+    }
+}
+
+__global__ void seg_scatter_rows_k(const int64_t *rp, int64_t n, const int64_t *nzpos, const int64_t *epos,
+                                   int32_t *nz_rows, int32_t *empty_rows)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (rp[v + 1] > rp[v]) nz_rows[nzpos[v]] = (int32_t)v;
+        else empty_rows[epos[v]] = (int32_t)v;
+    }
+}
+
+// colf[e] = col[e] for e < m, 0 in the padding up to total.
+__global__ void seg_copy_cols_k(const int32_t *col, int64_t m, int64_t total, uint32_t *colf)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        colf[e] = e < m ? (uint32_t)col[e] : 0u;
+}
+
+// Mark the first nonzero of every nonempty row.
+__global__ void seg_mark_k(const int64_t *rp, int64_t n, uint32_t *colf)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        if (rp[v + 1] > rp[v]) colf[rp[v]] |= SEG_ROW_START;
+}
+
+// crow0[t] = number of nonempty rows whose first nonzero precedes t * tn,
+// for t = 0 .. tiles (nzpos: exclusive prefix of the nonempty-row flags and
+// their total at n).
+__global__ void seg_tiles_k(const int64_t *rp, int64_t n, int64_t m, const int64_t *nzpos, int64_t tn, int64_t tiles,
+                            int32_t *crow0)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= tiles; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t X = t * tn;
+        if (X >= m) {
+            crow0[t] = (int32_t)nzpos[n];
+            continue;
+        }
+        int64_t lo = 0, hi = n;   // first v with rp[v] >= X (rp[n] = m > X)
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (rp[mid] >= X) hi = mid; else lo = mid + 1;
+        }
+        crow0[t] = (int32_t)nzpos[lo];
+    }
+}
+
+}  // namespace tpa

@@ -136,9 +136,13 @@ struct Workspace {
     DevBuf cpart;           // binned-row kernels: chunk sums of long rows [chunks][KP]
     DevBuf agg;             // segmented kernel: tagged carry-out words [tiles][KP] (zeroed when allocated)
     bool u_clean = false;   // u, touched and x2 are known to be all zero
-    // rows of x without in-edges may hold nonzeros (x0 written there): 0 no,
-    // 1 only the current chunk's seeds, 2 any of them
-    int x_dirty = 2;
+    // The segmented walk never writes the rows of y without in-edges, so they
+    // must already read as zero.  x_zkp / y_zkp: the padded width KP for
+    // whose layout [n][KP] the rows without in-edges of x / y are known to be
+    // zero (-1: the whole buffer is zero; 0: not known).  x_seeds: those rows
+    // of x are zero except the current chunk's seeds, which hold x0.
+    int x_zkp = 0, y_zkp = 0;
+    bool x_seeds = false;
     int32_t *hflag = nullptr;   // pinned host mirror of the done flag (2 slots)
 };
 
@@ -240,6 +244,9 @@ void weights_from_features(const float *feat, const float *theta, int d, int64_t
 void theta_grad(const float *feat, const float *w, const float *gw, int d, int64_t m, double *out, cudaStream_t s);
 double loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const int32_t *neg, int ntrip, double c,
                  int S, int T, int K, float *grad_w, cudaStream_t s);
+// Bytes of stranger-chain iterates the reverse sweep keeps before it switches
+// to checkpoints every ceil(sqrt(K+1)) iterations (tpa_set_adjoint_budget).
+extern size_t g_adjoint_budget;
 
 
 // Out-degrees of k device-resident seeds, copied to the host (one small copy and a wait).

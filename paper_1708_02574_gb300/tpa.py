@@ -53,6 +53,9 @@ def library():
         "tpa_edge_weights": (i32, [P, P, i32, i64, P, P]),
         "tpa_loss_grad": (i32, [P, P, P, P, i32, f64, i32, i32, i32, ctypes.POINTER(f64), P, P]),
         "tpa_theta_grad": (i32, [P, P, P, i32, i64, P, P]),
+        "tpa_sync": (i32, [P, P]),
+        "tpa_set_adjoint_budget": (i32, [ctypes.c_uint64]),
+        "tpa_server_sync": (i32, [P, P]),
         "tpa_server_create": (i32, [P, i32, i32, P, i64, P, ctypes.POINTER(P)]),
         "tpa_server_query": (i32, [P, P, i32, P]),
         "tpa_server_result": (i32, [P, ctypes.POINTER(P), ctypes.POINTER(i64)]),
@@ -240,6 +243,10 @@ class Server:
         _check(library().tpa_server_query(self._h, _ptr(s), int(k), _stream()))
         return self.out[:, :k]
 
+    def sync(self) -> None:
+        """tpa_server_sync: wait for the server's work, failing if a bounded device wait gave up."""
+        _check(library().tpa_server_sync(self._h, _stream()))
+
     def stats(self, k: int = 0) -> dict:
         gr, rp, lp, cp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(library().tpa_server_stats(self._h, int(k), ctypes.byref(gr), ctypes.byref(rp), ctypes.byref(lp),
@@ -397,16 +404,28 @@ def edge_weights(feat, theta):
     return w
 
 
-def loss_grad(g: Graph, seeds, pos, neg, c: float = 0.15, S: int = 5, T: int = 10, K: int = 100):
-    """tpa_loss_grad: (loss, dL/dw as a CUDA float32 tensor in CSR(A~) order)."""
+def loss_grad(g: Graph, seeds, pos, neg, c: float = 0.15, S: int = 5, T: int = 10, K: int = 100,
+              want_grad: bool = True):
+    """tpa_loss_grad: (loss, dL/dw as a CUDA float32 tensor in CSR(A~) order); with
+    want_grad=False the loss alone (no reverse sweep) and None."""
     torch = _torch()
     s, p, q = _as_i32(seeds), _as_i32(pos), _as_i32(neg)
     n, m = graph_info(g)
-    gw = torch.empty(max(m, 1), dtype=torch.float32, device="cuda")
+    gw = torch.empty(max(m, 1), dtype=torch.float32, device="cuda") if want_grad else None
     loss = ctypes.c_double()
     _check(library().tpa_loss_grad(g.handle, _ptr(s), _ptr(p), _ptr(q), int(len(s)), float(c), int(S), int(T),
                                    int(K), ctypes.byref(loss), _ptr(gw), _stream()))
-    return loss.value, gw[:m]
+    return loss.value, (gw[:m] if want_grad else None)
+
+
+def set_adjoint_budget(nbytes: int) -> None:
+    """tpa_set_adjoint_budget: iterate bytes kept before checkpointing."""
+    _check(library().tpa_set_adjoint_budget(int(nbytes)))
+
+
+def sync(g: Graph) -> None:
+    """tpa_sync: wait for the graph's work; TpaError(TPA_ETIMEOUT) if a bounded device wait gave up."""
+    _check(library().tpa_sync(g.handle, _stream()))
 
 
 def theta_grad(feat, w, grad_w):

@@ -178,3 +178,84 @@ def test_scale20_loss_grad_is_a_sum_over_triples(scale20):
         gsum += gq.double()
     assert np.isfinite(loss) and abs(loss - parts) <= 1e-6 * abs(parts)
     assert rel(gw.cpu().numpy(), gsum.cpu().numpy()) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# The stranger chain run for the count of the forward pass (the preprocessing
+# break at eps = 1e-9, about 90-110 iterations), as TPALinkLoss(K=None) and
+# the differentiation workload use it; iterate checkpointing; the loss alone.
+
+def forward_K(t, g):
+    t.preprocess(g, C, T, 1e-9)
+    return max(int(t.get_stranger(g)[1]), T)
+
+
+def test_loss_grad_at_forward_count(problem):
+    t = tpa()
+    og, g = problem["og"], problem["g"]
+    w = t.edge_weights(problem["feat_d"], problem["theta_d"])
+    t.set_edge_weights(g, w)
+    K = forward_K(t, g)
+    assert K > 60, K
+    sl = slice(0, 48)
+    loss, gw = t.loss_grad(g, problem["seeds"][sl], problem["pos"][sl], problem["neg"][sl], C, S, T, K)
+    wd = oracle.edge_weights(problem["theta"], problem["feat"])
+    rloss, rgw, _, _ = oracle.loss_grad(og, wd, problem["seeds"][sl], problem["pos"][sl], problem["neg"][sl],
+                                        C, S, T, K)
+    assert abs(loss - rloss) <= 1e-5 * abs(rloss)
+    assert rel(gw.cpu().numpy(), rgw) < 1e-3, rel(gw.cpu().numpy(), rgw)
+    gth = t.theta_grad(problem["feat_d"], w, gw).cpu().numpy()
+    assert rel(gth, oracle.theta_grad(problem["feat"], wd, rgw)) < 1e-3
+
+
+def test_checkpointed_iterates_are_bit_identical(problem):
+    """With a budget too small for the K+1 iterates, the reverse sweep keeps
+    every ceil(sqrt(K+1))-th one and recomputes the rest: same bits."""
+    import torch
+    t = tpa()
+    g = problem["g"]
+    w = t.edge_weights(problem["feat_d"], problem["theta_d"])
+    t.set_edge_weights(g, w)
+    K = forward_K(t, g)
+    args = (problem["seeds"][:16], problem["pos"][:16], problem["neg"][:16], C, S, T, K)
+    loss_a, gw_a = t.loss_grad(g, *args)
+    try:
+        t.set_adjoint_budget(1)
+        loss_b, gw_b = t.loss_grad(g, *args)
+    finally:
+        t.set_adjoint_budget(16 << 30)
+    assert loss_a == loss_b
+    assert torch.equal(gw_a, gw_b)
+
+
+def test_loss_alone_and_autograd_without_grad(problem):
+    import torch
+    t = tpa()
+    g = problem["g"]
+    w = t.edge_weights(problem["feat_d"], problem["theta_d"])
+    t.set_edge_weights(g, w)
+    K = 30
+    args = (problem["seeds"], problem["pos"], problem["neg"], C, S, T, K)
+    loss, _ = t.loss_grad(g, *args)
+    loss_only, none = t.loss_grad(g, *args, want_grad=False)
+    assert none is None and loss_only == loss
+    theta = problem["theta_d"].clone()          # no gradient wanted: no reverse sweep
+    with torch.no_grad():
+        l2 = t.TPALinkLoss.apply(theta, problem["feat_d"], g, problem["seeds"], problem["pos"], problem["neg"],
+                                 C, S, T, K)
+    assert l2.item() == loss
+
+
+def test_scale20_loss_grad_at_forward_count(scale20):
+    """The differentiation workload's own K (the preprocessing count on the
+    weighted R-MAT scale-20 graph), 32 triples against the FP64 oracle."""
+    t = tpa()
+    g = scale20["g"]
+    K = forward_K(t, g)
+    sl = slice(0, 32)
+    loss, gw = t.loss_grad(g, scale20["seeds"][sl], scale20["pos"][sl], scale20["neg"][sl], C, S, T, K)
+    wd = oracle.edge_weights(scale20["theta"], scale20["feat"])
+    rloss, rgw, _, _ = oracle.loss_grad(scale20["og"], wd, scale20["seeds"][sl], scale20["pos"][sl],
+                                        scale20["neg"][sl], C, S, T, K)
+    assert abs(loss - rloss) <= 1e-5 * abs(rloss)
+    assert rel(gw.cpu().numpy(), rgw) < 1e-3, rel(gw.cpu().numpy(), rgw)

@@ -57,6 +57,43 @@ def test_two_steps_match_cpi():
         assert abs(norms[1] - ref2.astype(np.float64).sum()) <= 1e-6 * max(1.0, norms[1])
 
 
+def test_two_steps_match_the_oracle():
+    """x1 = (1-c) A~^T x0 and x2 from two calls in a row, and r = x1 + x2,
+    against the FP64 oracle's Algorithm 1 with s_iter = t_iter = 1, = 2 and
+    s_iter = 1, t_iter = 2 (R-MAT scale 14 and a scale-16 graph that spans
+    more merge-path tiles)."""
+    import torch
+    import oracle
+    import paper_1708_02574_gb300 as tpa
+
+    for scale in (14, 16):
+        n = 1 << scale
+        s, d = synth.rmat_edges(scale, 16)
+        g = tpa.build_graph(n, s, d)
+        og = oracle.build_graph(n, s, d)
+        rp, col, val = tpa.get_csr(g, 0)
+        m = g.m
+        assert m == og.m
+        cand = synth.nodes_with_out_edge(n, s, d)
+        for seed in (int(cand[0]), int(cand[len(cand) // 2])):
+            x0 = torch.zeros(n, dtype=torch.float32, device="cuda")
+            x0[seed] = C
+            y1 = torch.empty(n, dtype=torch.float32, device="cuda")
+            y2 = torch.empty(n, dtype=torch.float32, device="cuda")
+            r = torch.zeros(n, dtype=torch.float32, device="cuda")
+            tpa.cpi_step_noalloc(n, m, rp, col, val, C, x0, y1, r)
+            tpa.cpi_step_noalloc(n, m, rp, col, val, C, y1, y2, r)
+            q = np.zeros(n)
+            q[seed] = 1.0
+            ref1, _ = oracle.cpi(og, q, C, EPS, 1, 1)
+            ref2, _ = oracle.cpi(og, q, C, EPS, 2, 2)
+            ref12, _ = oracle.cpi(og, q, C, EPS, 1, 2)
+            close(y1.cpu().numpy(), ref1, f"x1 scale {scale} seed {seed}")
+            close(y2.cpu().numpy(), ref2, f"x2 scale {scale} seed {seed}")
+            close(r.cpu().numpy(), ref12, f"x1 + x2 scale {scale} seed {seed}")
+        g.free()
+
+
 def test_rejects_sizes_beyond_the_scratch():
     import paper_1708_02574_gb300 as tpa
 
