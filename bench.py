@@ -61,10 +61,22 @@ def parse_args(argv=None):
                          "BLOCKS equal communities and a share P_IN of edges inside them")
     ap.add_argument("--valued-products", action="store_true",
                     help="products that read the value array instead of the default pattern-only products")
+    ap.add_argument("--variant", action="append", default=[], metavar="NAME",
+                    help="use the SpMV/SpMM variant NAME (e.g. 'seg<8,8,8>') for its padded width; repeatable")
     ap.add_argument("--profile-case", choices=["preprocess", "query8"], default=None,
                     help="run one small case for an ncu capture and exit (no JSON line): preprocessing of the "
                          "graph, or two 8-seed queries of light seeds after it")
     return ap.parse_args(argv)
+
+
+def apply_variants(tpa, names):
+    """Force the named kernel variants (tpa_set_variant) for their widths."""
+    by_name = {v["name"]: v for v in tpa.variants()}
+    for nm in names:
+        v = by_name.get(nm)
+        if v is None:
+            raise SystemExit(f"unknown variant {nm!r}; known: {sorted(by_name)}")
+        tpa.set_variant(v["kp"], v["index"])
 
 
 def accuracy_study(args):
@@ -76,6 +88,7 @@ def accuracy_study(args):
     import paper_1708_02574_gb300 as tpa
     from paper_1708_02574_gb300 import accuracy
     tpa.set_pattern(not args.valued_products)
+    apply_variants(tpa, args.variant)
     n = 1 << args.scale
     if args.graph == "rmat":
         src, dst = synth.rmat_edges(args.scale, args.edge_factor)
@@ -106,6 +119,7 @@ def profile_case(args):
     import synth
     import paper_1708_02574_gb300 as tpa
     tpa.set_pattern(not args.valued_products)
+    apply_variants(tpa, args.variant)
     n = 1 << args.scale
     src, dst = synth.rmat_edges(args.scale, args.edge_factor)
     g = tpa.build_graph(n, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda())
@@ -321,6 +335,7 @@ def main(argv=None):
     import paper_1708_02574_gb300 as tpa
 
     tpa.set_pattern(not args.valued_products)
+    apply_variants(tpa, args.variant)
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist

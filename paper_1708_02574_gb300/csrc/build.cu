@@ -430,7 +430,7 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
 
     // 4. allocate the graph arrays
     const size_t mb = (size_t)std::max<int64_t>(m, 1);
-    const size_t mp = (size_t)(m + CSR_PAD);
+    const size_t mp = (size_t)csr_len(m);
     g->rp_t.ensure((size_t)(n + 1) * sizeof(int64_t), s);
     g->col_t.ensure(mp * sizeof(int32_t), s);
     g->val_t.ensure(mp * sizeof(float), s);
@@ -438,7 +438,7 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
     g->col_a.ensure(mp * sizeof(int32_t), s);
     g->val_a.ensure(mp * sizeof(float), s);
     for (DevBuf *b : {&g->col_t, &g->val_t, &g->col_a, &g->val_a})
-        TPA_CUDA(cudaMemsetAsync(static_cast<char *>(b->p) + (size_t)m * 4, 0, (size_t)CSR_PAD * 4, s));
+        TPA_CUDA(cudaMemsetAsync(static_cast<char *>(b->p) + (size_t)m * 4, 0, (mp - (size_t)m) * 4, s));
     g->outdeg.ensure((size_t)n * sizeof(int32_t), s);
     g->inv_deg32.ensure((size_t)n * sizeof(float), s);
     cnt.ensure((size_t)n * sizeof(int32_t), s);

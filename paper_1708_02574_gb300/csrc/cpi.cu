@@ -204,6 +204,7 @@ static void bind_seg(Params &p, tpa_graph *g, int which, int64_t tn, int kp, cud
     }
     need(W.agg, (size_t)T.tiles * kp * sizeof(unsigned long long), "carry-out words");
     need(R.colf, (size_t)T.tiles * tn * sizeof(uint32_t), "flagged columns");
+    TPA_REQUIRE(T.tiles * tn <= csr_len(g->m), "segmented walk: value array shorter than the tiles");
     p.colf = R.colf.as<uint32_t>();
     p.nz_rows = R.nz_rows.as<int32_t>();
     p.empty_rows = R.empty_rows.as<int32_t>();
@@ -325,27 +326,33 @@ static int64_t launch_spmvp(const Params &p, cudaStream_t s)
 }
 
 // Segmented flag walk (spmm_seg.cuh): persistent grid of at most the
-// kernel's occupancy times the SM count (its waits need every CTA resident);
-// returns the CTAs launched (rows of the L1 partial buffer).
-template <int V, int R, int PF>
+// kernel's occupancy times the SM count, launched cooperatively (its waits
+// need every CTA resident); returns the CTAs launched (rows of the L1
+// partial buffer).
+template <int V, int R, int PF, int NB>
 static int64_t launch_seg(const Params &p, cudaStream_t s)
 {
-    constexpr size_t smem = seg_smem_bytes<V, R>();
-    static_assert(smem <= 227 * 1024, "shared memory per block");
-    auto *const valued = spmm_seg_k<V, R, PF, false>;
-    auto *const pattern = spmm_seg_k<V, R, PF, true>;
+    constexpr size_t smem_v = SegSmem<V, R, NB, false>::BYTES;
+    constexpr size_t smem_p = SegSmem<V, R, NB, true>::BYTES;
+    static_assert(smem_v <= 200 * 1024 && smem_p <= 200 * 1024, "shared memory per block");
+    auto *const valued = spmm_seg_k<V, R, PF, NB, false>;
+    auto *const pattern = spmm_seg_k<V, R, PF, NB, true>;
     static int per_sm_v = 0, per_sm_p = 0;
     if (!per_sm_v) {
-        for (auto *fn : {valued, pattern}) {
-            TPA_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            TPA_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                          (int)cudaSharedmemCarveoutMaxShared));
-        }
-        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_v, valued, SEG_WARPS * 32, smem));
-        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_p, pattern, SEG_WARPS * 32, smem));
+        TPA_CUDA(cudaFuncSetAttribute(valued, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v));
+        TPA_CUDA(cudaFuncSetAttribute(pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_v, valued, SEG_WARPS * 32, smem_v));
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_p, pattern, SEG_WARPS * 32, smem_p));
         TPA_REQUIRE(per_sm_v >= 1 && per_sm_p >= 1, "segmented walk: the kernel does not fit on an SM");
+        // ask for the shared-memory share those CTAs need (the rest stays L1)
+        for (int k = 0; k < 2; ++k) {
+            const size_t need = (size_t)(k ? per_sm_p : per_sm_v) * ((k ? smem_p : smem_v) + 3 * 1024);
+            const int pct = (int)std::min<size_t>(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024));
+            TPA_CUDA(cudaFuncSetAttribute(k ? pattern : valued, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+        }
     }
-    const int per_sm = p.inv_deg ? per_sm_p : per_sm_v;
+    const bool pat = p.inv_deg != nullptr;
+    const int per_sm = pat ? per_sm_p : per_sm_v;
     int64_t grid =
         std::max<int64_t>(1, std::min<int64_t>((p.seg_tiles + SEG_WARPS - 1) / SEG_WARPS, (int64_t)per_sm * num_sms()));
     // a cooperative launch: the driver starts every CTA at once or refuses
@@ -355,13 +362,13 @@ static int64_t launch_seg(const Params &p, cudaStream_t s)
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.blockDim = dim3(SEG_WARPS * 32);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = pat ? smem_p : smem_v;
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     for (;;) {
         cfg.gridDim = dim3((unsigned)grid);
-        const cudaError_t e = cudaLaunchKernelEx(&cfg, p.inv_deg ? pattern : valued, p);
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, pat ? pattern : valued, p);
         if (e == cudaSuccess) break;
         if (e != cudaErrorCooperativeLaunchTooLarge || grid == 1) TPA_CUDA(e);
         cudaGetLastError();
@@ -467,8 +474,8 @@ struct Variant {
 #define TPA_VARIANTG(G, V, I, PF) \
     {{G, V, I, PF, 32}, launch_spmvg<G, V, I, PF, 8>, launch_fix<G * V>, "walker<" #G "," #V "," #I "," #PF ">"}
 #define TPA_VARIANTB(KP) {{1, KP, 4, 4, 32}, launch_binned<KP>, launch_bin_finish<KP>, "bins<" #KP ">", true}
-#define TPA_VARIANTS(V, R, PF) \
-    {{1, V, R, PF, 32}, launch_seg<V, R, PF>, nullptr, "seg<" #V "," #R "," #PF ">", false, true}
+#define TPA_VARIANTS(V, R, PF, NB) \
+    {{1, V, R, PF, 32}, launch_seg<V, R, PF, NB>, nullptr, "seg<" #V "," #R "," #PF "," #NB ">", false, true}
 #define TPA_VARIANTP(G, V, I, PF, W, MB)                                 \
     {{G, V, I, PF, 32}, launch_spmvp<G, V, I, PF, W, MB>, launch_fix<G * V>, \
      "pipe<" #G "," #V "," #I "," #PF "," #W "," #MB ">"}
@@ -480,17 +487,17 @@ static const Variant kVariants[] = {
     TPA_VARIANTP(1, 4, 4, 4, 8, 1),
     TPA_VARIANTP(2, 4, 8, 8, 4, 5),
     TPA_VARIANTP(4, 4, 8, 8, 4, 1),
-    TPA_VARIANTS(1, 16, 16),
-    TPA_VARIANTS(2, 8, 8),
-    TPA_VARIANTS(4, 8, 8),
-    TPA_VARIANTS(8, 8, 8),
-    TPA_VARIANTS(1, 32, 16),
-    TPA_VARIANTS(1, 8, 8),
-    TPA_VARIANTS(2, 16, 8),
-    TPA_VARIANTS(4, 4, 4),
-    TPA_VARIANTS(4, 16, 8),
-    TPA_VARIANTS(8, 8, 4),
-    TPA_VARIANTS(8, 4, 4),
+    TPA_VARIANTS(1, 8, 8, 3),
+    TPA_VARIANTS(2, 8, 8, 3),
+    TPA_VARIANTS(4, 8, 8, 3),
+    TPA_VARIANTS(8, 8, 4, 2),
+    TPA_VARIANTS(1, 16, 16, 2),
+    TPA_VARIANTS(1, 4, 4, 4),
+    TPA_VARIANTS(2, 4, 4, 4),
+    TPA_VARIANTS(4, 4, 4, 4),
+    TPA_VARIANTS(8, 4, 4, 4),
+    TPA_VARIANTS(8, 8, 8, 2),
+    TPA_VARIANTS(8, 4, 4, 2),
     TPA_VARIANT(8, 4, 16, 8),
     TPA_VARIANT(16, 4, 16, 8),
     TPA_VARIANT(32, 4, 32, 8),

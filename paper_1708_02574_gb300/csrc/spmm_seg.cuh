@@ -6,9 +6,12 @@
 // nonzeros, one warp per tile in a static strided order (tile t on warp
 // t mod W, so the warps in flight work on one band of rows and their gathers
 // share L2).  Lane l of a tile owns nonzeros [t*TN + R*l, t*TN + R*l + R):
-//   1. its R column ids come in two or four 16-byte streaming loads of a copy
-//      of the column array whose bit 31 marks the first nonzero of a row, so
-//      no row pointer is read and nothing is staged in shared memory;
+//   1. its R column ids come from a copy of the column array whose bit 31
+//      marks the first nonzero of a row (no row pointer is read); each warp
+//      keeps its next NB tiles of column words (and values) in flight with
+//      1-D bulk copies (cp.async.bulk) into a ring of shared-memory stages,
+//      each completing on its own mbarrier, so the copies cost no load
+//      instructions and the tile's words are there when its turn comes;
 //   2. it gathers the R rows X[col][0..V) (V = padded batch width, one lane
 //      holds a whole row: one 32-byte load at V = 8) and walks them in order,
 //      closing a row sum at every row start;
@@ -154,15 +157,23 @@ __device__ __forceinline__ void seg_lookback(const Params &p, int64_t t, uint32_
     }
 }
 
-// Epilogue of one finished row for the segmented kernel (lane holds the row).
+// Epilogue of one finished row for the segmented kernel (lane holds the row;
+// w_row: RN32(1/outdeg) of the row for pattern-only products).
+template <int V, bool PAT>
+__device__ __forceinline__ void seg_emit_w(const Params &p, int64_t v, const float (&sv)[V], const int (&alive)[V],
+                                           float (&l1)[V], float w_row)
+{
+    if (p.mode == MODE_ACC)
+        epilogue_red<V, V, PAT ? PM_PATTERN : PM_VALUED>(p, v, 0, sv, alive, l1, w_row);
+    else
+        epilogue<V, V, PAT ? PM_PATTERN : PM_VALUED>(p, v, 0, sv, alive, l1);
+}
+
 template <int V, bool PAT>
 __device__ __forceinline__ void seg_emit(const Params &p, int64_t v, const float (&sv)[V], const int (&alive)[V],
                                          float (&l1)[V])
 {
-    if (p.mode == MODE_ACC)
-        epilogue_red<V, V, PAT ? PM_PATTERN : PM_VALUED>(p, v, 0, sv, alive, l1, PAT ? __ldg(p.inv_deg + v) : 0.0f);
-    else
-        epilogue<V, V, PAT ? PM_PATTERN : PM_VALUED>(p, v, 0, sv, alive, l1);
+    seg_emit_w<V, PAT>(p, v, sv, alive, l1, PAT && p.mode == MODE_ACC ? __ldg(p.inv_deg + v) : 0.0f);
 }
 
 // Finish row `row`, whose part in tile t is `part`, with the carry-outs of
@@ -181,21 +192,90 @@ __device__ __forceinline__ void seg_finish(const Params &p, int64_t t, int32_t r
     }
 }
 
-// Dynamic shared memory of the segmented kernel: per warp, the sums of the
-// rows that start and end in its tile (at most TN - 1 of V floats).
-template <int V, int R>
-constexpr size_t seg_smem_bytes()
+// ------------------------------------------ bulk copies and mbarriers ---
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
 {
-    return (size_t)SEG_WARPS * 32 * R * V * sizeof(float);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int V, int R, int PF, bool PAT>
+// One expected arrival that also expects `bytes` from bulk copies.
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of a barrier; false (and the error flag
+// raised) when it gives up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, Ctl *hdr)
+{
+    long long spins = 0;
+    while (!mbar_test(bar, parity)) {
+        if (++spins > SEG_SPIN_LIMIT) {
+            atomicOr(&hdr->error, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completing on the barrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared memory of the segmented kernel, per warp: NB stages of one tile's
+// column words (and values), the sums of the rows finished in the tile (slot
+// TN-1 holds the part of the row that ends at the tile's first row start),
+// and one barrier per stage.
+template <int V, int R, int NB, bool PAT>
+struct SegSmem {
+    static constexpr int TN = 32 * R;
+    static constexpr size_t STAGE = (size_t)TN * sizeof(uint32_t) * (PAT ? 1 : 2);
+    static constexpr size_t RS = (size_t)TN * V * sizeof(float);
+    static constexpr size_t PER_WARP = NB * STAGE + RS + 16 * NB;
+    static constexpr size_t BYTES = SEG_WARPS * PER_WARP;
+};
+
+template <int V, int R, int NB, bool PAT>
+__device__ __forceinline__ void seg_issue(const Params &p, unsigned char *stage, uint64_t *bar, int64_t t)
+{
+    using SM = SegSmem<V, R, NB, PAT>;
+    constexpr unsigned CB = SM::TN * sizeof(uint32_t);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the stage come first
+    mbar_expect(bar, PAT ? CB : 2 * CB);
+    bulk_g2s(stage, p.colf + t * SM::TN, CB, bar);
+    if constexpr (!PAT) bulk_g2s(stage + CB, p.val + t * SM::TN, CB, bar);
+}
+
+template <int V, int R, int PF, int NB, bool PAT>
 __global__ void __launch_bounds__(SEG_WARPS * 32) spmm_seg_k(Params p)
 {
+    using SM = SegSmem<V, R, NB, PAT>;
     static_assert(R % 4 == 0 && R % PF == 0 && R <= 32, "R");
     static_assert(V == 1 || V == 2 || V == 4 || V == 8, "V");
-    constexpr int TN = 32 * R;
-    extern __shared__ __align__(16) float seg_smem[];
+    constexpr int TN = SM::TN;
+    extern __shared__ __align__(128) unsigned char seg_smem[];
     __shared__ double s_fin[256];
     __shared__ float s_l1[SEG_WARPS][V];
     __shared__ int s_last;
@@ -204,8 +284,10 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) spmm_seg_k(Params p)
     const uint32_t ep_raw = *(volatile uint32_t *)&cv.hdr->epoch;
     const uint32_t ep = (ep_raw + 1u) & 0x7fffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float *rs = seg_smem + (size_t)warp * TN * V;
     const unsigned FULL = 0xffffffffu;
+    unsigned char *wbase = seg_smem + (size_t)warp * SM::PER_WARP;
+    float *rs = reinterpret_cast<float *>(wbase + NB * SM::STAGE);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(wbase + NB * SM::STAGE + SM::RS);
 
     // rows of y that the walk never writes but that must read as zero
     if (p.zero_mode == 1) {
@@ -228,56 +310,84 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) spmm_seg_k(Params p)
         }
     }
 
-    int alive[V];
+    unsigned amask = 0;
     float l1[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) {
-        alive[j] = cv.alive[j];
+        amask |= (cv.alive[j] ? 1u : 0u) << j;
         l1[j] = 0.0f;
     }
+    int alive[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) alive[j] = (amask >> j) & 1u;
+
+    const int64_t nw = (int64_t)gridDim.x * SEG_WARPS;
+    const int64_t t0 = (int64_t)blockIdx.x * SEG_WARPS + warp;
+    // prologue: barriers, and the first NB tiles of this warp in flight
+    if (lane == 0) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) mbar_init(bars + b);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (t0 + b * nw < p.seg_tiles) seg_issue<V, R, NB, PAT>(p, wbase + b * SM::STAGE, bars + b, t0 + b * nw);
+    }
+    __syncwarp();
+    int32_t crow_next = t0 < p.seg_tiles ? __ldg(p.tile_crow0 + t0) : 0;
+
     // the row a tile finishes through the carry-outs of earlier tiles, held
-    // until the warp's next tile is done
+    // until the warp's next tile is under way
     bool pend = false;
     int64_t pend_t = 0;
     int32_t pend_row = 0;
     float pend_part[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) pend_part[j] = 0.0f;
-    const int64_t nw = (int64_t)gridDim.x * SEG_WARPS;
-    for (int64_t t = (int64_t)blockIdx.x * SEG_WARPS + warp; t < p.seg_tiles; t += nw) {
-        const int64_t e0 = t * TN + (int64_t)lane * R;
-        // 1. column words (the copy is padded to whole tiles) and row starts
+
+    int it = 0;
+    bool broke = false;
+    for (int64_t t = t0; t < p.seg_tiles; t += nw, ++it) {
+        const int b = it % NB;
+        const int64_t crow0 = crow_next;
+        if (t + nw < p.seg_tiles) crow_next = __ldg(p.tile_crow0 + t + nw);
+        // the carry-out the pending row needs first, loaded early
+        unsigned long long probe = 0ull;
+        if (pend && lane < V) probe = ld_relaxed_u64(p.agg + (pend_t - 1) * V + lane);
+
+        // 1. column words (and values) of the tile from its stage
+        unsigned char *stage = wbase + b * SM::STAGE;
+        if (!mbar_wait(bars + b, (unsigned)(it / NB) & 1u, cv.hdr)) {
+            broke = true;
+            break;
+        }
         uint32_t cw[R];
+        float vv[PAT ? 1 : R];
 #pragma unroll
         for (int q = 0; q < R / 4; ++q) {
-            const uint4 c = ld_cols4(p.colf + e0 + 4 * q);
+            const uint4 c = reinterpret_cast<const uint4 *>(stage)[lane * (R / 4) + q];
             cw[4 * q] = c.x;
             cw[4 * q + 1] = c.y;
             cw[4 * q + 2] = c.z;
             cw[4 * q + 3] = c.w;
-        }
-        float vv[PAT ? 1 : R];
-        if constexpr (!PAT) {
-            if (e0 + R <= p.m) {
-#pragma unroll
-                for (int q = 0; q < R / 4; ++q) {
-                    const float4 v4 = ld_vals4(p.val + e0 + 4 * q);
-                    vv[4 * q] = v4.x;
-                    vv[4 * q + 1] = v4.y;
-                    vv[4 * q + 2] = v4.z;
-                    vv[4 * q + 3] = v4.w;
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < R; ++i) vv[i] = e0 + i < p.m ? __ldg(p.val + e0 + i) : 0.0f;
+            if constexpr (!PAT) {
+                const float4 v4 = reinterpret_cast<const float4 *>(stage + TN * sizeof(uint32_t))[lane * (R / 4) + q];
+                vv[4 * q] = v4.x;
+                vv[4 * q + 1] = v4.y;
+                vv[4 * q + 2] = v4.z;
+                vv[4 * q + 3] = v4.w;
             }
         }
+        const int64_t e0 = t * TN + (int64_t)lane * R;
+        const bool full = (t + 1) * TN <= p.m;
         const int64_t left = p.m - e0;
         const unsigned vm = left >= R ? (R == 32 ? FULL : (1u << R) - 1u) : left > 0 ? (1u << left) - 1u : 0u;
         unsigned fm = 0;
 #pragma unroll
         for (int i = 0; i < R; ++i) fm |= (cw[i] >> 31) << i;
         fm &= vm;
+        __syncwarp();   // every lane has its words: the stage takes the warp's tile NB rounds ahead
+        if (lane == 0 && t + NB * nw < p.seg_tiles) seg_issue<V, R, NB, PAT>(p, stage, bars + b, t + NB * nw);
+
         const int nf = __popc(fm);
         int incl = nf;
 #pragma unroll
@@ -287,125 +397,161 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) spmm_seg_k(Params p)
         }
         const int excl = incl - nf;
         const int q = __shfl_sync(FULL, incl, 31);
+        // ids of the rows the epilogue pass finishes (lane k: row k), loaded early
+        const int32_t vk = lane < q - 1 ? __ldg(p.nz_rows + crow0 + lane) : 0;
 
-        // 2. gathers and the walk: a row sum closes at every row start
-        float acc[V], head[V];
+        // 2. gathers and the walk: at a row start the running sum goes to its
+        //    slot (the row that ends there) and restarts; one FFMA per column
+        float acc[V];
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-            acc[j] = 0.0f;
-            head[j] = 0.0f;
-        }
-        int seen = 0;
+        for (int j = 0; j < V; ++j) acc[j] = 0.0f;
+        int slot = excl - 1;   // row ending at this lane's next row start (-1: the tile's first row)
 #pragma unroll
         for (int c0 = 0; c0 < R; c0 += PF) {
             float xv[PF][V];
+            if (full) {   // every nonzero of the tile exists: no masks on the gathers
 #pragma unroll
-            for (int it = 0; it < PF; ++it) {
-                const int i = c0 + it;
-                if ((vm >> i) & 1u) {
-                    ld_row<V>(p.x + (int64_t)(cw[i] & ~SEG_ROW_START) * V, xv[it]);
-                } else {
+                for (int u = 0; u < PF; ++u) ld_row<V>(p.x + (int64_t)(cw[c0 + u] & ~SEG_ROW_START) * V, xv[u]);
+            } else {
 #pragma unroll
-                    for (int j = 0; j < V; ++j) xv[it][j] = 0.0f;
+                for (int u = 0; u < PF; ++u) {
+                    const int i = c0 + u;
+                    if ((vm >> i) & 1u) {
+                        ld_row<V>(p.x + (int64_t)(cw[i] & ~SEG_ROW_START) * V, xv[u]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < V; ++j) xv[u][j] = 0.0f;
+                    }
                 }
             }
 #pragma unroll
-            for (int it = 0; it < PF; ++it) {
-                const int i = c0 + it;
-                if ((fm >> i) & 1u) {
-                    if (seen == 0) {
-#pragma unroll
-                        for (int j = 0; j < V; ++j) head[j] = acc[j];
-                    } else {
-                        st_row<V>(rs + (excl + seen - 1) * V, acc);
-                    }
-#pragma unroll
-                    for (int j = 0; j < V; ++j) acc[j] = 0.0f;
-                    ++seen;
+            for (int u = 0; u < PF; ++u) {
+                const int i = c0 + u;
+                const bool f = (fm >> i) & 1u;
+                if (f) {
+                    st_row<V>(rs + (slot >= 0 ? slot : TN - 1) * V, acc);
+                    ++slot;
                 }
+                const float keep = f ? 0.0f : 1.0f;
                 if constexpr (PAT) {
 #pragma unroll
-                    for (int j = 0; j < V; ++j) acc[j] += xv[it][j];
+                    for (int j = 0; j < V; ++j) acc[j] = fmaf(acc[j], keep, xv[u][j]);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < V; ++j) acc[j] = fmaf(vv[i], xv[it][j], acc[j]);
+                    for (int j = 0; j < V; ++j) acc[j] = fmaf(vv[i], xv[u][j], acc[j] * keep);
                 }
             }
         }
 
         // 3. segmented scan of the lanes' trailing sums, restarting at lanes in
-        //    which a row starts; inc of lane l is the sum from the last row start
-        //    at or before lane l through the end of lane l
-        float inc[V];
-#pragma unroll
-        for (int j = 0; j < V; ++j) inc[j] = acc[j];
+        //    which a row starts; acc of lane l becomes the sum from the last
+        //    row start at or before lane l through the end of lane l
         int key = nf > 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             float up[V];
 #pragma unroll
-            for (int j = 0; j < V; ++j) up[j] = __shfl_up_sync(FULL, inc[j], o);
+            for (int j = 0; j < V; ++j) up[j] = __shfl_up_sync(FULL, acc[j], o);
             const int kup = __shfl_up_sync(FULL, key, o);
             if (lane >= o) {
                 if (!key) {
 #pragma unroll
-                    for (int j = 0; j < V; ++j) inc[j] += up[j];
+                    for (int j = 0; j < V; ++j) acc[j] += up[j];
                 }
                 key |= kup;
             }
         }
-        // the row that ends just before this lane's first row start
-        float first_tot[V];
+        // the row that ends at this lane's first row start: add what earlier lanes hold
+        {
+            float cin[V];
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const float cin = __shfl_up_sync(FULL, inc[j], 1);
-            first_tot[j] = (lane > 0 ? cin : 0.0f) + head[j];
+            for (int j = 0; j < V; ++j) {
+                cin[j] = __shfl_up_sync(FULL, acc[j], 1);
+                if (lane == 0) cin[j] = 0.0f;
+            }
+            if (nf > 0) {
+                float *sp = rs + (excl > 0 ? excl - 1 : TN - 1) * V;
+                float h[V];
+                ld_row_smem<V>(sp, h);
+#pragma unroll
+                for (int j = 0; j < V; ++j) h[j] += cin[j];
+                st_row<V>(sp, h);
+            }
         }
-        if (nf > 0 && excl > 0) st_row<V>(rs + (excl - 1) * V, first_tot);
         // carry-out of the tile, tagged with this launch and whether a row starts in it
         if (lane == 31) {
             const uint32_t tag = (ep << 1) | (q > 0 ? 1u : 0u);
 #pragma unroll
-            for (int j = 0; j < V; ++j) st_relaxed_u64(p.agg + t * V + j, seg_pack(inc[j], tag));
+            for (int j = 0; j < V; ++j) st_relaxed_u64(p.agg + t * V + j, seg_pack(acc[j], tag));
         }
         __syncwarp();
 
-        // 4. rows that start and end in the tile: lane per row, coalesced
-        const int64_t crow0 = p.tile_crow0[t];
-        for (int k = lane; k < q - 1; k += 32) {
-            const int64_t v = p.nz_rows[crow0 + k];
-            float sv[V];
-            ld_row_smem<V>(rs + k * V, sv);
-            seg_emit<V, PAT>(p, v, sv, alive, l1);
-        }
-
-        // 5. the row that ends in this tile after starting in an earlier one (or
-        //    runs to the end of the matrix from an earlier tile) needs the
-        //    carry-outs of the tiles before; it is finished one tile of this
-        //    warp later, when those were published long ago
+        // 4. the pending row of the warp's previous tile
         if (pend) {
-            seg_finish<V, PAT>(p, pend_t, pend_row, pend_part, ep, cv.hdr, lane, alive, l1);
+            float back[V];
+            const unsigned long long w = lane < V ? probe : 0ull;
+            const bool ready = __all_sync(FULL, lane >= V || (uint32_t)(w >> 33) == ep);
+            const bool start = __shfl_sync(FULL, (int)((w >> 32) & 1ull), 0) != 0;
+            if (ready && start) {
+#pragma unroll
+                for (int j = 0; j < V; ++j) back[j] = __shfl_sync(FULL, __uint_as_float((uint32_t)w), j);
+            } else {
+                seg_lookback<V>(p, pend_t, ep, cv.hdr, lane, back);
+            }
+            if (lane == 0) {
+                float tot[V];
+#pragma unroll
+                for (int j = 0; j < V; ++j) tot[j] = pend_part[j] + back[j];
+                seg_emit<V, PAT>(p, (int64_t)pend_row, tot, alive, l1);
+            }
             pend = false;
         }
+        // the row that ends in this tile after starting in an earlier one (or
+        // runs to the end of the matrix from an earlier tile) waits for the
+        // warp's next tile
         const bool last = t == p.seg_tiles - 1;
         if ((q > 0 && t > 0) || (q == 0 && last)) {
             if (q > 0) {
-                const int f0 = __ffs(__ballot_sync(FULL, nf > 0)) - 1;
-#pragma unroll
-                for (int j = 0; j < V; ++j) pend_part[j] = __shfl_sync(FULL, first_tot[j], f0);
+                ld_row_smem<V>(rs + (TN - 1) * V, pend_part);
             } else {
 #pragma unroll
-                for (int j = 0; j < V; ++j) pend_part[j] = __shfl_sync(FULL, inc[j], 31);
+                for (int j = 0; j < V; ++j) pend_part[j] = __shfl_sync(FULL, acc[j], 31);
             }
             pend = true;
             pend_t = t;
-            pend_row = p.nz_rows[crow0 - 1];
+            pend_row = __ldg(p.nz_rows + crow0 - 1);
+        }
+
+        // 5. rows that start and end in the tile: lane per row, coalesced
+        if (lane < q - 1) {
+            float sv[V];
+            ld_row_smem<V>(rs + lane * V, sv);
+            seg_emit<V, PAT>(p, (int64_t)vk, sv, alive, l1);
+        }
+        for (int k = lane + 32; k < q - 1; k += 32) {
+            float sv[V];
+            ld_row_smem<V>(rs + k * V, sv);
+            seg_emit<V, PAT>(p, (int64_t)__ldg(p.nz_rows + crow0 + k), sv, alive, l1);
         }
         // 6. the last row that starts in the last tile ends with the matrix
-        if (last && q > 0 && lane == 31) seg_emit<V, PAT>(p, (int64_t)p.nz_rows[crow0 + q - 1], inc, alive, l1);
+        if (last && q > 0 && lane == 31) seg_emit<V, PAT>(p, (int64_t)__ldg(p.nz_rows + crow0 + q - 1), acc, alive, l1);
         __syncwarp();   // rs is rewritten by the next tile
     }
-    if (pend) seg_finish<V, PAT>(p, pend_t, pend_row, pend_part, ep, cv.hdr, lane, alive, l1);
+    if (broke) {   // a stage never arrived: wait (bounded) for the copies still in flight before leaving
+        const int64_t mine = t0 < p.seg_tiles ? (p.seg_tiles - 1 - t0) / nw + 1 : 0;
+        for (int k = it; k < it + NB && k < mine; ++k) mbar_wait(bars + k % NB, (unsigned)(k / NB) & 1u, cv.hdr);
+        pend = false;
+    }
+    if (pend) {
+        float back[V];
+        seg_lookback<V>(p, pend_t, ep, cv.hdr, lane, back);
+        if (lane == 0) {
+            float tot[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) tot[j] = pend_part[j] + back[j];
+            seg_emit<V, PAT>(p, (int64_t)pend_row, tot, alive, l1);
+        }
+    }
 
     // L1 partial of the CTA; the last CTA to finish sums the partials in a fixed
     // order and applies the break test of Algorithm 1 per column

@@ -112,13 +112,18 @@ struct SegTiles {
     int64_t tn = 0, tiles = 0;
     DevBuf crow0;
 };
-constexpr int64_t SEG_MAX_TN = 1024;   // the padding of the column copy covers tiles up to this size
+constexpr int64_t SEG_MAX_TN = 1024;   // the padding of the column arrays covers tiles up to this size
 
 // ---------------------------------------------------------------- graph ---
-// The column and value arrays of both CSRs hold CSR_PAD extra zero elements
-// after the m real ones, so kernels may stage a tile's nonzeros in 16-byte
-// chunks rounded outward.
+// The column and value arrays of both CSRs hold at least CSR_PAD extra zero
+// elements after the m real ones, so kernels may stage a tile's nonzeros in
+// 16-byte chunks rounded outward; they are allocated to csr_len(m) elements,
+// which also covers the whole last tile of a segmented walk (tiles of at
+// most SEG_MAX_TN nonzeros, whose bulk copies read whole tiles).
 constexpr int64_t CSR_PAD = 4;
+constexpr int64_t CSR_TILE_PAD = 1024;
+inline int64_t csr_len(int64_t m) { return (m + CSR_TILE_PAD - 1) / CSR_TILE_PAD * CSR_TILE_PAD + CSR_TILE_PAD; }
+static_assert(CSR_TILE_PAD >= SEG_MAX_TN, "CSR padding covers a whole tile");
 
 struct Workspace {
     DevBuf x, y, r;         // iterates and accumulator
