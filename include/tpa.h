@@ -289,47 +289,52 @@ tpa_status tpa_seed_order(const int32_t *outdeg, int k, int S, int32_t *perm);
 
 /* ---------------------------------------------------- batched serving ---
  * Algorithm 3 for a stream of request batches of uneven size, with the launch
- * sequence of each batch size captured once in a CUDA graph and replayed.
+ * sequence of each kind of batch captured once in a CUDA graph and replayed.
  * Not part of the paper (its online phase answers one seed at a time).
  *
  * A server answers into one caller-owned device buffer out (float32, node-
  * major, row stride ldo >= max_k): after tpa_server_query with k seeds,
- * out[v * ldo + j] for j < k is the TPA score of node v for seeds[j].  A
- * server keeps its own workspace (about 6 n * 8 floats for chunks of 8 seeds)
- * and graphs that point at it and at the graph's CSR: it must be freed before
- * the graph, and calls on one server must not overlap.  Results equal those
- * of tpa_query with the same settings bit for bit when tpa_query moves no
- * seed (a batch of one chunk, or without seeds of more than 256 out-edges);
- * otherwise the columns whose chunk changed agree to FP32 rounding (the
- * server keeps each seed in its chunk, its branches being chosen on the
- * device).  A change of a kernel
- * setting (tpa_set_variant, tpa_set_batch_width, tpa_set_push, tpa_set_pattern) makes the
- * server capture again, and so does a batch that needs more workspace than
- * any before it (its buffers are reallocated, and graphs captured over the
- * old ones are dropped, never replayed). */
+ * out[v * ldo + j] for j < k is the TPA score of node v for seeds[j].  Each
+ * batch runs as tpa_query would run it: seeds of more than 256 out-edges go
+ * to the last chunks, every chunk's push or pull branch for x1 and x2 is
+ * chosen on the host from the seeds' out-degrees (the server keeps a host
+ * copy of them, 4n bytes), and the moved columns are swapped back at the
+ * end; results equal tpa_query's bit for bit.  A captured graph is keyed by
+ * k and the string of chunk branches, so batches of the same size share
+ * graphs whatever their seeds; at most 64 graphs are kept (least recently
+ * used dropped).  A server keeps its own workspace (about 6 n * 8 floats for
+ * chunks of 8 seeds) and graphs that point at it and at the graph's CSR: it
+ * must be freed before the graph, and calls on one server must not overlap.
+ * A change of a kernel setting (tpa_set_variant, tpa_set_batch_width,
+ * tpa_set_push, tpa_set_pattern) makes the server capture again, and so does
+ * a batch that needs more workspace than any before it (its buffers are
+ * reallocated, and graphs captured over the old ones are dropped, never
+ * replayed).  Validated with oracle parity up to R-MAT scale 24 (16.8 M
+ * nodes, 8,192 seeds in uneven batches). */
 typedef struct tpa_server tpa_server;
 
 /* Create a server for queries with S family steps and at most max_k seeds
  * per batch on a preprocessed graph.  out: device buffer of n rows of ldo
  * floats, or NULL to let the server allocate one (ldo is then max_k; see
  * tpa_server_result).  Errors: TPA_ESTATE before tpa_preprocess; TPA_EINVAL
- * for S outside [1, T], max_k < 1, ldo < max_k, a host out, or a graph of
- * more than 2^22 nodes (the size the server is validated at). */
+ * for S outside [1, T], max_k < 1, ldo < max_k, or a host out. */
 tpa_status tpa_server_create(tpa_graph *g, int S, int max_k, float *out, int64_t ldo, void *stream,
                              tpa_server **srv);
 
 /* Answer one batch of k <= max_k seeds (host or device int32, 0 <= id < n;
  * ids are checked on the host, so device ids cost one small copy and a wait).
- * The first batch of a size runs directly and captures the graph for that
- * size; later batches of the size replay it.  Work is issued on stream. */
+ * The first batch of a kind (k and chunk branches) runs directly and its
+ * sequence is captured; later batches of that kind replay it.  Work is
+ * issued on stream. */
 tpa_status tpa_server_query(tpa_server *srv, const int32_t *seeds, int k, void *stream);
 
 /* The output buffer and its row stride. */
 tpa_status tpa_server_result(const tpa_server *srv, float **out, int64_t *ldo);
 
-/* Graphs held now, graph replays, kernel launches per replay of the graph
- * for batch size k (0 if none), and captures so far (every batch is either
- * a replay or a direct run followed by a capture).  NULL outputs are skipped. */
+/* Graphs held now, graph replays, kernel launches per replay of the most
+ * recently used graph for batch size k (0 if none), and captures so far
+ * (every batch is either a replay or a direct run followed by a capture).
+ * NULL outputs are skipped. */
 tpa_status tpa_server_stats(const tpa_server *srv, int k, int64_t *graphs, int64_t *replays,
                             int64_t *launches_per_replay, int64_t *captures);
 

@@ -32,6 +32,7 @@
 #include <cstring>
 #include <cmath>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "tpa_internal.cuh"
@@ -1174,6 +1175,51 @@ static bool group_heavy_seeds(const int32_t *od, int k, int chunk, std::vector<i
     return moved;
 }
 
+bool regroup_seeds(const int32_t *od, int k, int S, std::vector<int32_t> &perm)
+{
+    const int chunk = g_chunk_query ? g_chunk_query : DEFAULT_CHUNK_QUERY;
+    perm.resize((size_t)k);
+    for (int j = 0; j < k; ++j) perm[j] = j;
+    if (S - 1 < 3) return false;   // the push branch exists from S = 4
+    return group_heavy_seeds(od, k, chunk, perm);
+}
+
+std::string query_branches(const int32_t *od, int k, int S)
+{
+    const int chunk = g_chunk_query ? g_chunk_query : DEFAULT_CHUNK_QUERY;
+    std::string key;
+    for (int k0 = 0; k0 < k; k0 += chunk) {
+        const int kc = std::min(chunk, k - k0);
+        // the conditions of run_cpi_chunk's two-way chunks for a query
+        if (!g_push || S - 1 < 3 || kp_for(kc) > PUSH_MAX_KP) {
+            key.push_back('-');
+            continue;
+        }
+        bool light = true;
+        for (int j = 0; j < kc; ++j) light = light && od[k0 + j] <= PUSH_MAX_OUTDEG;
+        key.push_back(light ? 'p' : 'l');
+    }
+    return key;
+}
+
+// After a regrouped query has written every chunk in place, swap back the
+// column pairs listed in device memory: pairs[0] = count, then the pairs.
+// Grid-stride over n x count, so a captured launch serves any count.
+__global__ void swap_cols_dev_k(float *out, int64_t ldo, int64_t n, const int32_t *pairs)
+{
+    const int np = __ldg(pairs);
+    const int64_t total = n * np;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = i / np;
+        const int q = (int)(i % np);
+        float *row = out + v * ldo;
+        const int32_t a = __ldg(pairs + 1 + 2 * q), b = __ldg(pairs + 2 + 2 * q);
+        const float ta = row[a], tb = row[b];
+        row[a] = tb;
+        row[b] = ta;
+    }
+}
+
 __global__ void gather_seeds_k(const int32_t *seeds, const int32_t *perm, int k, int32_t *out)
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) out[j] = seeds[perm[j]];
@@ -1211,8 +1257,8 @@ void run_cpi(tpa_graph *g, const CpiArgs &a0, cudaStream_t s)
     // the moved columns back at the end.
     std::vector<int32_t> perm, od;
     bool grouped = false;
-    if (a.tpa_final && a.seed_outdeg && a.seeds && !a.set_ptr && a.r_internal && a.t_iter >= 3 && a.out &&
-        is_device_ptr(a.out))
+    if (!a.no_regroup && a.tpa_final && a.seed_outdeg && a.seeds && !a.set_ptr && a.r_internal && a.t_iter >= 3 &&
+        a.out && is_device_ptr(a.out))
         grouped = group_heavy_seeds(a.seed_outdeg, a.k, chunk, perm);
     Workspace &W = g->ws;
     std::vector<int32_t> pairs;
@@ -1237,6 +1283,11 @@ void run_cpi(tpa_graph *g, const CpiArgs &a0, cudaStream_t s)
         a.seed_outdeg = od.data();
     }
     for (int k0 = 0; k0 < a.k; k0 += chunk) run_cpi_chunk(g, a, k0, std::min(chunk, a.k - k0), s);
+    if (a.dev_pairs && a.max_pairs > 0) {
+        swap_cols_dev_k<<<grid_1d(g->n * a.max_pairs, 256), 256, 0, s>>>(a.out, a.ldo, g->n, a.dev_pairs);
+        note_launch("finalize");
+        TPA_CHECK_LAUNCH();
+    }
     if (grouped) {
         const int np = (int)(pairs.size() / 2);
         swap_cols_k<<<grid_1d(g->n * np, 256), 256, 0, s>>>(a.out, a.ldo, g->n, W.cols.as<int32_t>() + a.k, np);

@@ -241,6 +241,12 @@ struct CpiArgs {
     // seed sets (device int64[k+1]): column j starts from q = 1/|S_j| on the
     // members seeds[set_ptr[j] .. set_ptr[j+1]) instead of one seed
     const int64_t *set_ptr = nullptr;
+    // the caller has ordered the seeds already (no regrouping here); when
+    // dev_pairs is set (device int32: a count, then that many column pairs,
+    // at most max_pairs), the paired columns of out are swapped at the end
+    bool no_regroup = false;
+    const int32_t *dev_pairs = nullptr;
+    int max_pairs = 0;
 };
 
 // adjoint.cu
@@ -258,6 +264,17 @@ extern size_t g_adjoint_budget;
 std::vector<int32_t> seed_outdegrees(tpa_graph *g, const int32_t *d_seeds, int k, cudaStream_t s);
 
 void run_cpi(tpa_graph *g, const CpiArgs &a, cudaStream_t s);
+
+// The order tpa_query runs the k seeds of a call in, from their out-degrees
+// od (host): perm[j] is the original position of the seed placed at j.
+// False when nothing moves.
+bool regroup_seeds(const int32_t *od, int k, int S, std::vector<int32_t> &perm);
+
+// The branch each query chunk of k seeds with out-degrees od (in run order,
+// host) takes for x1 and x2: one character per chunk, 'p' push, 'l' pull,
+// '-' neither (the chunk pulls every iteration); a captured launch sequence
+// is valid for the seeds of any batch with the same string.
+std::string query_branches(const int32_t *od, int k, int S);
 
 // Counter bumped by every change of a kernel setting (variant, chunk widths,
 // push path): launch sequences captured before a change are stale.
