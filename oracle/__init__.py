@@ -28,12 +28,12 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``liboracle.so`` (plain C, -O2, no fast-math, single thread)."""
+    """Compile ``liboracle.so`` (plain C, -O2, no fast-math; OpenMP over independent rows)."""
     srcs = [s for s in _SRCS if os.path.exists(s)]
     stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in srcs)
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fno-fast-math", "-ffp-contract=off",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
                                "-shared", "-fPIC", *srcs, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -47,6 +47,8 @@ def _load():
         lib.orc_set_fault.argtypes = [ctypes.c_int]
         lib.orc_set_fault.restype = None
         lib.orc_get_fault.restype = ctypes.c_int
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads.restype = None
         lib.orc_build.restype = i64
         lib.orc_build.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P]
         lib.orc_cpi.restype = i64
@@ -79,6 +81,11 @@ def _bind_adjoint(lib):
 
 def _p(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def set_threads(t: int) -> None:
+    """Threads of the oracle's loops over rows (0 = all cores); results do not depend on it."""
+    _load().orc_set_threads(int(t))
 
 
 def set_fault(k: int) -> None:

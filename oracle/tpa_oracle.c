@@ -8,8 +8,10 @@
  * benchmark's CPU-baseline leg may load it; the product path never calls it
  * and shares no code with it.
  *
- * Everything is double precision, sequential, and written straight from the
- * paper's definitions:
+ * Everything is double precision and written straight from the paper's
+ * definitions; the loops over rows may run on several threads (each row's
+ * sum keeps its sequential order, norms are summed sequentially), which
+ * changes no result:
  *   - Table 1: A~ is the row-normalised adjacency matrix (A~_uv = 1/outdeg(u)
  *     for an edge u->v of the simple graph); the propagation operator is
  *     (1-c) A~^T.
@@ -38,6 +40,9 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -47,10 +52,24 @@ static int g_fault = 0;
 void orc_set_fault(int f) { g_fault = f; }
 int orc_get_fault(void) { return g_fault; }
 
-static int cmp_u64(const void *a, const void *b)
+static int cmp_i32(const void *a, const void *b)
 {
-    const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    const int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
     return (x > y) - (x < y);
+}
+
+/* Threads of the parallel loops below (0 = the OpenMP default, all cores).
+ * Every parallel loop runs over independent rows and keeps each row's own
+ * sums in their sequential order, so results do not depend on it. */
+static int g_threads = 0;
+void orc_set_threads(int t) { g_threads = t; }
+static int nthreads(void)
+{
+#ifdef _OPENMP
+    return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /*
@@ -60,61 +79,100 @@ static int cmp_u64(const void *a, const void *b)
  *              value 1/outdeg(u)                 (rp_t, col_t, val_t)
  *   CSR(A~):   row u lists the out-neighbours v of u in ascending order,
  *              value 1/outdeg(u)                 (rp_a, col_a, val_a)
- * plus outdeg[u].  Arrays sized for m_in entries; any output may be NULL.
+ * plus outdeg[u].  Arrays sized for m_in entries; any output may be NULL
+ * (CSR(A~) is built only when rp_a is given).  The edges are bucketed by
+ * destination (counting sort), each bucket is sorted and its duplicates
+ * dropped; CSR(A~) is then a counting sort of CSR(A~^T) by source, which
+ * keeps each row's destinations ascending.
  * Returns the number m of distinct non-self-loop edges, or -1.
  */
 int64_t orc_build(int64_t n, int64_t m_in, const int32_t *src, const int32_t *dst,
                   int64_t *rp_t, int32_t *col_t, double *val_t,
                   int64_t *rp_a, int32_t *col_a, double *val_a, int32_t *outdeg)
 {
-    uint64_t *key = (uint64_t *)malloc((size_t)(m_in > 0 ? m_in : 1) * sizeof(uint64_t));
+    int64_t *off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t *len = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
     int32_t *deg = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
-    if (!key || !deg) { free(key); free(deg); return -1; }
-
-    /* (dst, src) pairs without self-loops, sorted, duplicates removed */
-    int64_t k = 0;
+    if (!off || !len || !deg) { free(off); free(len); free(deg); return -1; }
+    /* bucket the sources of the non-self-loop edges by destination */
     for (int64_t e = 0; e < m_in; ++e) {
-        if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) { free(key); free(deg); return -1; }
-        if (src[e] == dst[e]) continue;
-        key[k++] = ((uint64_t)(uint32_t)dst[e] << 32) | (uint32_t)src[e];
+        if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) { free(off); free(len); free(deg); return -1; }
+        if (src[e] != dst[e]) off[dst[e] + 1]++;
     }
-    qsort(key, (size_t)k, sizeof(uint64_t), cmp_u64);
+    for (int64_t v = 0; v < n; ++v) off[v + 1] += off[v];
+    const int64_t k = off[n];
+    int32_t *bucket = (int32_t *)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
+    int64_t *fill = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!bucket || !fill) { free(off); free(len); free(deg); free(bucket); free(fill); return -1; }
+    memcpy(fill, off, (size_t)n * sizeof(int64_t));
+    for (int64_t e = 0; e < m_in; ++e)
+        if (src[e] != dst[e]) bucket[fill[dst[e]]++] = src[e];
+    free(fill);
+    /* sort each bucket and keep its distinct sources at its front */
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(nthreads())
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t *b = bucket + off[v];
+        const int64_t cnt = off[v + 1] - off[v];
+        if (cnt > 1) qsort(b, (size_t)cnt, sizeof(int32_t), cmp_i32);
+        int64_t u = 0;
+        for (int64_t i = 0; i < cnt; ++i)
+            if (i == 0 || b[i] != b[i - 1]) b[u++] = b[i];
+        len[v] = u;
+    }
     int64_t m = 0;
-    for (int64_t i = 0; i < k; ++i)
-        if (i == 0 || key[i] != key[i - 1]) key[m++] = key[i];
+    for (int64_t v = 0; v < n; ++v) m += len[v];
 
-    for (int64_t i = 0; i < m; ++i) deg[(uint32_t)key[i]]++;
+    for (int64_t v = 0; v < n; ++v)
+        for (int64_t i = 0; i < len[v]; ++i) deg[bucket[off[v] + i]]++;
     if (g_fault == 6) {               /* planted: normalise by in-degree */
-        memset(deg, 0, (size_t)n * sizeof(int32_t));
-        for (int64_t i = 0; i < m; ++i) deg[key[i] >> 32]++;
+        for (int64_t v = 0; v < n; ++v) deg[v] = (int32_t)len[v];
     }
     if (outdeg) memcpy(outdeg, deg, (size_t)n * sizeof(int32_t));
 
+    int64_t *rpt = rp_t;
+    int64_t *tmp_rp = NULL;
+    if (!rpt && rp_a) {               /* CSR(A~) is built from CSR(A~^T)'s rows */
+        tmp_rp = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+        if (!tmp_rp) { free(off); free(len); free(deg); free(bucket); return -1; }
+        rpt = tmp_rp;
+    }
+    if (rpt) {
+        rpt[0] = 0;
+        for (int64_t v = 0; v < n; ++v) rpt[v + 1] = rpt[v] + len[v];
+    }
     if (rp_t) {
-        memset(rp_t, 0, (size_t)(n + 1) * sizeof(int64_t));
-        for (int64_t i = 0; i < m; ++i) rp_t[(key[i] >> 32) + 1]++;
-        for (int64_t v = 0; v < n; ++v) rp_t[v + 1] += rp_t[v];
-        for (int64_t i = 0; i < m; ++i) {
-            const int32_t u = (int32_t)(uint32_t)key[i];
-            if (col_t) col_t[i] = u;
-            if (val_t) val_t[i] = deg[u] > 0 ? 1.0 / (double)deg[u] : 0.0;
-        }
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(nthreads())
+        for (int64_t v = 0; v < n; ++v)
+            for (int64_t i = 0; i < len[v]; ++i) {
+                const int32_t u = bucket[off[v] + i];
+                if (col_t) col_t[rp_t[v] + i] = u;
+                if (val_t) val_t[rp_t[v] + i] = deg[u] > 0 ? 1.0 / (double)deg[u] : 0.0;
+            }
     }
     if (rp_a) {
-        /* re-key as (src, dst) and sort again */
-        for (int64_t i = 0; i < m; ++i) key[i] = (key[i] << 32) | (key[i] >> 32);
-        qsort(key, (size_t)m, sizeof(uint64_t), cmp_u64);
+        /* counting sort of the edges by source; rows v are visited in
+         * ascending order, so each source's destinations come out ascending */
         memset(rp_a, 0, (size_t)(n + 1) * sizeof(int64_t));
-        for (int64_t i = 0; i < m; ++i) rp_a[(key[i] >> 32) + 1]++;
+        for (int64_t v = 0; v < n; ++v)
+            for (int64_t i = 0; i < len[v]; ++i) rp_a[bucket[off[v] + i] + 1]++;
         for (int64_t u = 0; u < n; ++u) rp_a[u + 1] += rp_a[u];
-        for (int64_t i = 0; i < m; ++i) {
-            const int32_t u = (int32_t)(key[i] >> 32);
-            if (col_a) col_a[i] = (int32_t)(uint32_t)key[i];
-            if (val_a) val_a[i] = deg[u] > 0 ? 1.0 / (double)deg[u] : 0.0;
-        }
+        int64_t *pos = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+        if (!pos) { free(off); free(len); free(deg); free(bucket); free(tmp_rp); return -1; }
+        memcpy(pos, rp_a, (size_t)n * sizeof(int64_t));
+        for (int64_t v = 0; v < n; ++v)
+            for (int64_t i = 0; i < len[v]; ++i) {
+                const int32_t u = bucket[off[v] + i];
+                const int64_t at = pos[u]++;
+                if (col_a) col_a[at] = (int32_t)v;
+                if (val_a) val_a[at] = deg[u] > 0 ? 1.0 / (double)deg[u] : 0.0;
+            }
+        free(pos);
     }
-    free(key);
+    free(tmp_rp);
+    free(off);
+    free(len);
     free(deg);
+    free(bucket);
     return m;
 }
 
@@ -131,6 +189,7 @@ static void propagate(int64_t n, const int64_t *rp, const int32_t *col, const do
         for (int64_t v = 0; v < n; ++v) y[v] *= decay;
         return;
     }
+#pragma omp parallel for schedule(dynamic, 4096) num_threads(nthreads())
     for (int64_t v = 0; v < n; ++v) {
         double s = 0.0;
         for (int64_t e = rp[v]; e < rp[v + 1]; ++e) s += val[e] * x[col[e]];

@@ -282,3 +282,26 @@ def test_query_rejects_bad_input():
         oracle.query(g, 5, C, 5, 10, rs)
     with pytest.raises(ValueError):
         oracle.query(g, 0, C, 6, 5, rs)
+
+
+def test_oracle_threads_do_not_change_results():
+    """The oracle's loops over rows may run on several threads; every row's
+    sum keeps its order and norms are summed sequentially, so the CSR, the
+    preprocessing vector and a query are bit-identical on 1 and on many
+    threads (R-MAT scale 12 with duplicates and self-loops in the raw list)."""
+    n = 1 << 12
+    s, d = synth.rmat_edges(12, 16)
+    outs = []
+    try:
+        for t in (1, 0, 3):
+            oracle.set_threads(t)
+            og = oracle.build_graph(n, s, d)
+            rs, it = oracle.preprocess(og, 0.15, 10, 1e-9)
+            q = oracle.query(og, 5, 0.15, 5, 10, rs, 1e-9)
+            outs.append((og.rp_t.copy(), og.col_t.copy(), og.val_t.copy(), og.rp_a.copy(), og.col_a.copy(),
+                         rs, it, q))
+    finally:
+        oracle.set_threads(0)
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
