@@ -61,12 +61,148 @@ def parse_args(argv=None):
                          "BLOCKS equal communities and a share P_IN of edges inside them")
     ap.add_argument("--valued-products", action="store_true",
                     help="products that read the value array instead of the default pattern-only products")
+    ap.add_argument("--serving", action="store_true",
+                    help="measure batched serving instead: R-MAT --serving-scale (default 24), 8,192 seeds in "
+                         "uneven batches of {1,7,32,100,256}, tpa_query per batch against CUDA-graph replays "
+                         "(tpa_server); one JSON line")
+    ap.add_argument("--serving-scale", type=int, default=24)
+    ap.add_argument("--serving-seeds", type=int, default=8192)
+    ap.add_argument("--adjoint", action="store_true",
+                    help="measure the gradient of the link-prediction loss instead: R-MAT scale 20, 8 edge "
+                         "features, 4,096 triples, K = the preprocessing count; one JSON line")
     ap.add_argument("--variant", action="append", default=[], metavar="NAME",
                     help="use the SpMV/SpMM variant NAME (e.g. 'seg<8,8,8>') for its padded width; repeatable")
     ap.add_argument("--profile-case", choices=["preprocess", "query8"], default=None,
                     help="run one small case for an ncu capture and exit (no JSON line): preprocessing of the "
                          "graph, or two 8-seed queries of light seeds after it")
     return ap.parse_args(argv)
+
+
+def event_time(torch, fn, reps: int) -> float:
+    """Seconds per call of fn (CUDA events on the current stream, after one warm-up call)."""
+    fn()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0 / reps
+
+
+def serving_study(args):
+    """Batched serving (Algorithm 3 per request, batched): the seed stream in
+    uneven batches answered by tpa_query per batch and by tpa_server replays;
+    every timed pass follows an untimed one over the same batches."""
+    import torch
+    import synth
+    import paper_1708_02574_gb300 as tpa
+    tpa.set_pattern(not args.valued_products)
+    apply_variants(tpa, args.variant)
+    sc = args.serving_scale
+    n = 1 << sc
+    src, dst = synth.rmat_edges(sc, args.edge_factor)
+    g = tpa.build_graph(n, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda())
+    tpa.preprocess(g, C, T, EPS)
+    cand = synth.nodes_with_out_edge(n, src, dst)
+    total = args.serving_seeds
+    seeds = synth.query_seeds(cand, total)
+    sizes = synth.batch_sizes(total)
+    m_raw = int(src.size)
+    del src, dst
+    batches, off = [], 0
+    for k in sizes:
+        batches.append(torch.from_numpy(seeds[off:off + k]).cuda())
+        off += k
+    srv = tpa.Server(g, S, max_k=max(sizes))
+    clocks = ClockSampler(nvsmi_device_id())
+    clocks.start()
+    res = {}
+    for name, run in (("direct", lambda b: tpa.query(g, b, S)), ("graphs", lambda b: srv.query(b))):
+        def stream_pass():
+            for b in batches:
+                run(b)
+        res[name] = total / event_time(torch, stream_pass, max(1, args.steps // 5))
+    clk = clocks.stop()
+    srv.sync()
+    tpa.sync(g)
+    st = srv.stats(256)
+    line = {"study": "batched_serving", "metric": "seeds/s (uneven request batches, CUDA-graph replays)",
+            "value": res["graphs"], "unit": "seeds/s", "higher_is_better": True, "data": "synthetic",
+            "dtype": "f32", "direct_tpa_query_seeds_per_s": res["direct"],
+            "graphs_over_direct": res["graphs"] / res["direct"],
+            "config": {"workload": f"{total} seeds in uneven batches of {{1,7,32,100,256}} on R-MAT scale {sc} "
+                                   f"(ef {args.edge_factor}), c={C} S={S} T={T}",
+                       "n": n, "m": g.m, "m_raw": m_raw, "batches": len(sizes), "max_k": max(sizes)},
+            "server": st, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    srv.free()
+    g.free()
+    return 0
+
+
+def adjoint_study(args):
+    """Gradient of the link-prediction loss on TPA scores w.r.t. the edge-weight
+    parameters: R-MAT scale 20, 8 features per edge ~ N(0,1), theta ~ N(0, 0.1^2),
+    4,096 (seed, positive, negative) triples, K = the preprocessing count on the
+    weighted graph.  One gradient = tpa_loss_grad + tpa_theta_grad."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1708_02574_gb300 as tpa
+    apply_variants(tpa, args.variant)
+    sc, ntrip, d = 20, 4096, 8
+    n = 1 << sc
+    src, dst = synth.rmat_edges(sc, 16)
+    g = tpa.build_graph(n, src, dst)
+    m = g.m
+    feat = torch.from_numpy(synth.edge_features(m, d)).cuda()
+    theta = torch.from_numpy(synth.theta(d)).cuda()
+    cand = synth.nodes_with_out_edge(n, src, dst)
+    seeds, pos, neg = synth.triples(n, src, dst, cand, ntrip)
+    w = tpa.edge_weights(feat, theta)
+    tpa.set_edge_weights(g, w)
+    tpa.preprocess(g, C, T, EPS)
+    K = max(int(tpa.get_stranger(g)[1]), T)
+    sd, ps, ng = (torch.from_numpy(x).cuda() for x in (seeds, pos, neg))
+
+    def grad():
+        _, gw = tpa.loss_grad(g, sd, ps, ng, C, S, T, K)
+        tpa.theta_grad(feat, w, gw)
+
+    def loss_only():
+        tpa.loss_grad(g, sd, ps, ng, C, S, T, K, want_grad=False)
+
+    clocks = ClockSampler(nvsmi_device_id())
+    clocks.start()
+    t_grad = event_time(torch, grad, max(3, args.steps // 2))
+    t_loss = event_time(torch, loss_only, max(3, args.steps // 2))
+    clk = clocks.stop()
+    # algorithmic bytes of one gradient: SpMVs over CSR(A~^T) and CSR(A~) at
+    # 8m + 20n (k = 1) or 8m + 4n + 16nk (k = 8), edge passes at 16m (SDDMM:
+    # row and column ids read, gradient read and written), the row Jacobian
+    # at 16m, the theta reduction at (8 + 4d)m
+    batches = (ntrip + 7) // 8
+    spmv = s8d_bytes(n, m, 1)
+    spmm = s8d_bytes(n, m, 8)
+    alg = (K * spmv + batches * ((S - 1) * spmm + (S - 2) * spmm + (S - 1) * 16.0 * m)
+           + K * spmv + K * 16.0 * m + 16.0 * m + (8.0 + 4.0 * d) * m)
+    hbm, peak_kind = peaks()
+    line = {"study": "adjoint", "metric": "gradients/s (loss + dL/dtheta over 4,096 triples)",
+            "value": 1.0 / t_grad, "unit": "gradients/s", "higher_is_better": True, "data": "synthetic",
+            "dtype": "f32 (fp64 reductions)", "ms_per_gradient": 1000.0 * t_grad,
+            "ms_loss_only": 1000.0 * t_loss, "triples_per_s": ntrip / t_grad, "K": K,
+            "config": {"workload": f"link-prediction loss gradient, {ntrip} triples, R-MAT scale {sc} (ef 16), "
+                                   f"{d} features, c={C} S={S} T={T}", "n": n, "m": m},
+            "roofline": {"bound": "hbm", "achieved": alg / t_grad / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / t_grad / 1e9 / hbm, "alg_bytes_per_gradient": alg,
+                         "peak_source": f"{peak_kind} hbm_gbs (copy)"},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    g.free()
+    return 0
 
 
 def apply_variants(tpa, names):
@@ -254,6 +390,39 @@ def ncu_traffic(variant: str, scale: int):
     return None
 
 
+def bench_config(args, n: int, m: int, m_raw: int, world: int = 1) -> dict:
+    """The workload a line measures; both arms print the same dict."""
+    Q = args.queries
+    return {"workload": workload(args), "graph": f"R-MAT scale {args.scale} ef {args.edge_factor}",
+            "n": n, "m": m, "m_raw": m_raw, "queries_per_rank": Q, "query_batch": args.batch if args.batch > 0 else Q,
+            "c": C, "S": S, "T": T, "eps": EPS, "parallelism": f"replicas x{world} (seed-sharded)",
+            "products": "valued" if args.valued_products else "pattern-only",
+            "l2": f"inputs larger than L2 (CSR {8 * m / 1e9:.1f} GB with values, scores {4 * n * Q / 1e9:.1f} GB "
+                  f"per step)"}
+
+
+def host_cpu() -> dict:
+    """Core count and model of this host (the oracle's timing is quoted with it)."""
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":")[0].strip().lower()
+            if k in ("model name", "cpu model", "hardware") and not model:
+                model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count() or 1, "model": model}
+
+
+def s8d_bytes(n: int, m: int, k: int) -> float:
+    """Algorithmic bytes of one SpMV (k = 1) or k-column SpMM over CSR(A~^T):
+    8m (column and value) + 20n for the SpMV, 8m + 4n + 16nk for the SpMM."""
+    return 8.0 * m + 20.0 * n if k == 1 else 8.0 * m + 4.0 * n + 16.0 * n * k
+
+
 # ------------------------------------------------------------ reference ---
 def run_reference(args):
     """FP64 oracle on the host cores, bounded sample of the same workload."""
@@ -280,41 +449,59 @@ def run_reference(args):
             times.append(dt + share)
     total = sum(times)
     value = len(times) / total
-    sample = (f"per step: 1 oracle TPA query (4 SpMV over m={og.m}) plus 1/{args.queries} of the oracle's "
-              f"measured CSR build ({t_build:.1f} s) and preprocessing ({t_pre:.1f} s, {pre_it} iterations)")
+    host = host_cpu()
+    sample = (f"oracle on {host['nproc']} OpenMP threads; per step: 1 oracle TPA query (4 SpMV over m={og.m}) "
+              f"plus 1/{args.queries} of the oracle's measured CSR build ({t_build:.1f} s) and preprocessing "
+              f"({t_pre:.1f} s, {pre_it} iterations)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload(args), "n": n, "m": og.m, "queries": args.queries},
-            "cpu_baseline": {"value": value, "unit": "seeds/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": bench_config(args, n, og.m, int(src.size), args.gpus),
+            "cpu_baseline": {"value": value, "unit": "seeds/s", "cores": host["nproc"], "kind": "oracle",
+                             "sample": sample, "host": host},
             "e2e": {"value": value, "unit": "seeds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- ours ---
 def cpu_baseline(args, src, dst, seeds, gpu_pre_iters):
-    """Time the oracle as it stands on a bounded sample: full CSR build, 3 preprocessing
-    iterations (scaled to the iteration count), 2 queries (scaled to the query count)."""
+    """Time the oracle as it stands on a bounded sample, on one host core and on
+    all of them (its loops over rows run on OpenMP threads; results are the
+    same bits): the CSR build, 3 preprocessing iterations (scaled to the
+    iteration count) and 2 queries (scaled to the query count).  `value` is
+    the all-core estimate."""
     import numpy as np
     import oracle
     n = 1 << args.scale
-    t0 = time.perf_counter()
-    og = oracle.build_graph(n, src, dst)
-    t_build = time.perf_counter() - t0
+    host = host_cpu()
     q = np.full(n, 1.0 / n)
-    t0 = time.perf_counter()
-    oracle.cpi(og, q, C, EPS, T, 3)
-    t_it = (time.perf_counter() - t0) / 3
     rs = np.zeros(n)
-    t0 = time.perf_counter()
-    for sd in seeds[:2]:
-        oracle.query(og, int(sd), C, S, T, rs, EPS)
-    t_q = (time.perf_counter() - t0) / 2
-    est = t_build + gpu_pre_iters * t_it + args.queries * t_q
-    return {"value": args.queries / est, "unit": "seeds/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle CSR build timed in full ({t_build:.1f} s); 3 preprocessing iterations timed "
-                       f"({t_it:.2f} s each) and scaled to {gpu_pre_iters}; 2 queries timed ({t_q:.2f} s each) "
-                       f"and scaled to {args.queries}")}
+    est = {}
+    try:
+        for cores in (1, host["nproc"]):
+            oracle.set_threads(cores)
+            t0 = time.perf_counter()
+            og = oracle.build_graph(n, src, dst)
+            t_build = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            oracle.cpi(og, q, C, EPS, T, 3)
+            t_it = (time.perf_counter() - t0) / 3
+            t0 = time.perf_counter()
+            for sd in seeds[:2]:
+                oracle.query(og, int(sd), C, S, T, rs, EPS)
+            t_q = (time.perf_counter() - t0) / 2
+            total = t_build + gpu_pre_iters * t_it + args.queries * t_q
+            est[cores] = (args.queries / total, t_build, t_it, t_q)
+            del og
+    finally:
+        oracle.set_threads(0)
+    one, allc = est[1], est[host["nproc"]]
+    return {"value": allc[0], "unit": "seeds/s", "cores": host["nproc"], "kind": "oracle", "host": host,
+            "single_core": {"value": one[0], "cores": 1},
+            "sample": (f"oracle on {host['nproc']} threads: CSR build timed in full ({allc[1]:.1f} s), 3 "
+                       f"preprocessing iterations ({allc[2]:.3f} s each) scaled to {gpu_pre_iters}, 2 queries "
+                       f"({allc[3]:.3f} s each) scaled to {args.queries}; on 1 thread {one[1]:.1f} s, "
+                       f"{one[2]:.3f} s and {one[3]:.3f} s")}
 
 
 def main(argv=None):
@@ -323,6 +510,10 @@ def main(argv=None):
         return profile_case(args)
     if args.accuracy:
         return accuracy_study(args)
+    if args.serving:
+        return serving_study(args)
+    if args.adjoint:
+        return adjoint_study(args)
     rank, world, local = dist_env()
     if args.impl == "reference":
         if rank == 0:
@@ -449,16 +640,25 @@ def main(argv=None):
         sp = stats.get(fam, {})
         if sp.get("total_ms", 0) <= 0:
             return None
-        achieved = sp["alg_bytes"] / (sp["total_ms"] / 1000.0) / 1e9
-        per_launch = sp["alg_bytes"] / max(1, sp["launches"])
-        variant = names.get(tpa.get_variant(int(fam[len("spmm_kp"):])), "?")
+        kp = int(fam[len("spmm_kp"):])
+        avg_s = sp["total_ms"] / 1000.0 / max(1, sp["launches"])
+        # the contract's bytes: 8m + 20n per SpMV, 8m + 4n + 16nk per k-column
+        # SpMM (every launch of the bench's chunks has k = kp columns)
+        per_launch = s8d_bytes(n, m, kp)
+        achieved = per_launch / avg_s / 1e9
+        moved = sp["alg_bytes"] / max(1, sp["launches"])   # what the kernel reads and writes itself
+        variant = names.get(tpa.get_variant(kp), "?")
         products = "valued" if args.valued_products else "pattern"
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": ncu_traffic(f"{variant}+{products}", args.scale), "variant": variant,
                 "products": products,
-                "kernel": f"{fam}: merge-path SpMV/SpMM over CSR(A~^T), {variant}, {products} products",
-                "launches": sp["launches"], "avg_launch_ms": sp["total_ms"] / max(1, sp["launches"]),
-                "alg_bytes_per_launch": per_launch, "peak_source": f"{peak_kind} hbm_gbs (copy), burst",
+                "kernel": f"{fam}: SpMV/SpMM over CSR(A~^T), {variant}, {products} products",
+                "launches": sp["launches"], "avg_launch_ms": 1000.0 * avg_s,
+                "alg_bytes_per_launch": per_launch,
+                "alg_bytes_rule": "8m + 20n (k = 1) or 8m + 4n + 16nk per launch, m after merging duplicates",
+                "moved_bytes_per_launch": moved, "achieved_moved": moved / avg_s / 1e9,
+                "frac_moved": moved / avg_s / 1e9 / hbm,
+                "peak_source": f"{peak_kind} hbm_gbs (copy), burst",
                 "kernel_share_of_step": sp["total_ms"] / (1000.0 * t_rank)}
 
     fams = [f for f in stats if f.startswith("spmm_kp")]
@@ -478,12 +678,7 @@ def main(argv=None):
         line = {"metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": workload(args), "graph": f"R-MAT scale {args.scale} ef {args.edge_factor}",
-                           "n": n, "m": m, "m_raw": int(src.size), "queries_per_rank": Q, "query_batch": batch,
-                           "c": C, "S": S, "T": T, "eps": EPS, "parallelism": f"replicas x{world} (seed-sharded)",
-                           "products": "valued" if args.valued_products else "pattern-only",
-                           "l2": f"inputs larger than L2 (CSR {8 * m / 1e9:.1f} GB with values, "
-                                 f"scores {4 * n * Q / 1e9:.1f} GB per step)"},
+                "config": bench_config(args, n, m, int(src.size), world),
                 "roofline": roof, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk,
                 "phases_ms": phases, "preprocess_iters": pre_iters,
@@ -548,16 +743,39 @@ def measure_e2e(args, tpa, torch, n, src, dst, seeds):
 
     step()
     torch.cuda.synchronize()
-    k = max(1, min(args.steps, 3))
+    k = max(3, args.steps)
     t0 = time.perf_counter()
     for _ in range(k):
         step()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    # what the host link gives a plain copy of the same bytes (the scores are
+    # written by the kernels straight into the pinned buffer instead)
+    link = {}
+    try:
+        dev = torch.empty((n, Q), dtype=torch.float32, device="cuda")
+        dev.fill_(1.0)
+        srcd = torch.empty(src.size, dtype=torch.int32, device="cuda")
+        stream = torch.cuda.current_stream()
+        for name, dst_t, src_t in (("d2h", out_h, dev), ("h2d", srcd, src_h)):
+            dst_t.copy_(src_t, non_blocking=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                dst_t.copy_(src_t, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            nbytes = src_t.numel() * src_t.element_size()
+            link[f"{name}_copy_gbs"] = 3 * nbytes / (e0.elapsed_time(e1) / 1000.0) / 1e9
+            link[f"{name}_copy_bytes"] = int(nbytes)
+        del dev, srcd
+    except RuntimeError as e:   # not enough device memory for the copy test
+        link = {"unavailable": str(e)[:200]}
     del out_h
-    return {"value": Q * k / dt, "unit": "seeds/s", "steps": k,
+    return {"value": Q * k / dt, "unit": "seeds/s", "steps": k, "ms_per_step": 1000.0 * dt / k,
             "h2d_bytes_per_step": int(src.nbytes + dst.nbytes + seeds.nbytes),
-            "d2h_bytes_per_step": int(4 * n * Q)}
+            "d2h_bytes_per_step": int(4 * n * Q), "host_link_plain_copy": link}
 
 
 if __name__ == "__main__":

@@ -38,3 +38,29 @@ def test_workload_label_follows_arguments():
         "TPA preprocessing + 1000 single-seed queries on R-MAT scale 22 (ef 16), c=0.15 S=5 T=10 eps=1e-9")
     a = bench.parse_args(["--scale", "26", "--edge-factor", "28", "--queries", "64"])
     assert "64 single-seed queries on R-MAT scale 26 (ef 28)" in bench.workload(a)
+
+
+def test_reference_arm_config_matches_ours():
+    """Both arms print the same config dict (bench_config), and the reference
+    arm names the host it ran on."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--scale", "10",
+           "--queries", "20", "--steps", "3", "--warmup", "3"]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT)
+    d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
+    args = bench.parse_args(["--scale", "10", "--queries", "20"])
+    mine = bench.bench_config(args, d["config"]["n"], d["config"]["m"], d["config"]["m_raw"], 1)
+    assert d["config"] == mine
+    host = d["cpu_baseline"]["host"]
+    assert host["nproc"] >= 1 and isinstance(host["model"], str)
+
+
+def test_contract_bytes():
+    """8m + 20n per SpMV and 8m + 4n + 16nk per k-column SpMM."""
+    sys.path.insert(0, ROOT)
+    import bench
+    n, m = 4_194_304, 65_243_475
+    assert bench.s8d_bytes(n, m, 1) == 8 * m + 20 * n
+    assert bench.s8d_bytes(n, m, 8) == 8 * m + 4 * n + 16 * n * 8
+    assert abs(bench.s8d_bytes(n, m, 8) / 1e9 - 1.0756) < 1e-3
