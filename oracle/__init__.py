@@ -106,20 +106,24 @@ class Graph:
     outdeg: np.ndarray  # int32[n]
 
 
-def build_graph(n: int, src: np.ndarray, dst: np.ndarray) -> Graph:
+def build_graph(n: int, src: np.ndarray, dst: np.ndarray, with_a: bool = True) -> Graph:
+    """orc_build: both CSRs of A~ (with_a=False: CSR(A~^T) alone, the CSR(A~)
+    fields then None -- enough for Algorithms 1-3 on very large graphs)."""
     lib = _load()
     src = np.ascontiguousarray(src, dtype=np.int32)
     dst = np.ascontiguousarray(dst, dtype=np.int32)
     mi = src.size
     rp_t = np.empty(n + 1, np.int64); col_t = np.empty(max(mi, 1), np.int32); val_t = np.empty(max(mi, 1))
-    rp_a = np.empty(n + 1, np.int64); col_a = np.empty(max(mi, 1), np.int32); val_a = np.empty(max(mi, 1))
+    rp_a = col_a = val_a = None
+    if with_a:
+        rp_a = np.empty(n + 1, np.int64); col_a = np.empty(max(mi, 1), np.int32); val_a = np.empty(max(mi, 1))
     outdeg = np.empty(n, np.int32)
     m = lib.orc_build(n, mi, _p(src), _p(dst), _p(rp_t), _p(col_t), _p(val_t),
                       _p(rp_a), _p(col_a), _p(val_a), _p(outdeg))
     if m < 0:
         raise ValueError("orc_build rejected the edge list")
-    return Graph(n, int(m), rp_t, col_t[:m].copy(), val_t[:m].copy(), rp_a, col_a[:m].copy(),
-                 val_a[:m].copy(), outdeg)
+    return Graph(n, int(m), rp_t, col_t[:m], val_t[:m], rp_a, None if col_a is None else col_a[:m],
+                 None if val_a is None else val_a[:m], outdeg)
 
 
 def cpi(g: Graph, q: np.ndarray, c: float, eps: float, s_iter: int, t_iter: int | None,

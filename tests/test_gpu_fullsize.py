@@ -191,11 +191,12 @@ def test_scale24_server_stream(full24):
 # ---------------------------------------------------------------------------
 # Billion-edge graph: R-MAT scale 26, edge factor 28 (67,108,864 nodes,
 # 1,879,048,192 raw edges, key 1), preprocessing and one batch of 64 queries
-# (seeds uniform over nodes with an out-edge, key 2).  The FP64 oracle cannot
-# run at this size, so the checks are properties that hold at any size:
-# CSR invariants and sampled rows against the raw edge list, bounds of
-# Lemma 2 / Theorem 2 on r~_stranger and r_TPA, push against pull branch, and
-# batched against single-seed queries.
+# (seeds uniform over nodes with an out-edge, key 2).  Properties that hold at
+# any size (CSR invariants and sampled rows against the raw edge list, bounds
+# of Lemma 2 / Theorem 2, push against pull branch, batched against
+# single-seed), and the FP64 oracle on the host's cores (CSR(A~^T) only,
+# about 25 GB of host memory): the whole r~_stranger vector and sampled query
+# columns element-wise at L1 <= 1e-5 and max-abs <= 1e-7.
 
 SCALE26, EF26, SEEDS26 = 26, 28, 64
 
@@ -278,3 +279,30 @@ def test_scale26_batched_queries(big26):
     one = tpa.query(g, seeds[5:6], S)
     d1 = (one[:, 0].double() - out[:, 5].double()).abs()
     assert float(d1.sum()) <= 1e-5 and float(d1.max()) <= 1e-7
+
+
+@pytest.fixture(scope="module")
+def oracle26(big26):
+    og = oracle.build_graph(big26["n"], big26["s"], big26["d"], with_a=False)
+    rs, it = oracle.preprocess(og, C, T, EPS)
+    return dict(og=og, rs=rs, it=it)
+
+
+def test_scale26_preprocess_oracle(big26, oracle26):
+    """Algorithm 2 on the billion-edge graph: GPU FP32 against the FP64 oracle."""
+    tpa = big26["tpa"]
+    assert big26["g"].m == oracle26["og"].m
+    r, it = tpa.get_stranger(big26["g"])
+    parity(r.cpu().numpy(), oracle26["rs"], "r_stranger scale 26")
+    assert abs(it - oracle26["it"]) <= 1
+
+
+def test_scale26_query_columns_oracle(big26, oracle26):
+    """Algorithm 3 on the billion-edge graph: the first and last columns of the
+    64-seed batch against the FP64 oracle."""
+    tpa = big26["tpa"]
+    seeds = big26["seeds"]
+    out = tpa.query(big26["g"], seeds, S)
+    for j in (0, len(seeds) - 1):
+        ref = oracle.query(oracle26["og"], int(seeds[j]), C, S, T, oracle26["rs"], EPS)
+        parity(out[:, j].cpu().numpy(), ref, f"scale 26 column {j} seed {seeds[j]}")
