@@ -326,18 +326,24 @@ static int64_t launch_spmvp(const Params &p, cudaStream_t s)
     return grid * WARPS;
 }
 
-// Segmented flag walk (spmm_seg.cuh): persistent grid of at most the
-// kernel's occupancy times the SM count, launched cooperatively (its waits
-// need every CTA resident); returns the CTAs launched (rows of the L1
-// partial buffer).
-template <int V, int R, int PF, int NB>
+// Segmented flag walk (spmm_seg.cuh; AHEAD: the gathers-ahead kernel):
+// persistent grid of at most the kernel's occupancy times the SM count,
+// launched cooperatively (its waits need every CTA resident); returns the
+// CTAs launched (rows of the L1 partial buffer).
+template <int V, int R, int PF, int NB, bool AHEAD>
 static int64_t launch_seg(const Params &p, cudaStream_t s)
 {
-    constexpr size_t smem_v = SegSmem<V, R, NB, false>::BYTES;
-    constexpr size_t smem_p = SegSmem<V, R, NB, true>::BYTES;
+    constexpr size_t smem_v = AHEAD ? SegaSmem<V, R, NB, false>::BYTES : SegSmem<V, R, NB, false>::BYTES;
+    constexpr size_t smem_p = AHEAD ? SegaSmem<V, R, NB, true>::BYTES : SegSmem<V, R, NB, true>::BYTES;
     static_assert(smem_v <= 200 * 1024 && smem_p <= 200 * 1024, "shared memory per block");
-    auto *const valued = spmm_seg_k<V, R, PF, NB, false>;
-    auto *const pattern = spmm_seg_k<V, R, PF, NB, true>;
+    void (*valued)(Params), (*pattern)(Params);
+    if constexpr (AHEAD) {
+        valued = spmm_sega_k<V, R, PF, NB, false>;
+        pattern = spmm_sega_k<V, R, PF, NB, true>;
+    } else {
+        valued = spmm_seg_k<V, R, PF, NB, false>;
+        pattern = spmm_seg_k<V, R, PF, NB, true>;
+    }
     static int per_sm_v = 0, per_sm_p = 0;
     if (!per_sm_v) {
         TPA_CUDA(cudaFuncSetAttribute(valued, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v));
@@ -476,7 +482,9 @@ struct Variant {
     {{G, V, I, PF, 32}, launch_spmvg<G, V, I, PF, 8>, launch_fix<G * V>, "walker<" #G "," #V "," #I "," #PF ">"}
 #define TPA_VARIANTB(KP) {{1, KP, 4, 4, 32}, launch_binned<KP>, launch_bin_finish<KP>, "bins<" #KP ">", true}
 #define TPA_VARIANTS(V, R, PF, NB) \
-    {{1, V, R, PF, 32}, launch_seg<V, R, PF, NB>, nullptr, "seg<" #V "," #R "," #PF "," #NB ">", false, true}
+    {{1, V, R, PF, 32}, launch_seg<V, R, PF, NB, false>, nullptr, "seg<" #V "," #R "," #PF "," #NB ">", false, true}
+#define TPA_VARIANTA(V, R, PF, NB) \
+    {{1, V, R, PF, 32}, launch_seg<V, R, PF, NB, true>, nullptr, "sega<" #V "," #R "," #PF "," #NB ">", false, true}
 #define TPA_VARIANTP(G, V, I, PF, W, MB)                                 \
     {{G, V, I, PF, 32}, launch_spmvp<G, V, I, PF, W, MB>, launch_fix<G * V>, \
      "pipe<" #G "," #V "," #I "," #PF "," #W "," #MB ">"}
@@ -492,13 +500,12 @@ static const Variant kVariants[] = {
     TPA_VARIANTS(2, 8, 8, 3),
     TPA_VARIANTS(4, 8, 8, 3),
     TPA_VARIANTS(8, 8, 4, 2),
-    TPA_VARIANTS(1, 16, 16, 2),
     TPA_VARIANTS(1, 4, 4, 4),
-    TPA_VARIANTS(2, 4, 4, 4),
-    TPA_VARIANTS(4, 4, 4, 4),
-    TPA_VARIANTS(8, 4, 4, 4),
     TPA_VARIANTS(8, 8, 8, 2),
-    TPA_VARIANTS(8, 4, 4, 2),
+    TPA_VARIANTA(1, 8, 8, 2),
+    TPA_VARIANTA(2, 8, 8, 2),
+    TPA_VARIANTA(4, 8, 8, 2),
+    TPA_VARIANTA(8, 8, 4, 2),
     TPA_VARIANT(8, 4, 16, 8),
     TPA_VARIANT(16, 4, 16, 8),
     TPA_VARIANT(32, 4, 32, 8),

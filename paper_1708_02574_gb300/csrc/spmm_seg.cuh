@@ -268,28 +268,11 @@ __device__ __forceinline__ void seg_issue(const Params &p, unsigned char *stage,
     if constexpr (!PAT) bulk_g2s(stage + CB, p.val + t * SM::TN, CB, bar);
 }
 
-template <int V, int R, int PF, int NB, bool PAT>
-__global__ void __launch_bounds__(SEG_WARPS * 32) spmm_seg_k(Params p)
+// Rows of y that the walk never writes but that must read as zero: the
+// empty seed rows (zero_mode 1) or every empty row (zero_mode 2).
+template <int V>
+__device__ __forceinline__ void seg_zero_rows(const Params &p)
 {
-    using SM = SegSmem<V, R, NB, PAT>;
-    static_assert(R % 4 == 0 && R % PF == 0 && R <= 32, "R");
-    static_assert(V == 1 || V == 2 || V == 4 || V == 8, "V");
-    constexpr int TN = SM::TN;
-    extern __shared__ __align__(128) unsigned char seg_smem[];
-    __shared__ double s_fin[256];
-    __shared__ float s_l1[SEG_WARPS][V];
-    __shared__ int s_last;
-    const CtlView cv = ctl_view(p.ctl);
-    if (gate_off(p.gate, p.ctl) || *(volatile int32_t *)&cv.hdr->done) return;
-    const uint32_t ep_raw = *(volatile uint32_t *)&cv.hdr->epoch;
-    const uint32_t ep = (ep_raw + 1u) & 0x7fffffffu;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned FULL = 0xffffffffu;
-    unsigned char *wbase = seg_smem + (size_t)warp * SM::PER_WARP;
-    float *rs = reinterpret_cast<float *>(wbase + NB * SM::STAGE);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(wbase + NB * SM::STAGE + SM::RS);
-
-    // rows of y that the walk never writes but that must read as zero
     if (p.zero_mode == 1) {
         for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p.zk; j += gridDim.x * blockDim.x) {
             const int64_t s = p.zseeds[j];
@@ -309,6 +292,78 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) spmm_seg_k(Params p)
             st_row<V>(p.y + (int64_t)p.empty_rows[i] * V, z);
         }
     }
+}
+
+// End of a segmented launch: the CTA's L1 partial; the last CTA to finish
+// sums the partials in a fixed order and applies the break test of
+// Algorithm 1 per column, then opens the next launch's epoch.
+template <int V>
+__device__ __forceinline__ void seg_close_launch(const Params &p, const CtlView &cv, const float (&l1)[V],
+                                                 uint32_t ep_raw, int lane, int warp)
+{
+    __shared__ double s_fin[256];
+    __shared__ float s_l1[SEG_WARPS][V];
+    __shared__ int s_last;
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        float a = l1[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(FULL, a, o);
+        if (lane == 0) s_l1[warp][j] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < V) {
+        float a = 0.0f;
+#pragma unroll
+        for (int w = 0; w < SEG_WARPS; ++w) a += s_l1[w][threadIdx.x];
+        p.part[(int64_t)blockIdx.x * V + threadIdx.x] = (double)a;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&cv.hdr->ticket, 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    block_sum_partials<V>(p.part, gridDim.x, s_fin);
+    if (threadIdx.x < V) {
+        const int c = threadIdx.x;
+        const double a = s_fin[c];
+        if (c < p.k && cv.alive[c]) {
+            cv.norm[c] = a;
+            cv.iters[c] = p.iter;
+            if (a < p.eps && p.mode == MODE_ACC) cv.alive[c] = 0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int c = 0; c < p.k && c < V; ++c) any |= cv.alive[c];
+        cv.hdr->done = any ? 0 : 1;
+        cv.hdr->ticket = 0;
+        cv.hdr->epoch = ep_raw + 1u;
+    }
+}
+
+template <int V, int R, int PF, int NB, bool PAT>
+__global__ void __launch_bounds__(SEG_WARPS * 32) spmm_seg_k(Params p)
+{
+    using SM = SegSmem<V, R, NB, PAT>;
+    static_assert(R % 4 == 0 && R % PF == 0 && R <= 32, "R");
+    static_assert(V == 1 || V == 2 || V == 4 || V == 8, "V");
+    constexpr int TN = SM::TN;
+    extern __shared__ __align__(128) unsigned char seg_smem[];
+    const CtlView cv = ctl_view(p.ctl);
+    if (gate_off(p.gate, p.ctl) || *(volatile int32_t *)&cv.hdr->done) return;
+    const uint32_t ep_raw = *(volatile uint32_t *)&cv.hdr->epoch;
+    const uint32_t ep = (ep_raw + 1u) & 0x7fffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned FULL = 0xffffffffu;
+    unsigned char *wbase = seg_smem + (size_t)warp * SM::PER_WARP;
+    float *rs = reinterpret_cast<float *>(wbase + NB * SM::STAGE);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(wbase + NB * SM::STAGE + SM::RS);
+
+    seg_zero_rows<V>(p);
 
     unsigned amask = 0;
     float l1[V];
@@ -553,46 +608,387 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) spmm_seg_k(Params p)
         }
     }
 
-    // L1 partial of the CTA; the last CTA to finish sums the partials in a fixed
-    // order and applies the break test of Algorithm 1 per column
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-        float a = l1[j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(FULL, a, o);
-        if (lane == 0) s_l1[warp][j] = a;
+    seg_close_launch<V>(p, cv, l1, ep_raw, lane, warp);
+}
+
+// ------------------------------------- segmented walk, gathers ahead ---
+// The same walk with the gathers of a warp's next tile in flight while its
+// current tile is summed: each lane copies the rows X[col] of its R nonzeros
+// of the next tile into a shared-memory buffer with cp.async, which holds no
+// register while the copies fly (two buffers per warp).  The walk then reads
+// its rows from shared memory.  A row sum that a lane finishes is parked in
+// the cell of a nonzero the lane has already consumed, and a table of cell
+// positions (slot -> cell) lets the coalesced pass find the finished rows.
+//
+// Cell layout: the row of nonzero i of lane l is cell i*32 + l; a row of
+// V <= 4 floats is one 4V-byte cell, a row of 8 floats two 16-byte halves TN
+// cells apart, so the 16-byte reads of consecutive lanes hit consecutive
+// banks.
+template <int V, int R, int NB, bool PAT>
+struct SegaSmem {
+    static constexpr int TN = 32 * R;
+    static constexpr size_t STAGE = (size_t)TN * sizeof(uint32_t) * (PAT ? 1 : 2);
+    static constexpr size_t XB = (size_t)TN * V * sizeof(float);
+    static constexpr size_t POS = (size_t)TN * sizeof(uint16_t);
+    static constexpr size_t PER_WARP = NB * STAGE + 2 * XB + POS + 16 * NB;
+    static constexpr size_t BYTES = SEG_WARPS * PER_WARP;
+    static_assert(STAGE % 16 == 0 && XB % 16 == 0 && POS % 16 == 0, "16-byte sections");
+};
+
+template <int V, int TN>
+__device__ __forceinline__ void sega_ld(const float *xb, int c, float (&o)[V])
+{
+    if constexpr (V == 8) {
+        const float4 a = reinterpret_cast<const float4 *>(xb)[c];
+        const float4 b = reinterpret_cast<const float4 *>(xb)[TN + c];
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+        o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+    } else {
+        ld_row_smem<V>(xb + c * V, o);
     }
-    __syncthreads();
-    if (threadIdx.x < V) {
-        float a = 0.0f;
-#pragma unroll
-        for (int w = 0; w < SEG_WARPS; ++w) a += s_l1[w][threadIdx.x];
-        p.part[(int64_t)blockIdx.x * V + threadIdx.x] = (double)a;
+}
+
+template <int V, int TN>
+__device__ __forceinline__ void sega_st(float *xb, int c, const float (&v)[V])
+{
+    if constexpr (V == 8) {
+        reinterpret_cast<float4 *>(xb)[c] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4 *>(xb)[TN + c] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+        st_row<V>(xb + c * V, v);
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&cv.hdr->ticket, 1) == (int)gridDim.x - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    block_sum_partials<V>(p.part, gridDim.x, s_fin);
-    if (threadIdx.x < V) {
-        const int c = threadIdx.x;
-        const double a = s_fin[c];
-        if (c < p.k && cv.alive[c]) {
-            cv.norm[c] = a;
-            cv.iters[c] = p.iter;
-            if (a < p.eps && p.mode == MODE_ACC) cv.alive[c] = 0;
+}
+
+// cp.async of one row of V floats (global, 4V-byte aligned) into cell c.
+template <int V, int TN>
+__device__ __forceinline__ void sega_fetch(float *xb, int c, const float *src)
+{
+    const unsigned d = smem_u32(xb);
+    if constexpr (V == 8) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d + c * 16), "l"(src) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d + (TN + c) * 16), "l"(src + 4) : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d + c * V * 4), "l"(src), "n"(V * 4)
+                     : "memory");
+    }
+}
+
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cpa_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Take tile t from its stage: wait (bounded) for the stage, read the lane's
+// R column words (and values), return the row-start flags of its existing
+// nonzeros in fm, and send the gathers of their rows into buffer xb as one
+// commit group.  False (the error flag raised) when the stage never arrived.
+template <int V, int R, bool PAT>
+__device__ __forceinline__ bool sega_take(const Params &p, const unsigned char *stage, uint64_t *bar,
+                                          unsigned parity, Ctl *hdr, int64_t t, float *xb, int lane, unsigned &fm,
+                                          float (&vv)[PAT ? 1 : R])
+{
+    constexpr int TN = 32 * R;
+    if (!__all_sync(0xffffffffu, mbar_wait(bar, parity, hdr))) return false;
+    uint32_t cw[R];
+#pragma unroll
+    for (int q = 0; q < R / 4; ++q) {
+        const uint4 c = reinterpret_cast<const uint4 *>(stage)[lane * (R / 4) + q];
+        cw[4 * q] = c.x;
+        cw[4 * q + 1] = c.y;
+        cw[4 * q + 2] = c.z;
+        cw[4 * q + 3] = c.w;
+        if constexpr (!PAT) {
+            const float4 v4 = reinterpret_cast<const float4 *>(stage + TN * sizeof(uint32_t))[lane * (R / 4) + q];
+            vv[4 * q] = v4.x;
+            vv[4 * q + 1] = v4.y;
+            vv[4 * q + 2] = v4.z;
+            vv[4 * q + 3] = v4.w;
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int any = 0;
-        for (int c = 0; c < p.k && c < V; ++c) any |= cv.alive[c];
-        cv.hdr->done = any ? 0 : 1;
-        cv.hdr->ticket = 0;
-        cv.hdr->epoch = ep_raw + 1u;
+    const int64_t left = p.m - (t * TN + (int64_t)lane * R);
+    const unsigned vm = left >= R ? (R == 32 ? 0xffffffffu : (1u << R) - 1u) : left > 0 ? (1u << left) - 1u : 0u;
+    unsigned f = 0;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        f |= (cw[i] >> 31) << i;
+        if ((vm >> i) & 1u) sega_fetch<V, TN>(xb, i * 32 + lane, p.x + (int64_t)(cw[i] & ~SEG_ROW_START) * V);
     }
+    fm = f & vm;
+    cpa_commit();
+    return true;
+}
+
+template <int V, int R, int PF, int NB, bool PAT>
+__global__ void __launch_bounds__(SEG_WARPS * 32) spmm_sega_k(Params p)
+{
+    using SM = SegaSmem<V, R, NB, PAT>;
+    static_assert(R % 4 == 0 && R % PF == 0 && R <= 32 && NB >= 2, "R");
+    static_assert(V == 1 || V == 2 || V == 4 || V == 8, "V");
+    static_assert(SM::TN <= 65536, "cell index in 16 bits");
+    constexpr int TN = SM::TN;
+    constexpr int XBF = (int)(SM::XB / sizeof(float));
+    extern __shared__ __align__(128) unsigned char seg_smem[];
+    const CtlView cv = ctl_view(p.ctl);
+    if (gate_off(p.gate, p.ctl) || *(volatile int32_t *)&cv.hdr->done) return;
+    const uint32_t ep_raw = *(volatile uint32_t *)&cv.hdr->epoch;
+    const uint32_t ep = (ep_raw + 1u) & 0x7fffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned FULL = 0xffffffffu;
+    unsigned char *wbase = seg_smem + (size_t)warp * SM::PER_WARP;
+    float *xbuf = reinterpret_cast<float *>(wbase + NB * SM::STAGE);
+    uint16_t *pos = reinterpret_cast<uint16_t *>(wbase + NB * SM::STAGE + 2 * SM::XB);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(wbase + NB * SM::STAGE + 2 * SM::XB + SM::POS);
+
+    seg_zero_rows<V>(p);
+
+    unsigned amask = 0;
+    float l1[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        amask |= (cv.alive[j] ? 1u : 0u) << j;
+        l1[j] = 0.0f;
+    }
+    int alive[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) alive[j] = (amask >> j) & 1u;
+
+    const int64_t nw = (int64_t)gridDim.x * SEG_WARPS;
+    const int64_t t0 = (int64_t)blockIdx.x * SEG_WARPS + warp;
+    const int64_t mine = t0 < p.seg_tiles ? (p.seg_tiles - 1 - t0) / nw + 1 : 0;   // tiles of this warp
+    if (lane == 0) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) mbar_init(bars + b);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (b < mine) seg_issue<V, R, NB, PAT>(p, wbase + b * SM::STAGE, bars + b, t0 + b * nw);
+    }
+    __syncwarp();
+    int32_t crow_next = mine > 0 ? __ldg(p.tile_crow0 + t0) : 0;
+
+    bool pend = false;
+    int64_t pend_t = 0;
+    int32_t pend_row = 0;
+    float pend_part[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) pend_part[j] = 0.0f;
+
+    // the warp's first tile: flags, values and gathers
+    unsigned fm = 0;
+    float vv[PAT ? 1 : R];
+    int64_t broke_at = -1;   // index of the warp tile whose stage never arrived
+    if (mine > 0) {
+        if (!sega_take<V, R, PAT>(p, wbase, bars, 0u, cv.hdr, t0, xbuf, lane, fm, vv)) {
+            broke_at = 0;
+        } else {
+            __syncwarp();
+            if (lane == 0 && NB < mine) seg_issue<V, R, NB, PAT>(p, wbase, bars, t0 + NB * nw);
+        }
+    }
+
+    int it = 0;
+    for (int64_t t = t0; broke_at < 0 && t < p.seg_tiles; t += nw, ++it) {
+        float *xb = xbuf + (it & 1) * XBF;
+        const int64_t crow0 = crow_next;
+        if (t + nw < p.seg_tiles) crow_next = __ldg(p.tile_crow0 + t + nw);
+        unsigned long long probe = 0ull;
+        if (pend && lane < V) probe = ld_relaxed_u64(p.agg + (pend_t - 1) * V + lane);
+
+        // 1. the next tile's gathers go out before this one is summed
+        unsigned fm_nx = 0;
+        float vv_nx[PAT ? 1 : R];
+        if (it + 1 < mine) {
+            const int k = it + 1, b = k % NB;
+            if (!sega_take<V, R, PAT>(p, wbase + b * SM::STAGE, bars + b, (unsigned)(k / NB) & 1u, cv.hdr, t + nw,
+                                      xbuf + (k & 1) * XBF, lane, fm_nx, vv_nx)) {
+                cpa_wait<0>();
+                broke_at = k;
+                break;
+            }
+            __syncwarp();   // every lane has its words: the stage takes the warp's tile NB rounds ahead
+            if (lane == 0 && k + NB < mine) seg_issue<V, R, NB, PAT>(p, wbase + b * SM::STAGE, bars + b, t + (NB + 1) * nw);
+        } else {
+            cpa_commit();   // an empty group: one group per tile
+        }
+        cpa_wait<1>();      // this lane's rows of tile t have landed
+
+        const bool full = (t + 1) * TN <= p.m;
+        const int64_t left = p.m - (t * TN + (int64_t)lane * R);
+        const unsigned vm = left >= R ? (R == 32 ? FULL : (1u << R) - 1u) : left > 0 ? (1u << left) - 1u : 0u;
+        const int nf = __popc(fm);
+        int incl = nf;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - nf;
+        const int q = __shfl_sync(FULL, incl, 31);
+        // ids (and pattern-only weights) of the rows the coalesced pass finishes, loaded early
+        const int32_t vk = lane < q - 1 ? __ldg(p.nz_rows + crow0 + lane) : 0;
+        const float wk = (PAT && p.mode == MODE_ACC && lane < q - 1) ? __ldg(p.inv_deg + vk) : 0.0f;
+
+        // 2. the walk over the rows in shared memory: at a row start the
+        //    running sum is parked in the cell of the lane's previous nonzero
+        float acc[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) acc[j] = 0.0f;
+        int seen = 0;   // row starts passed in this lane
+#pragma unroll
+        for (int c0 = 0; c0 < R; c0 += PF) {
+            float xv[PF][V];
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int i = c0 + u;
+                sega_ld<V, TN>(xb, i * 32 + lane, xv[u]);
+                if (!full && !((vm >> i) & 1u)) {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) xv[u][j] = 0.0f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int i = c0 + u;
+                const bool f = (fm >> i) & 1u;
+                if (i > 0 && f) {
+                    sega_st<V, TN>(xb, (i - 1) * 32 + lane, acc);
+                    if (seen > 0) pos[excl + seen - 1] = (uint16_t)((i - 1) * 32 + lane);
+                }
+                seen += f ? 1 : 0;
+                const float keep = f ? 0.0f : 1.0f;
+                if constexpr (PAT) {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) acc[j] = fmaf(acc[j], keep, xv[u][j]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) acc[j] = fmaf(vv[i], xv[u][j], acc[j] * keep);
+                }
+            }
+        }
+
+        // 3. segmented scan of the lanes' trailing sums (as in spmm_seg_k)
+        int key = nf > 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            float up[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) up[j] = __shfl_up_sync(FULL, acc[j], o);
+            const int kup = __shfl_up_sync(FULL, key, o);
+            if (lane >= o) {
+                if (!key) {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) acc[j] += up[j];
+                }
+                key |= kup;
+            }
+        }
+        // the row that ends at this lane's first row start: its part in this
+        // lane (cell of the nonzero before the start; none when the start is
+        // the lane's first nonzero, whose sum then parks in the lane's last
+        // cell, never a parking cell) plus what earlier lanes hold
+        {
+            float cin[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                cin[j] = __shfl_up_sync(FULL, acc[j], 1);
+                if (lane == 0) cin[j] = 0.0f;
+            }
+            if (nf > 0) {
+                const int i0 = __ffs(fm) - 1;
+                const int c = (i0 > 0 ? i0 - 1 : R - 1) * 32 + lane;
+                float h[V];
+                if (i0 > 0) {
+                    sega_ld<V, TN>(xb, c, h);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) h[j] = 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < V; ++j) h[j] += cin[j];
+                sega_st<V, TN>(xb, c, h);
+                pos[excl > 0 ? excl - 1 : TN - 1] = (uint16_t)c;
+            }
+        }
+        // carry-out of the tile, tagged with this launch and whether a row starts in it
+        if (lane == 31) {
+            const uint32_t tag = (ep << 1) | (q > 0 ? 1u : 0u);
+#pragma unroll
+            for (int j = 0; j < V; ++j) st_relaxed_u64(p.agg + t * V + j, seg_pack(acc[j], tag));
+        }
+        __syncwarp();
+
+        // 4. the pending row of the warp's previous tile
+        if (pend) {
+            float back[V];
+            const unsigned long long w = lane < V ? probe : 0ull;
+            const bool ready = __all_sync(FULL, lane >= V || (uint32_t)(w >> 33) == ep);
+            const bool start = __shfl_sync(FULL, (int)((w >> 32) & 1ull), 0) != 0;
+            if (ready && start) {
+#pragma unroll
+                for (int j = 0; j < V; ++j) back[j] = __shfl_sync(FULL, __uint_as_float((uint32_t)w), j);
+            } else {
+                seg_lookback<V>(p, pend_t, ep, cv.hdr, lane, back);
+            }
+            if (lane == 0) {
+                float tot[V];
+#pragma unroll
+                for (int j = 0; j < V; ++j) tot[j] = pend_part[j] + back[j];
+                seg_emit<V, PAT>(p, (int64_t)pend_row, tot, alive, l1);
+            }
+            pend = false;
+        }
+        const bool last = t == p.seg_tiles - 1;
+        if ((q > 0 && t > 0) || (q == 0 && last)) {
+            if (q > 0) {
+                sega_ld<V, TN>(xb, pos[TN - 1], pend_part);
+            } else {
+#pragma unroll
+                for (int j = 0; j < V; ++j) pend_part[j] = __shfl_sync(FULL, acc[j], 31);
+            }
+            pend = true;
+            pend_t = t;
+            pend_row = __ldg(p.nz_rows + crow0 - 1);
+        }
+
+        // 5. rows that start and end in the tile: lane per row, coalesced
+        if (lane < q - 1) {
+            float sv[V];
+            sega_ld<V, TN>(xb, pos[lane], sv);
+            seg_emit_w<V, PAT>(p, (int64_t)vk, sv, alive, l1, wk);
+        }
+        for (int k = lane + 32; k < q - 1; k += 32) {
+            float sv[V];
+            sega_ld<V, TN>(xb, pos[k], sv);
+            seg_emit<V, PAT>(p, (int64_t)__ldg(p.nz_rows + crow0 + k), sv, alive, l1);
+        }
+        // 6. the last row that starts in the last tile ends with the matrix
+        if (last && q > 0 && lane == 31) seg_emit<V, PAT>(p, (int64_t)__ldg(p.nz_rows + crow0 + q - 1), acc, alive, l1);
+        fm = fm_nx;
+        if constexpr (!PAT) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) vv[i] = vv_nx[i];
+        }
+        __syncwarp();   // the buffer and the cell table are rewritten two tiles on
+    }
+    if (broke_at >= 0) {   // a stage never arrived: wait (bounded) for the copies still in flight before leaving
+        for (int64_t k = broke_at; k < broke_at + NB && k < mine; ++k)
+            mbar_wait(bars + k % NB, (unsigned)(k / NB) & 1u, cv.hdr);
+        pend = false;
+    }
+    if (pend) {
+        float back[V];
+        seg_lookback<V>(p, pend_t, ep, cv.hdr, lane, back);
+        if (lane == 0) {
+            float tot[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) tot[j] = pend_part[j] + back[j];
+            seg_emit<V, PAT>(p, (int64_t)pend_row, tot, alive, l1);
+        }
+    }
+    seg_close_launch<V>(p, cv, l1, ep_raw, lane, warp);
 }
 
 // The TPA finalize r_TPA = (1+alpha) r_family + r~_stranger for the rows the

@@ -131,3 +131,48 @@ def test_variant_preprocess(rmat12, forced, pattern):
     r, it = t.get_stranger(rmat12["g"])
     parity(r.cpu().numpy(), rmat12["rs"], f"{forced['name']} r_stranger")
     assert abs(it - rmat12["it"]) <= 1
+
+
+@pytest.fixture(scope="module")
+def rmat17():
+    n = 1 << 17
+    s, d = synth.rmat_edges(17, 16)
+    og = oracle.build_graph(n, s, d)
+    g = tpa().build_graph(n, s, d)
+    rs, it = oracle.preprocess(og, C, T, EPS)
+    return dict(n=n, og=og, g=g, rs=rs, it=it, cand=synth.nodes_with_out_edge(n, s, d))
+
+
+def segmented_ids():
+    try:
+        return [v["index"] for v in tpa().variants() if v["name"].startswith("seg")]
+    except Exception:
+        return [0]
+
+
+@pytest.mark.parametrize("forced", segmented_ids(), indirect=True)
+def test_segmented_walk_many_tiles_per_warp(rmat17, forced, pattern):
+    """R-MAT scale 17 (about 2 million nonzeros): every warp of the persistent
+    segmented grid walks several tiles, so the stage ring, the gathers sent
+    one tile ahead, the deferred rows and the look-back across warps all run."""
+    t = tpa()
+    kp = forced["kp"]
+    if kp == 1:
+        t.preprocess(rmat17["g"], C, T, EPS)
+        r, it = t.get_stranger(rmat17["g"])
+        parity(r.cpu().numpy(), rmat17["rs"], f"{forced['name']} r_stranger")
+        assert abs(it - rmat17["it"]) <= 1
+        return
+    forced_name = forced["name"]
+    t.set_variant(kp, -1)
+    t.preprocess(rmat17["g"], C, T, EPS)
+    t.set_variant(kp, forced["index"])
+    seeds = synth.query_seeds(rmat17["cand"], kp, key=90 + kp)
+    seeds[0] = 0
+    t.set_push(False)
+    out = t.query(rmat17["g"], seeds, S).cpu().numpy()
+    again = t.query(rmat17["g"], seeds, S).cpu().numpy()
+    assert np.array_equal(out, again), forced_name
+    for j in sorted({0, kp // 2, kp - 1}):
+        ref = oracle.query(rmat17["og"], int(seeds[j]), C, S, T, rmat17["rs"], EPS)
+        parity(out[:, j], ref, f"{forced_name} col {j} seed {seeds[j]}")
