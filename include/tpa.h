@@ -54,6 +54,9 @@ const char *tpa_last_error(void);
  * holds CSR(A~^T) (rows = destinations, sources ascending) for the pull
  * products of Algorithm 1 and CSR(A~) (rows = sources) for the push step
  * and the adjoint, both on the device of `stream`.
+ * The build is unweighted; a weighted graph takes a second call,
+ * tpa_set_edge_weights (weights in CSR(A~) edge order, after duplicates
+ * are merged, so a weight belongs to one distinct edge).
  * Errors: TPA_EINVAL for n < 1, n >= 2^31, m_edges < 0, an id out of range;
  * TPA_ENOMEM, TPA_ECUDA.  *out is set only on success.
  */
