@@ -649,8 +649,15 @@ def main(argv=None):
         moved = sp["alg_bytes"] / max(1, sp["launches"])   # what the kernel reads and writes itself
         variant = names.get(tpa.get_variant(kp), "?")
         products = "valued" if args.valued_products else "pattern"
+        traffic = ncu_traffic(f"{variant}+{products}", args.scale)
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": ncu_traffic(f"{variant}+{products}", args.scale), "variant": variant,
+                "traffic": traffic, "variant": variant,
+                # DRAM GB/s from the ncu bytes over this run's launch time, and
+                # its ratio to the algorithmic bytes (gather over-fetch when > 1)
+                "dram_gbs": traffic / avg_s / 1e9 if traffic else None,
+                "traffic_over_alg": traffic / per_launch if traffic else None,
+                # edges traversed per second (each nonzero of CSR(A~^T) once per launch)
+                "gteps": m / avg_s / 1e9,
                 "products": products,
                 "kernel": f"{fam}: SpMV/SpMM over CSR(A~^T), {variant}, {products} products",
                 "launches": sp["launches"], "avg_launch_ms": 1000.0 * avg_s,
