@@ -98,7 +98,14 @@ tpa_status tpa_get_stranger(const tpa_graph *g, float *out, int64_t *iters, void
  * host memory that is not page-locked), seeds with more out-edges than the
  * push branch takes (256) are swapped into the last chunks of the query, so
  * that the other chunks push x1 and x2, and the swapped columns are put back
- * at the end; results then agree with unmoved seeds to FP32 rounding.  Requires 1 <= S <= T, k >= 1, 0 <= seeds[j] < n.
+ * at the end; results then agree with unmoved seeds to FP32 rounding.
+ * With out in page-locked host memory the kernels write the scores into it
+ * directly (no swap), or, with tpa_set_output_group_width(w) and k >= 2w,
+ * the seeds run in column groups of w: each group is computed into a device
+ * buffer (two are kept, n x w floats each), with the swap above inside the
+ * group, and copied to out while the next group computes.  Host outputs are
+ * complete when the call returns.
+ * Requires 1 <= S <= T, k >= 1, 0 <= seeds[j] < n.
  * Errors: TPA_ESTATE before tpa_preprocess; TPA_EINVAL.
  */
 tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *out, void *stream);
@@ -264,6 +271,15 @@ int tpa_get_batch_width(void);
  * every streamed nonzero serves more seeds). */
 tpa_status tpa_set_cpi_batch_width(int width);
 int tpa_get_cpi_batch_width(void);
+
+/* Column groups of a tpa_query whose output is page-locked host memory (see
+ * tpa_query): width = 0 (the default) has the kernels write the host memory
+ * directly; a multiple of 8 in [8, 4096] computes groups of that many
+ * columns in device memory and copies each to the host while the next one
+ * computes (for k >= 2 x width).  TPA_EINVAL for another value.  The getter
+ * returns the setting. */
+tpa_status tpa_set_output_group_width(int width);
+int tpa_get_output_group_width(void);
 
 /* Direction choice in tpa_query (default on): for chunks of up to 8 seeds,
  * each with at most 256 out-edges, and S >= 4, the sparse iterates x1 and x2

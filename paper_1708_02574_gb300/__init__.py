@@ -37,6 +37,8 @@ from .tpa import (  # noqa: F401
     query_sets,
     save_preprocessed,
     set_batch_width,
+    set_output_group_width,
+    get_output_group_width,
     set_cpi_batch_width,
     get_cpi_batch_width,
     set_push,

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <new>
@@ -206,6 +207,53 @@ using namespace tpa;
     }                                             \
     return TPA_OK;
 
+// Columns per group when a query's scores go to page-locked host memory
+// through device buffers (tpa_set_output_group_width; 0: the kernels write
+// the host memory directly, the default).  Grouping applies from two groups
+// on, so that a copy overlaps a computation.
+static std::atomic<int> g_group_width{0};
+
+static int stage_width(int k)
+{
+    const int w = g_group_width.load();
+    return w > 0 && k >= 2 * w ? w : 0;
+}
+
+// Algorithm 3 for the columns of a host output in groups of gw: group i is
+// computed on s into stage[i & 1] and copied to the host on the copy stream,
+// which group i + 2 waits for before it reuses the buffer.
+static void query_in_groups(tpa_graph *g, const CpiArgs &a0, float *host, int gw, cudaStream_t s)
+{
+    Workspace &W = g->ws;
+    if (!W.copy) TPA_CUDA(cudaStreamCreateWithFlags(&W.copy, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+        if (!W.ready[b]) TPA_CUDA(cudaEventCreateWithFlags(&W.ready[b], cudaEventDisableTiming));
+        if (!W.copied[b]) TPA_CUDA(cudaEventCreateWithFlags(&W.copied[b], cudaEventDisableTiming));
+        W.stage[b].ensure((size_t)g->n * gw * sizeof(float), s);
+    }
+    const int k = a0.k;
+    int groups = 0;
+    for (int g0 = 0; g0 < k; g0 += gw, ++groups) {
+        const int b = groups & 1, kg = std::min(gw, k - g0);
+        if (groups >= 2) TPA_CUDA(cudaStreamWaitEvent(s, W.copied[b], 0));
+        CpiArgs a = a0;
+        a.seeds = a0.seeds + g0;
+        a.seed_outdeg = a0.seed_outdeg + g0;
+        a.k = kg;
+        a.out = W.stage[b].as<float>();
+        a.ldo = kg;
+        run_cpi(g, a, s);
+        TPA_CUDA(cudaEventRecord(W.ready[b], s));
+        TPA_CUDA(cudaStreamWaitEvent(W.copy, W.ready[b], 0));
+        TPA_CUDA(cudaMemcpy2DAsync(host + g0, (size_t)k * sizeof(float), W.stage[b].p, (size_t)kg * sizeof(float),
+                                   (size_t)kg * sizeof(float), (size_t)g->n, cudaMemcpyDeviceToHost, W.copy));
+        TPA_CUDA(cudaEventRecord(W.copied[b], W.copy));
+    }
+    // the caller's stream completes after both copies (and the stage buffers
+    // are freed on it only after them)
+    for (int b = 0; b < std::min(groups, 2); ++b) TPA_CUDA(cudaStreamWaitEvent(s, W.copied[b], 0));
+}
+
 extern "C" {
 
 const char *tpa_last_error(void) { return g_err; }
@@ -279,7 +327,14 @@ void tpa_free_graph(tpa_graph *g)
             kv.second.head_row.release(s);
             kv.second.head_first.release(s);
         }
+    g->ws.stage[0].release(s);
+    g->ws.stage[1].release(s);
     if (g->ws.hflag) cudaFreeHost(g->ws.hflag);
+    for (int b = 0; b < 2; ++b) {
+        if (g->ws.ready[b]) cudaEventDestroy(g->ws.ready[b]);
+        if (g->ws.copied[b]) cudaEventDestroy(g->ws.copied[b]);
+    }
+    if (g->ws.copy) cudaStreamDestroy(g->ws.copy);
     cudaStreamSynchronize(s);
     trim_pool();
     delete g;
@@ -386,12 +441,16 @@ tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *ou
     std::vector<int32_t> hs = read_seeds(seeds, k, g->n, s);
     g->ws.seeds.ensure((size_t)k * sizeof(int32_t), s);
     TPA_CUDA(cudaMemcpyAsync(g->ws.seeds.p, hs.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    // Host output: page-locked memory is written by the kernels directly (over
-    // the host link, while later chunks compute); other host memory is staged.
+    // Host output.  Page-locked memory is written by the kernels directly
+    // (over the host link, while later chunks compute), or, with a group
+    // width set, filled by column groups: each group is computed into a
+    // device buffer and copied to the host by the copy engine while the next
+    // group computes.  Other host memory is staged and copied at the end.
     const bool host_out = !is_device_ptr(out);
     float *mapped = host_out ? static_cast<float *>(mapped_host_ptr(out)) : nullptr;
+    const int gw = mapped ? stage_width(k) : 0;
     float *dout = out;
-    if (host_out) {
+    if (host_out && !gw) {
         if (mapped) {
             dout = mapped;
         } else {
@@ -414,7 +473,11 @@ tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *ou
     a.ldo = k;
     std::vector<int32_t> od = seed_outdegrees(g, a.seeds, k, s);   // the host picks each chunk's branch
     a.seed_outdeg = od.data();
-    run_cpi(g, a, s);
+    if (gw) {
+        query_in_groups(g, a, out, gw, s);
+    } else {
+        run_cpi(g, a, s);
+    }
     if (host_out) {
         if (!mapped)
             TPA_CUDA(cudaMemcpyAsync(out, dout, (size_t)g->n * k * sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -684,5 +747,18 @@ tpa_status tpa_load_preprocessed(tpa_graph *g, const char *path, void *stream)
     g->has_pre = true;
     API_END
 }
+
+tpa_status tpa_set_output_group_width(int width)
+{
+    clear_error();
+    if (!(width == 0 || (width >= 8 && width <= 4096 && width % 8 == 0))) {
+        set_error("tpa_set_output_group_width: %d is neither 0 nor a multiple of 8 in [8, 4096]", width);
+        return TPA_EINVAL;
+    }
+    g_group_width.store(width);
+    return TPA_OK;
+}
+
+int tpa_get_output_group_width(void) { return g_group_width.load(); }
 
 }  // extern "C"

@@ -134,6 +134,10 @@ struct Workspace {
     DevBuf sets;            // int64 seed-set offsets
     DevBuf seeds_g, cols;   // a query's seeds regrouped; their positions, then the swapped column pairs
     DevBuf out;             // device staging for host outputs
+    DevBuf stage[2];        // column groups of a host output, computed in turn while the other is copied
+    cudaStream_t copy = nullptr;                   // the copies of staged column groups to the host
+    cudaEvent_t ready[2] = {nullptr, nullptr};     // a group's scores are in stage[b]
+    cudaEvent_t copied[2] = {nullptr, nullptr};    // stage[b] has reached the host
     DevBuf iters;           // int32 per-column iteration counts
     DevBuf u;               // push path: 64-bit fixed-point accumulator [n][KP]
     DevBuf touched;         // push path: one bit per row reached by the push

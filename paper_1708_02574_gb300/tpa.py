@@ -74,6 +74,8 @@ def library():
         "tpa_set_cpi_batch_width": (i32, [i32]),
         "tpa_get_cpi_batch_width": (i32, []),
         "tpa_set_push": (i32, [i32]),
+        "tpa_set_output_group_width": (i32, [i32]),
+        "tpa_get_output_group_width": (i32, []),
         "tpa_set_pattern": (i32, [i32]),
         "tpa_seed_order": (i32, [P, i32, i32, P]),
         "tpa_profile_reset": (i32, [i32]),
@@ -365,6 +367,15 @@ def cpi_step_noalloc(n: int, m: int, row_ptr, col, val, c: float, x, y, r=None, 
     All tensors must be CUDA tensors; the CSR is that of A~^T (rows = destinations)."""
     _check(library().tpa_cpi_step_noalloc(int(n), int(m), _ptr(row_ptr), _ptr(col), _ptr(val), float(c), _ptr(x),
                                           _ptr(y), _ptr(r), _ptr(l1), _stream()))
+
+
+def set_output_group_width(width: int) -> None:
+    """Column groups of a query into page-locked host memory: 0 direct writes (default), else the width."""
+    _check(library().tpa_set_output_group_width(int(width)))
+
+
+def get_output_group_width() -> int:
+    return int(library().tpa_get_output_group_width())
 
 
 def set_push(enable: bool) -> None:

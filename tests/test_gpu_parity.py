@@ -161,15 +161,21 @@ def test_host_buffers_through_c_abi(rmat14):
     assert np.array_equal(out, dev)
 
 
-@pytest.mark.parametrize("k", [13, 150])
-def test_pinned_host_output(rmat14, k):
+@pytest.mark.parametrize("k,group", [(13, 0), (150, 0), (150, 72), (600, 256)])
+def test_pinned_host_output(rmat14, k, group):
     """Page-locked host output: the kernels write the scores straight into it
-    (every seed in its chunk)."""
+    (group 0), or column groups are computed in device buffers and copied
+    while the next group computes (150 columns in groups of 72: three groups,
+    the third reusing the first one's buffer; 600 in groups of 256)."""
     import torch
     t = tpa()
     seeds = synth.query_seeds(rmat14["cand"], k, key=14)
     out = torch.full((rmat14["n"], k), -1.0, dtype=torch.float32).pin_memory()
-    t.query(rmat14["g"], seeds, S, out=out)
+    t.set_output_group_width(group)
+    try:
+        t.query(rmat14["g"], seeds, S, out=out)
+    finally:
+        t.set_output_group_width(0)
     dev = t.query(rmat14["g"], seeds, S).cpu()
     if k <= 8 or not (rmat14["og"].outdeg[seeds] > 256).any():
         assert torch.equal(out, dev)
