@@ -181,19 +181,20 @@ def adjoint_study(args):
     t_loss = event_time(torch, loss_only, max(3, args.steps // 2))
     clk = clocks.stop()
     # algorithmic bytes of one gradient: SpMVs over CSR(A~^T) and CSR(A~) at
-    # 8m + 20n (k = 1) or 8m + 4n + 16nk (k = 8), edge passes at 16m (SDDMM:
+    # 8m + 20n (k = 1) or 8m + 4n + 16nk (k = the family batch), edge passes at 16m (SDDMM:
     # row and column ids read, gradient read and written), the row Jacobian
     # at 16m, the theta reduction at (8 + 4d)m
-    batches = (ntrip + 7) // 8
+    kb = tpa.get_adjoint_batch_width()   # triples per family batch
+    batches = (ntrip + kb - 1) // kb
     spmv = s8d_bytes(n, m, 1)
-    spmm = s8d_bytes(n, m, 8)
+    spmm = s8d_bytes(n, m, kb)
     alg = (K * spmv + batches * ((S - 1) * spmm + (S - 2) * spmm + (S - 1) * 16.0 * m)
            + K * spmv + K * 16.0 * m + 16.0 * m + (8.0 + 4.0 * d) * m)
     hbm, peak_kind = peaks()
     line = {"study": "adjoint", "metric": "gradients/s (loss + dL/dtheta over 4,096 triples)",
             "value": 1.0 / t_grad, "unit": "gradients/s", "higher_is_better": True, "data": "synthetic",
             "dtype": "f32 (fp64 reductions)", "ms_per_gradient": 1000.0 * t_grad,
-            "ms_loss_only": 1000.0 * t_loss, "triples_per_s": ntrip / t_grad, "K": K,
+            "ms_loss_only": 1000.0 * t_loss, "triples_per_s": ntrip / t_grad, "K": K, "family_batch": kb,
             "config": {"workload": f"link-prediction loss gradient, {ntrip} triples, R-MAT scale {sc} (ef 16), "
                                    f"{d} features, c={C} S={S} T={T}", "n": n, "m": m},
             "roofline": {"bound": "hbm", "achieved": alg / t_grad / 1e9, "peak": hbm, "unit": "GB/s",

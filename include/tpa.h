@@ -100,7 +100,9 @@ tpa_status tpa_get_stranger(const tpa_graph *g, float *out, int64_t *iters, void
  * that the other chunks push x1 and x2, and the swapped columns are put back
  * at the end; results then agree with unmoved seeds to FP32 rounding.
  * With out in page-locked host memory the kernels write the scores into it
- * directly (no swap), or, with tpa_set_output_group_width(w) and k >= 2w,
+ * directly (no swap) when its rows are 16-byte aligned (k a multiple of 4;
+ * otherwise the scores are staged in device memory and copied once), or,
+ * with tpa_set_output_group_width(w) and k >= 2w,
  * the seeds run in column groups of w: each group is computed into a device
  * buffer (two are kept, n x w floats each), with the swap above inside the
  * group, and copied to out while the next group computes.  Host outputs are
@@ -212,6 +214,14 @@ tpa_status tpa_edge_weights(const float *feat, const float *theta, int d, int64_
  * vectors instead of K+1, for K more SpMVs); the gradient is bit-identical.
  */
 tpa_status tpa_set_adjoint_budget(uint64_t bytes);
+
+/* Triples per family batch of tpa_loss_grad: the forward and reverse family
+ * chains of `width` triples run as one [n][width] SpMM per step (8, 16 or
+ * 32; 0 restores the default).  Wider batches stream the CSR fewer times per
+ * triple.  The gradient differs between widths only by FP32 rounding.
+ * TPA_EINVAL for another value; the getter returns the width in effect. */
+tpa_status tpa_set_adjoint_batch_width(int width);
+int tpa_get_adjoint_batch_width(void);
 
 /*
  * L = sum over ntrip triples (s, p, q) of softplus(r[q] - r[p]), where

@@ -21,6 +21,8 @@ from .tpa import (  # noqa: F401
     edge_weights,
     loss_grad,
     set_adjoint_budget,
+    set_adjoint_batch_width,
+    get_adjoint_batch_width,
     set_edge_weights,
     sync,
     theta_grad,

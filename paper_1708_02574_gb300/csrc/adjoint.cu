@@ -25,7 +25,7 @@
 namespace tpa {
 namespace {
 
-constexpr int KB = 8;                                  // triples per family batch
+constexpr int KB_DEFAULT = 8;   // triples per family batch (8, 16 or 32; 8 measured fastest at scale 20)
 constexpr double G_SCALE = 1099511627776.0;            // 2^40, fixed point of G
 
 unsigned grid_for(int64_t work, int threads = 256)
@@ -93,6 +93,7 @@ __global__ void stranger_sum_k(const float *xs, int64_t n, int T, int K, float *
 }
 
 // F_0 = c e_s for the batch's columns (padding columns stay zero)
+template <int KB>
 __global__ void family_init_k(float *F0, const int32_t *seeds, int kb, float c)
 {
     const int j = threadIdx.x;
@@ -100,6 +101,7 @@ __global__ void family_init_k(float *F0, const int32_t *seeds, int kb, float c)
 }
 
 // Scores at (p, q), loss and sigma per triple; G (stranger seed) in fixed point.
+template <int KB>
 __global__ void pair_k(const float *F, int64_t n, int S, const int32_t *pos, const int32_t *neg, int kb, float opa,
                        const float *rs, double *loss, double *sg, unsigned long long *gacc)
 {
@@ -123,6 +125,7 @@ __global__ void pair_k(const float *F, int64_t n, int S, const int32_t *pos, con
 }
 
 // lam[q][j] += (1+alpha) sg_j, lam[p][j] -= (1+alpha) sg_j  (one thread per column)
+template <int KB>
 __global__ void scatter_g_k(float *lam, const int32_t *pos, const int32_t *neg, const double *sg, int kb, float opa)
 {
     const int j = threadIdx.x;
@@ -156,12 +159,27 @@ template <int W>
 __global__ void sddmm_k(const int32_t *row, const int32_t *col, int64_t m, const float *lam, const float *X, int kc,
                         float coef, float *GE)
 {
+    // the padding columns kc .. W-1 of lam and X are zero, so summing all W
+    // columns in order gives the same FP32 dot as stopping at kc
+    (void)kc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t u = row[e], v = col[e];
         float dot = 0.0f;
+        if constexpr (W % 4 == 0) {
+            const float4 *lv = reinterpret_cast<const float4 *>(lam + v * W);
+            const float4 *xu = reinterpret_cast<const float4 *>(X + u * W);
 #pragma unroll
-        for (int j = 0; j < W; ++j)
-            if (j < kc) dot = fmaf(__ldg(lam + v * W + j), __ldg(X + u * W + j), dot);
+            for (int q = 0; q < W / 4; ++q) {
+                const float4 a = __ldg(lv + q), b = __ldg(xu + q);
+                dot = fmaf(a.x, b.x, dot);
+                dot = fmaf(a.y, b.y, dot);
+                dot = fmaf(a.z, b.z, dot);
+                dot = fmaf(a.w, b.w, dot);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < W; ++j) dot = fmaf(__ldg(lam + v * W + j), __ldg(X + u * W + j), dot);
+        }
         GE[e] += coef * dot;
     }
 }
@@ -343,6 +361,56 @@ struct StrangerIterates {
     }
 };
 
+int g_adjoint_batch = 0;   // triples per family batch (tpa_set_adjoint_batch_width; 0: the default)
+
+int adjoint_batch_width() { return g_adjoint_batch ? g_adjoint_batch : KB_DEFAULT; }
+
+namespace {
+
+// The family chains of all triples in batches of KB (columns [n][KB], padding
+// columns zero): forward x_1 .. x_{S-1} from c e_seed, the scores at the
+// positive and negative nodes with the loss and its sigma, and (want_grad)
+// the backward chain lam_{S-1} .. lam_1 with the edge products of each step
+// added into GE.
+template <int KB>
+void family_batches(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const int32_t *neg, int ntrip, int S,
+                    float c, float decay, float opa, bool want_grad, DevBuf &rs, DevBuf &F, DevBuf &lamA, DevBuf &lamB,
+                    DevBuf &GE, DevBuf &loss, DevBuf &sg, DevBuf &gacc, cudaStream_t s)
+{
+    const int64_t n = g->n, m = g->m;
+    need(F, (size_t)S * n * KB * sizeof(float), "family iterates");
+    need(lamA, (size_t)n * KB * sizeof(float), "family adjoint");
+    need(lamB, (size_t)n * KB * sizeof(float), "family adjoint");
+    float *Fp = F.as<float>();
+    for (int t0 = 0; t0 < ntrip; t0 += KB) {
+        const int kb = std::min(KB, ntrip - t0);
+        TPA_CUDA(cudaMemsetAsync(Fp, 0, (size_t)n * KB * sizeof(float), s));
+        family_init_k<KB><<<1, 32, 0, s>>>(Fp, seeds + t0, kb, c);
+        for (int i = 1; i < S; ++i)
+            spmv_apply(g, 0, Fp + (int64_t)(i - 1) * n * KB, Fp + (int64_t)i * n * KB, KB, decay, s);
+        pair_k<KB><<<1, 32, 0, s>>>(Fp, n, S, pos + t0, neg + t0, kb, opa, rs.as<float>(), loss.as<double>() + t0,
+                                    sg.as<double>() + t0, gacc.as<unsigned long long>());
+        note_launch("adjoint", 2);
+        if (!want_grad) continue;
+        float *lam = lamA.as<float>(), *nxt = lamB.as<float>();
+        TPA_CUDA(cudaMemsetAsync(lam, 0, (size_t)n * KB * sizeof(float), s));
+        scatter_g_k<KB><<<1, 32, 0, s>>>(lam, pos + t0, neg + t0, sg.as<double>() + t0, kb, opa);
+        for (int i = S - 1; i >= 1; --i) {
+            sddmm_k<KB><<<grid_for(m), 256, 0, s>>>(g->row_a.as<int32_t>(), g->col_a.as<int32_t>(), m, lam,
+                                                    Fp + (int64_t)(i - 1) * n * KB, kb, decay, GE.as<float>());
+            if (i > 1) {
+                spmv_apply(g, 1, lam, nxt, KB, decay, s);
+                std::swap(lam, nxt);
+                scatter_g_k<KB><<<1, 32, 0, s>>>(lam, pos + t0, neg + t0, sg.as<double>() + t0, kb, opa);
+            }
+        }
+        note_launch("adjoint", 1 + 2 * (S - 1));
+        TPA_CHECK_LAUNCH();
+    }
+}
+
+}  // namespace
+
 size_t g_adjoint_budget = (size_t)16 << 30;   // iterate bytes kept before checkpointing starts
 
 // Loss and dL/dw (device float[m], CSR(A~) order; grad_w = nullptr: the loss
@@ -359,9 +427,10 @@ double loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const i
     DevBuf rs, F, lamA, lamB, GE, loss, sg, gacc, Gs, two;
     StrangerIterates X;
     rs.ensure((size_t)n * sizeof(float), s);
-    F.ensure((size_t)S * n * KB * sizeof(float), s);
-    lamA.ensure((size_t)n * KB * sizeof(float), s);
-    lamB.ensure((size_t)n * KB * sizeof(float), s);
+    const int KBW = adjoint_batch_width();
+    F.ensure((size_t)S * n * KBW * sizeof(float), s);
+    lamA.ensure((size_t)n * KBW * sizeof(float), s);
+    lamB.ensure((size_t)n * KBW * sizeof(float), s);
     loss.ensure((size_t)ntrip * sizeof(double), s);
     sg.ensure((size_t)ntrip * sizeof(double), s);
     gacc.ensure((size_t)n * sizeof(unsigned long long), s);
@@ -394,32 +463,20 @@ double loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const i
     }
     TPA_CHECK_LAUNCH();
 
-    // family chains in batches of KB triples: forward, scores, backward
-    float *Fp = F.as<float>();
-    for (int t0 = 0; t0 < ntrip; t0 += KB) {
-        const int kb = std::min(KB, ntrip - t0);
-        TPA_CUDA(cudaMemsetAsync(Fp, 0, (size_t)n * KB * sizeof(float), s));
-        family_init_k<<<1, 32, 0, s>>>(Fp, seeds + t0, kb, (float)c);
-        // always KB columns: the buffers are laid out [n][KB] and padding columns are zero
-        for (int i = 1; i < S; ++i) spmv_apply(g, 0, Fp + (int64_t)(i - 1) * n * KB, Fp + (int64_t)i * n * KB, KB, decay, s);
-        pair_k<<<1, 32, 0, s>>>(Fp, n, S, pos + t0, neg + t0, kb, opa, rs.as<float>(), loss.as<double>() + t0,
-                                sg.as<double>() + t0, gacc.as<unsigned long long>());
-        note_launch("adjoint", 2);
-        if (!want_grad) continue;
-        float *lam = lamA.as<float>(), *nxt = lamB.as<float>();
-        TPA_CUDA(cudaMemsetAsync(lam, 0, (size_t)n * KB * sizeof(float), s));
-        scatter_g_k<<<1, 32, 0, s>>>(lam, pos + t0, neg + t0, sg.as<double>() + t0, kb, opa);
-        for (int i = S - 1; i >= 1; --i) {
-            sddmm_k<KB><<<grid_for(m), 256, 0, s>>>(g->row_a.as<int32_t>(), g->col_a.as<int32_t>(), m, lam,
-                                                    Fp + (int64_t)(i - 1) * n * KB, kb, decay, GE.as<float>());
-            if (i > 1) {
-                spmv_apply(g, 1, lam, nxt, KB, decay, s);
-                std::swap(lam, nxt);
-                scatter_g_k<<<1, 32, 0, s>>>(lam, pos + t0, neg + t0, sg.as<double>() + t0, kb, opa);
-            }
-        }
-        note_launch("adjoint", 1 + 2 * (S - 1));
-        TPA_CHECK_LAUNCH();
+    // family chains in batches of kb triples: forward, scores, backward
+    switch (adjoint_batch_width()) {
+    case 16:
+        family_batches<16>(g, seeds, pos, neg, ntrip, S, (float)c, decay, opa, want_grad, rs, F, lamA, lamB, GE,
+                           loss, sg, gacc, s);
+        break;
+    case 32:
+        family_batches<32>(g, seeds, pos, neg, ntrip, S, (float)c, decay, opa, want_grad, rs, F, lamA, lamB, GE,
+                           loss, sg, gacc, s);
+        break;
+    default:
+        family_batches<8>(g, seeds, pos, neg, ntrip, S, (float)c, decay, opa, want_grad, rs, F, lamA, lamB, GE,
+                          loss, sg, gacc, s);
+        break;
     }
 
     if (want_grad) {

@@ -448,6 +448,9 @@ tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *ou
     // group computes.  Other host memory is staged and copied at the end.
     const bool host_out = !is_device_ptr(out);
     float *mapped = host_out ? static_cast<float *>(mapped_host_ptr(out)) : nullptr;
+    // rows not 16-byte aligned would take 4-byte stores over the host link:
+    // stage those in device memory and copy once
+    if (mapped && (k * sizeof(float)) % 16 != 0) mapped = nullptr;
     const int gw = mapped ? stage_width(k) : 0;
     float *dout = out;
     if (host_out && !gw) {
@@ -629,6 +632,19 @@ tpa_status tpa_set_adjoint_budget(uint64_t bytes)
     g_adjoint_budget = (size_t)bytes;
     return TPA_OK;
 }
+
+tpa_status tpa_set_adjoint_batch_width(int width)
+{
+    clear_error();
+    if (!(width == 0 || width == 8 || width == 16 || width == 32)) {
+        set_error("tpa_set_adjoint_batch_width: %d is not 0, 8, 16 or 32", width);
+        return TPA_EINVAL;
+    }
+    g_adjoint_batch = width;
+    return TPA_OK;
+}
+
+int tpa_get_adjoint_batch_width(void) { return adjoint_batch_width(); }
 
 tpa_status tpa_loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const int32_t *neg, int ntrip,
                          double c, int S, int T, int K, double *loss, float *grad_w, void *stream)

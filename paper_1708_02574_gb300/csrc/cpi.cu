@@ -1119,7 +1119,7 @@ std::vector<int32_t> seed_outdegrees(tpa_graph *g, const int32_t *d_seeds, int k
 
 void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float decay, cudaStream_t s)
 {
-    TPA_REQUIRE(kc >= 1 && kc <= 8, "spmv_apply: %d columns (at most 8)", kc);
+    TPA_REQUIRE(kc >= 1 && kc <= 32, "spmv_apply: %d columns (at most 32)", kc);
     const int KP = kp_for(kc);
     const Variant &var = pick_variant(KP);
     Workspace &W = g->ws;

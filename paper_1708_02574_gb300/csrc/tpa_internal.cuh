@@ -210,7 +210,7 @@ void exclusive_scan_i32_i64(const int32_t *in, int64_t *out, int64_t len, DevBuf
 // cpi.cu
 const Plan &get_plan(tpa_graph *g, int L, cudaStream_t s, int which = 0);   // which: 0 = A~^T, 1 = A~
 
-// One SpMV/SpMM step y = decay * M x for kc <= 8 columns (x, y node-major
+// One SpMV/SpMM step y = decay * M x for kc <= 32 columns (x, y node-major
 // [n][kp_for(kc)], padding columns of x zero) with M = A~^T (which = 0) or
 // M = A~ (which = 1).
 int kp_for(int k);
@@ -262,6 +262,10 @@ double loss_grad(tpa_graph *g, const int32_t *seeds, const int32_t *pos, const i
 // Bytes of stranger-chain iterates the reverse sweep keeps before it switches
 // to checkpoints every ceil(sqrt(K+1)) iterations (tpa_set_adjoint_budget).
 extern size_t g_adjoint_budget;
+// Triples per family batch of tpa_loss_grad (tpa_set_adjoint_batch_width;
+// 0: the default) and the width in effect.
+extern int g_adjoint_batch;
+int adjoint_batch_width();
 
 
 // Out-degrees of k device-resident seeds, copied to the host (one small copy and a wait).

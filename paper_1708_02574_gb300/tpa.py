@@ -55,6 +55,8 @@ def library():
         "tpa_theta_grad": (i32, [P, P, P, i32, i64, P, P]),
         "tpa_sync": (i32, [P, P]),
         "tpa_set_adjoint_budget": (i32, [ctypes.c_uint64]),
+        "tpa_set_adjoint_batch_width": (i32, [i32]),
+        "tpa_get_adjoint_batch_width": (i32, []),
         "tpa_server_sync": (i32, [P, P]),
         "tpa_server_create": (i32, [P, i32, i32, P, i64, P, ctypes.POINTER(P)]),
         "tpa_server_query": (i32, [P, P, i32, P]),
@@ -432,6 +434,15 @@ def loss_grad(g: Graph, seeds, pos, neg, c: float = 0.15, S: int = 5, T: int = 1
 def set_adjoint_budget(nbytes: int) -> None:
     """tpa_set_adjoint_budget: iterate bytes kept before checkpointing."""
     _check(library().tpa_set_adjoint_budget(int(nbytes)))
+
+
+def set_adjoint_batch_width(width: int) -> None:
+    """tpa_set_adjoint_batch_width: triples per family batch (8, 16, 32; 0 the default)."""
+    _check(library().tpa_set_adjoint_batch_width(int(width)))
+
+
+def get_adjoint_batch_width() -> int:
+    return int(library().tpa_get_adjoint_batch_width())
 
 
 def sync(g: Graph) -> None:

@@ -92,6 +92,32 @@ def test_loss_grad_matches_oracle(problem, ntrip, K):
     assert rel(gth, rgth) < 1e-3, (gth, rgth)
 
 
+@pytest.mark.parametrize("width", [8, 16, 32])
+def test_family_batch_widths(problem, width):
+    """Family chains in batches of 8, 16 or 32 triples (48 triples: 6, 3 or 2
+    batches, the last one of 32 partly padding) give the oracle's loss and
+    gradient; widths differ from one another only by FP32 rounding."""
+    t = tpa()
+    og, g = problem["og"], problem["g"]
+    w = t.edge_weights(problem["feat_d"], problem["theta_d"])
+    t.set_edge_weights(g, w)
+    K = 24
+    t.set_adjoint_batch_width(width)
+    try:
+        assert t.get_adjoint_batch_width() == width
+        loss, gw = t.loss_grad(g, problem["seeds"], problem["pos"], problem["neg"], C, S, T, K)
+    finally:
+        t.set_adjoint_batch_width(0)
+    loss8, gw8 = t.loss_grad(g, problem["seeds"], problem["pos"], problem["neg"], C, S, T, K)
+    wd = oracle.edge_weights(problem["theta"], problem["feat"])
+    rloss, rgw, _, _ = oracle.loss_grad(og, wd, problem["seeds"], problem["pos"], problem["neg"], C, S, T, K)
+    assert abs(loss - rloss) <= 1e-5 * abs(rloss)
+    assert rel(gw.cpu().numpy(), rgw) < 1e-3
+    assert rel(gw.cpu().numpy(), gw8.cpu().numpy()) < 1e-5
+    with pytest.raises(t.TpaError, match="EINVAL"):
+        t.set_adjoint_batch_width(12)
+
+
 def test_autograd_function(problem):
     import torch
     t = tpa()
