@@ -367,9 +367,9 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
-    """Identity of the SpMV/SpMM device code (kernels and the structs they read)."""
+    """Identity of the SpMV/SpMM device code (the files that define the kernels and Params)."""
     h = hashlib.sha256()
-    for f in ("spmm_kernels.cuh", "spmm_binned.cuh", "tpa_internal.cuh"):
+    for f in ("spmm_kernels.cuh", "spmm_binned.cuh"):
         with open(os.path.join(ROOT, "paper_1708_02574_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -412,6 +412,15 @@ def host_cpu() -> dict:
                 model = line.split(":", 1)[1].strip()
     except OSError:
         pass
+    if not model:   # Arm hosts name the core in lscpu only
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.split(":")[0].strip().lower() == "model name":
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
     if not model:
         import platform
         model = platform.processor() or platform.machine()
