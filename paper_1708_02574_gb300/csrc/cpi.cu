@@ -301,15 +301,44 @@ static int64_t launch_spmvg(const Params &p, cudaStream_t s)
 
 // Returns the rows of tl1 written: one per warp of the grid (at most
 // tiles + 7, the size the workspace reserves).
-template <int G, int V, int ITEMS, int PF, int WARPS, int MINB>
+// Cooperative launch of a persistent grid (kernels whose CTAs wait on one
+// another): the driver starts every CTA at once or refuses, and a refused
+// grid is halved until it fits.
+static int64_t launch_cooperative(void (*kern)(Params), const Params &p, int64_t grid, unsigned threads,
+                                  size_t smem, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    for (;;) {
+        cfg.gridDim = dim3((unsigned)grid);
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, p);
+        if (e == cudaSuccess) return grid;
+        if (e != cudaErrorCooperativeLaunchTooLarge || grid == 1) TPA_CUDA(e);
+        cudaGetLastError();
+        grid = (grid + 1) / 2;
+    }
+}
+
+// FUSE: the pipelined kernel that finishes its deferred rows itself (no
+// fixup), launched cooperatively; returns the CTAs launched.  Otherwise the
+// rows of tl1 written (one per warp).
+template <int G, int V, int ITEMS, int PF, int WARPS, int MINB, bool FUSE = false>
 static int64_t launch_spmvp(const Params &p, cudaStream_t s)
 {
     // one instantiation per product mode, so the valued kernel carries no test of it
-    constexpr size_t smem_v = WARPS * PipeSmem<G, V, ITEMS, false>::PER_WARP;
-    constexpr size_t smem_p = WARPS * PipeSmem<G, V, ITEMS, true>::PER_WARP;
+    constexpr size_t smem_v = WARPS * PipeSmem<G, V, ITEMS, false, FUSE>::PER_WARP;
+    constexpr size_t smem_p = WARPS * PipeSmem<G, V, ITEMS, true, FUSE>::PER_WARP;
     static_assert(smem_v <= 227 * 1024 && smem_p <= 227 * 1024, "shared memory per block");
-    auto *const valued = spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB, false>;
-    auto *const pattern = spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB, true>;
+    auto *const valued = spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB, false, FUSE>;
+    auto *const pattern = spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB, true, FUSE>;
     static int per_sm_v = 0, per_sm_p = 0;
     if (!per_sm_v) {
         TPA_CUDA(cudaFuncSetAttribute(valued, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v));
@@ -320,10 +349,15 @@ static int64_t launch_spmvp(const Params &p, cudaStream_t s)
         per_sm_p = std::max(per_sm_p, 1);
     }
     const int per_sm = p.inv_deg ? per_sm_p : per_sm_v;
-    const int64_t grid = std::min<int64_t>((p.tiles + WARPS - 1) / WARPS, (int64_t)per_sm * num_sms());
-    if (p.inv_deg) pattern<<<(unsigned)grid, WARPS * 32, smem_p, s>>>(p);
-    else valued<<<(unsigned)grid, WARPS * 32, smem_v, s>>>(p);
-    return grid * WARPS;
+    const int64_t grid =
+        std::max<int64_t>(1, std::min<int64_t>((p.tiles + WARPS - 1) / WARPS, (int64_t)per_sm * num_sms()));
+    if constexpr (FUSE) {
+        return launch_cooperative(p.inv_deg ? pattern : valued, p, grid, WARPS * 32, p.inv_deg ? smem_p : smem_v, s);
+    } else {
+        if (p.inv_deg) pattern<<<(unsigned)grid, WARPS * 32, smem_p, s>>>(p);
+        else valued<<<(unsigned)grid, WARPS * 32, smem_v, s>>>(p);
+        return grid * WARPS;
+    }
 }
 
 // Segmented flag walk (spmm_seg.cuh; AHEAD: the gathers-ahead kernel):
@@ -362,26 +396,7 @@ static int64_t launch_seg(const Params &p, cudaStream_t s)
     const int per_sm = pat ? per_sm_p : per_sm_v;
     int64_t grid =
         std::max<int64_t>(1, std::min<int64_t>((p.seg_tiles + SEG_WARPS - 1) / SEG_WARPS, (int64_t)per_sm * num_sms()));
-    // a cooperative launch: the driver starts every CTA at once or refuses
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof cfg);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.blockDim = dim3(SEG_WARPS * 32);
-    cfg.dynamicSmemBytes = pat ? smem_p : smem_v;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    for (;;) {
-        cfg.gridDim = dim3((unsigned)grid);
-        const cudaError_t e = cudaLaunchKernelEx(&cfg, pat ? pattern : valued, p);
-        if (e == cudaSuccess) break;
-        if (e != cudaErrorCooperativeLaunchTooLarge || grid == 1) TPA_CUDA(e);
-        cudaGetLastError();
-        grid = (grid + 1) / 2;
-    }
-    return grid;
+    return launch_cooperative(pat ? pattern : valued, p, grid, SEG_WARPS * 32, pat ? smem_p : smem_v, s);
 }
 
 // Upper bound of the CTAs of any persistent grid (32 resident blocks per SM at most).
@@ -485,6 +500,9 @@ struct Variant {
     {{1, V, R, PF, 32}, launch_seg<V, R, PF, NB, false>, nullptr, "seg<" #V "," #R "," #PF "," #NB ">", false, true}
 #define TPA_VARIANTA(V, R, PF, NB) \
     {{1, V, R, PF, 32}, launch_seg<V, R, PF, NB, true>, nullptr, "sega<" #V "," #R "," #PF "," #NB ">", false, true}
+#define TPA_VARIANTPF(G, V, I, PF, W, MB)                                \
+    {{G, V, I, PF, 32}, launch_spmvp<G, V, I, PF, W, MB, true>, nullptr, \
+     "pipef<" #G "," #V "," #I "," #PF "," #W "," #MB ">"}
 #define TPA_VARIANTP(G, V, I, PF, W, MB)                                 \
     {{G, V, I, PF, 32}, launch_spmvp<G, V, I, PF, W, MB>, launch_fix<G * V>, \
      "pipe<" #G "," #V "," #I "," #PF "," #W "," #MB ">"}
@@ -499,6 +517,7 @@ static const Variant kVariants[] = {
     TPA_VARIANTS(1, 8, 8, 3),
     TPA_VARIANTS(2, 8, 8, 3),
     TPA_VARIANTS(4, 8, 8, 3),
+    TPA_VARIANTPF(2, 4, 8, 8, 4, 5),
     TPA_VARIANTS(8, 8, 4, 2),
     TPA_VARIANTS(1, 4, 4, 4),
     TPA_VARIANTS(8, 8, 8, 2),
@@ -713,6 +732,18 @@ static unsigned size_for_variant(tpa_graph *g, const Variant &var, int which, in
     p.head = W.head.as<float>();
     p.tl1 = W.tl1.as<float>();
     if (var.binned) bind_bins(p, g, which, KP, s);
+    if (!var.fix) {   // finishes its deferred rows itself: tagged carry words, one L1 partial per CTA
+        const size_t agg_bytes = (size_t)std::max<int64_t>(1, P.tiles) * KP * sizeof(unsigned long long);
+        if (!W.agg.p || W.agg.bytes < agg_bytes) {
+            W.agg.ensure(agg_bytes, s);
+            TPA_CUDA(cudaMemsetAsync(W.agg.p, 0, W.agg.bytes, s));
+        }
+        need(W.agg, agg_bytes, "carry-out words");
+        const size_t part_bytes = (size_t)seg_grid_bound() * KP * sizeof(double);
+        if (W.fix.bytes < part_bytes) W.fix.ensure(part_bytes, s);
+        need(W.fix, part_bytes, "CTA partials");
+        p.agg = W.agg.as<unsigned long long>();
+    }
     return fix_blocks;
 }
 
@@ -940,9 +971,9 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
                     finalize_seg_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(W.ctl.p, p.empty_rows, p.n_empty, r, ldr,
                                                                         a.r_str, p.one_plus_alpha, p.out, p.ldo, n,
                                                                         kc);
-                else
-                    finalize_if_done_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(W.ctl.p, r, ldr, a.r_str,
-                                                                            p.one_plus_alpha, p.out, p.ldo, n, kc);
+                else   // usually returns at once: a grid of 8 blocks per SM (grid-stride when it works)
+                    finalize_if_done_k<<<std::min<unsigned>(grid_1d(n * kc, 256), 8u * (unsigned)num_sms()), 256, 0,
+                                         s>>>(W.ctl.p, r, ldr, a.r_str, p.one_plus_alpha, p.out, p.ldo, n, kc);
                 note_launch("finalize");
             }
             TPA_CHECK_LAUNCH();

@@ -127,6 +127,71 @@ __device__ __forceinline__ bool gate_off(int gate, const void *ctl)
     return gate == GATE_PUSH ? push == 0 : push != 0;
 }
 
+// ------------------------------------------- tagged carry-out words ---
+// A tile publishes its carry-out as 64-bit words that pair the value with a
+// launch tag, written and read relaxed: a reader needs no fence, it polls
+// (bounded) until the word carries its launch's tag.
+constexpr long long SEG_SPIN_LIMIT = 1ll << 22;   // polls of one carry-out word (about a second)
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long seg_pack(float v, uint32_t tag)
+{
+    return ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v);
+}
+
+// Streaming 16-byte load of four column words (read once per launch).
+__device__ __forceinline__ uint4 ld_cols4(const uint32_t *p)
+{
+    uint4 r;
+    asm volatile("ld.global.cs.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ float4 ld_vals4(const float *p)
+{
+    float4 r;
+    asm volatile("ld.global.cs.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+// Wait (bounded) for the carry-out word w of the current launch (tag `want`
+// in bits 33.., row-start flag in bit 32); returns the word, or a zero value
+// with the error flag raised when the wait gives up.  Once any wait of the
+// launch has given up, every other wait returns at once, so a launch ends
+// within about one wait limit whatever happens.
+__device__ __forceinline__ unsigned long long seg_wait(const unsigned long long *w, uint32_t want, Ctl *hdr)
+{
+    unsigned long long v = ld_relaxed_u64(w);
+    long long spins = 0;
+    unsigned ns = 32;
+    while ((uint32_t)(v >> 33) != want) {
+        if (++spins > SEG_SPIN_LIMIT || *(volatile int32_t *)&hdr->error) {
+            atomicOr(&hdr->error, 1);
+            return 0ull;
+        }
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        v = ld_relaxed_u64(w);
+    }
+    return v;
+}
+
+
 // ------------------------------------------------------------- helpers ---
 template <int V>
 __device__ __forceinline__ void ld_row(const float *p, float (&o)[V])
@@ -943,6 +1008,44 @@ __device__ __forceinline__ void epilogue_red(const Params &p, int64_t row, int c
     for (int j = 0; j < V; ++j) l1[j] += alive[j] ? fabsf(yv[j]) : 0.0f;
 }
 
+// Sum over b in [0, nb) of part[b * KP + c] for every column c < KP, by the
+// NT threads of one block in a fixed order (so the result is deterministic):
+// group grp of the NG = NT / KP groups adds b = grp, grp + NG, ... in increasing b
+// (loads issued eight at a time), then thread c adds the group sums in group
+// order.  The result for column c is left in s_fin[c] (s_fin holds 256).
+template <int KP, class T, int NT = 256>
+__device__ __forceinline__ void block_sum_partials_t(const T *part, unsigned nb, double *s_fin)
+{
+    static_assert(KP >= 1 && KP <= NT && NT % KP == 0 && NT <= 256, "KP");
+    constexpr unsigned NG = NT / KP;
+    const int c = threadIdx.x % KP, grp = threadIdx.x / KP;
+    double a = 0.0;
+    unsigned b = grp;
+    for (; b + 7u * NG < nb; b += 8u * NG) {
+        double v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = __ldcg(&part[(int64_t)(b + i * NG) * KP + c]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a += v[i];
+    }
+    for (; b < nb; b += NG) a += __ldcg(&part[(int64_t)b * KP + c]);
+    __syncthreads();
+    s_fin[grp * KP + c] = a;
+    __syncthreads();
+    if (threadIdx.x < KP) {
+        double t = 0.0;
+        for (unsigned g = 0; g < NG; ++g) t += s_fin[g * KP + threadIdx.x];
+        s_fin[threadIdx.x] = t;   // only this thread reads or writes column c's group-0 slot
+    }
+    __syncthreads();
+}
+
+template <int KP>
+__device__ __forceinline__ void block_sum_partials(const double *part, unsigned nb, double *s_fin)
+{
+    block_sum_partials_t<KP, double>(part, nb, s_fin);
+}
+
 template <int G, int V, int ITEMS, bool PAT>
 struct __align__(16) PipeTile {
     static constexpr int NW = 32 / G;
@@ -1072,10 +1175,13 @@ __device__ __forceinline__ void stage_tile(const Params &p, const TileMeta &m, c
     if (lane == 0) rp_s[nrows] = m.y0 + 0x7fffffff;
 }
 
-template <int G, int V, int ITEMS, int PF, bool PAT>
+// FUSE: the deferred row's part goes to pend_s (shared memory) instead of
+// p.head, and the carry-out to the tagged words p.agg instead of p.carry.
+template <int G, int V, int ITEMS, int PF, bool PAT, bool FUSE = false>
 __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, int64_t t, const int64_t *rp_s,
                                           const int32_t *cv_s, const float *inv_s, float *rs_s, int lane,
-                                          const int (&alive)[V], float (&l1)[V])
+                                          const int (&alive)[V], float (&l1)[V], float *pend_s = nullptr,
+                                          uint32_t tag = 0)
 {
     constexpr int NW = 32 / G, KP = G * V;
     const int w = lane / G, col0 = (lane % G) * V;
@@ -1167,12 +1273,23 @@ __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, in
         float tot[V];
 #pragma unroll
         for (int j = 0; j < V; ++j) tot[j] = first_val[j] + (w > 0 ? prev[j] : 0.0f);
-        if (first_row == 0 && m.defer)
-            st_row<V>(p.head + t * KP + col0, tot);
-        else
+        if (first_row == 0 && m.defer) {
+            if constexpr (FUSE)
+                st_row<V>(pend_s + col0, tot);
+            else
+                st_row<V>(p.head + t * KP + col0, tot);
+        } else {
             st_row<V>(rs_s + first_row * KP + col0, tot);
+        }
     }
-    if (w == NW - 1) st_row<V>(p.carry + t * KP + col0, acc);
+    if (w == NW - 1) {
+        if constexpr (FUSE) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) st_relaxed_u64(p.agg + t * KP + col0 + j, seg_pack(acc[j], tag));
+        } else {
+            st_row<V>(p.carry + t * KP + col0, acc);
+        }
+    }
     __syncwarp();
     // epilogue of the tile's finished rows, consecutive rows on consecutive
     // walkers (coalesced): accumulate by atomics (no load), the final family
@@ -1189,20 +1306,82 @@ __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, in
     }
 }
 
-// Shared memory per warp: two tile buffers and the row sums of one tile.
-template <int G, int V, int ITEMS, bool PAT>
+// Shared memory per warp: two tile buffers and the row sums of one tile
+// (FUSE: and two slots for the part of a deferred row).
+template <int G, int V, int ITEMS, bool PAT, bool FUSE = false>
 struct PipeSmem {
     using PT = PipeTile<G, V, ITEMS, PAT>;
     static constexpr size_t RS = (size_t)PT::L * G * V * sizeof(float);
-    static constexpr size_t PER_WARP = 2 * sizeof(PT) + RS;
+    static constexpr size_t PEND = FUSE ? ((size_t)2 * G * V * sizeof(float) + 15) / 16 * 16 : 0;
+    static constexpr size_t PER_WARP = 2 * sizeof(PT) + RS + PEND;
 };
 
+// Finish the deferred row `row` of tile pend_t inside the SpMM: its part in
+// pend_t (pend_s, KP floats) plus the carry-outs of tiles first .. pend_t-1,
+// read from the tagged words (bounded waits).  Lane (c, i) = (lane % KP,
+// lane / KP) adds column c of tiles first+i, first+i+32/KP, ... in order,
+// the lanes of a column are added in a fixed xor tree, and the G lanes of
+// walker 0 run the epilogue.  probe: the word of tile first+i loaded early.
+template <int G, int V, bool PAT>
+__device__ __forceinline__ void pipe_finish(const Params &p, int64_t pend_t, int64_t first, int32_t row, float w_row,
+                                            float *pend_s, unsigned long long probe, uint32_t ep, Ctl *hdr, int lane,
+                                            const int (&alive)[V], float (&l1)[V])
+{
+    constexpr int KP = G * V, LPC = 32 / KP;
+    static_assert(32 % KP == 0, "KP");
+    const int c = lane % KP, i = lane / KP;
+    float part = 0.0f;
+    int64_t u = first + i;
+    if (u < pend_t) {
+        unsigned long long w = probe;
+        if ((uint32_t)(w >> 33) != ep) w = seg_wait(p.agg + u * KP + c, ep, hdr);
+        part = __uint_as_float((uint32_t)w);
+    }
+    // longer spans (rows of hubs): four words in flight per lane
+    for (u += LPC; u < pend_t; u += 4 * LPC) {
+        unsigned long long w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t uu = u + q * LPC;
+            w[q] = uu < pend_t ? ld_relaxed_u64(p.agg + uu * KP + c) : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t uu = u + q * LPC;
+            if (uu < pend_t) {
+                if ((uint32_t)(w[q] >> 33) != ep) w[q] = seg_wait(p.agg + uu * KP + c, ep, hdr);
+                part += __uint_as_float((uint32_t)w[q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = KP; o < 32; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane < KP) pend_s[lane] += part;
+    __syncwarp();
+    if (lane < G) {
+        float sv[V];
+        ld_row_smem<V>(pend_s + lane * V, sv);
+        if (p.mode == MODE_ACC)
+            epilogue_red<KP, V, PAT ? PM_PATTERN : PM_VALUED>(p, (int64_t)row, lane * V, sv, alive, l1, w_row);
+        else
+            epilogue<KP, V, PAT ? PM_PATTERN : PM_VALUED>(p, (int64_t)row, lane * V, sv, alive, l1);
+    }
+    __syncwarp();
+}
+
 // MINB: resident blocks per SM requested from the register allocator.
-template <int G, int V, int ITEMS, int PF, int WARPS, int MINB, bool PAT>
+// FUSE: no fixup launch.  A tile whose first row began in an earlier tile
+// keeps that row's part in shared memory and finishes the row after the
+// warp's next tile (pipe_finish), from the carry-outs the earlier tiles
+// published as tagged words; the last CTA to finish reduces the L1 partials
+// and applies the break test.  The waits need every CTA resident: the grid
+// is launched cooperatively.
+template <int G, int V, int ITEMS, int PF, int WARPS, int MINB, bool PAT, bool FUSE = false>
 __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
 {
     using PT = PipeTile<G, V, ITEMS, PAT>;
-    using SM = PipeSmem<G, V, ITEMS, PAT>;
+    using SM = PipeSmem<G, V, ITEMS, PAT, FUSE>;
+    constexpr int KP = G * V;
     static_assert(ITEMS % PF == 0, "PF");
     static_assert(PF <= 32, "PF");
     static_assert(sizeof(PT) % 16 == 0 && offsetof(PT, cv) % 16 == 0, "layout");
@@ -1215,6 +1394,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
     unsigned char *base = pipe_smem + (size_t)warp * SM::PER_WARP;
     PT *buf = reinterpret_cast<PT *>(base);
     float *rs_s = reinterpret_cast<float *>(base + 2 * sizeof(PT));
+    float *pend_s = reinterpret_cast<float *>(base + 2 * sizeof(PT) + SM::RS);   // FUSE: 2 x KP floats
+    uint32_t ep_raw = 0, ep = 0;
+    if constexpr (FUSE) {
+        ep_raw = *(volatile uint32_t *)&cv.hdr->epoch;
+        ep = (ep_raw + 1u) & 0x7fffffffu;
+    }
+    bool pend = false;   // FUSE: a deferred row waits for the warp's next tile
+    int64_t pend_t = 0, pend_first = 0;
+    int32_t pend_row = 0;
+    float pend_w = 0.0f;
+    int pslot = 0;
     int alive[V];
     float l1[V];
 #pragma unroll
@@ -1240,15 +1430,86 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
         cp_async_commit();
         const TileMeta after = tile_meta(p, t + 2 * stride);
         load_chunks<RC, PAT>(p, after, rg, lane);   // in flight during this walk
+        // FUSE: the first carry-out word the deferred row needs, loaded early
+        unsigned long long probe = 0ull;
+        if constexpr (FUSE) {
+            const int64_t u = pend_first + lane / KP;
+            if (pend && u < pend_t) probe = ld_relaxed_u64(p.agg + u * KP + lane % KP);
+        }
         cp_async_wait_group<1>();              // this tile's copies have landed
         __syncwarp();
-        walk_tile<G, V, ITEMS, PF, PAT>(p, cur, t, buf[b].rp, buf[b].cv, buf[b].inv, rs_s, lane, alive, l1);
+        walk_tile<G, V, ITEMS, PF, PAT, FUSE>(p, cur, t, buf[b].rp, buf[b].cv, buf[b].inv, rs_s, lane, alive, l1,
+                                              pend_s + b * KP, ep << 1);
         __syncwarp();                          // buffers and row sums are rewritten next iteration
+        if constexpr (FUSE) {
+            if (pend) {
+                pipe_finish<G, V, PAT>(p, pend_t, pend_first, pend_row, pend_w, pend_s + pslot * KP, probe, ep,
+                                       cv.hdr, lane, alive, l1);
+                pend = false;
+            }
+            if (cur.defer) {
+                pend = true;
+                pend_t = t;
+                pend_row = cur.x0;
+                pend_first = __ldg(p.head_first + t);
+                pend_w = PAT && p.mode == MODE_ACC ? __ldg(p.inv_deg + cur.x0) : 0.0f;
+                pslot = b;
+            }
+        }
         cur = nxt;
         nxt = after;
         b ^= 1;
     }
     cp_async_wait_group<0>();
+    if constexpr (FUSE) {
+        if (pend)
+            pipe_finish<G, V, PAT>(p, pend_t, pend_first, pend_row, pend_w, pend_s + pslot * KP, 0ull, ep, cv.hdr,
+                                   lane, alive, l1);
+        // L1 partial of the CTA; the last CTA to finish sums the partials in a
+        // fixed order and applies the break test of Algorithm 1 per column
+        __shared__ float s_l1[WARPS][KP];
+        __shared__ double s_fin[256];
+        __shared__ int s_last;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            float a = l1[j];
+#pragma unroll
+            for (int o = G; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane < G) s_l1[warp][col0 + j] = a;
+        }
+        __syncthreads();
+        if (threadIdx.x < KP) {
+            float a = 0.0f;
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) a += s_l1[w][threadIdx.x];
+            p.part[(int64_t)blockIdx.x * KP + threadIdx.x] = (double)a;
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = (atomicAdd(&cv.hdr->ticket, 1) == (int)gridDim.x - 1);
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        block_sum_partials_t<KP, double, WARPS * 32>(p.part, gridDim.x, s_fin);
+        if (threadIdx.x < KP) {
+            const int c = threadIdx.x;
+            const double a = s_fin[c];
+            if (c < p.k && cv.alive[c]) {
+                cv.norm[c] = a;
+                cv.iters[c] = p.iter;
+                if (a < p.eps && p.mode == MODE_ACC) cv.alive[c] = 0;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int any = 0;
+            for (int c = 0; c < p.k && c < KP; ++c) any |= cv.alive[c];
+            cv.hdr->done = any ? 0 : 1;
+            cv.hdr->ticket = 0;
+            cv.hdr->epoch = ep_raw + 1u;
+        }
+        return;
+    }
     // this warp's L1 partial over all its tiles (fixed order: deterministic
     // for a given grid), one row of tl1 per warp of the grid
 #pragma unroll
@@ -1265,43 +1526,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
     }
 }
 
-// Sum over b in [0, nb) of part[b * KP + c] for every column c < KP, by the
-// 256 threads of one block in a fixed order (so the result is deterministic):
-// group grp of the 256 / KP groups adds b = grp, grp + NG, ... in increasing b
-// (loads issued eight at a time), then thread c adds the group sums in group
-// order.  The result for column c is left in s_fin[c] (s_fin holds 256).
-template <int KP, class T>
-__device__ __forceinline__ void block_sum_partials_t(const T *part, unsigned nb, double *s_fin)
-{
-    static_assert(KP >= 1 && KP <= 256 && 256 % KP == 0, "KP");
-    constexpr unsigned NG = 256 / KP;
-    const int c = threadIdx.x % KP, grp = threadIdx.x / KP;
-    double a = 0.0;
-    unsigned b = grp;
-    for (; b + 7u * NG < nb; b += 8u * NG) {
-        double v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = __ldcg(&part[(int64_t)(b + i * NG) * KP + c]);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) a += v[i];
-    }
-    for (; b < nb; b += NG) a += __ldcg(&part[(int64_t)b * KP + c]);
-    __syncthreads();
-    s_fin[grp * KP + c] = a;
-    __syncthreads();
-    if (threadIdx.x < KP) {
-        double t = 0.0;
-        for (unsigned g = 0; g < NG; ++g) t += s_fin[g * KP + threadIdx.x];
-        s_fin[threadIdx.x] = t;   // only this thread reads or writes column c's group-0 slot
-    }
-    __syncthreads();
-}
-
-template <int KP>
-__device__ __forceinline__ void block_sum_partials(const double *part, unsigned nb, double *s_fin)
-{
-    block_sum_partials_t<KP, double>(part, nb, s_fin);
-}
 
 // --------------------------------------------------------------- fixup ---
 constexpr int FIX_WARPS = 8;

@@ -44,66 +44,6 @@ namespace tpa {
 
 constexpr int SEG_WARPS = 8;                 // 256 threads: block_sum_partials runs on them
 constexpr uint32_t SEG_ROW_START = 0x80000000u;
-constexpr long long SEG_SPIN_LIMIT = 1ll << 22;   // polls of one carry-out word (about a second)
-
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long seg_pack(float v, uint32_t tag)
-{
-    return ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v);
-}
-
-// Streaming 16-byte load of four column words (read once per launch).
-__device__ __forceinline__ uint4 ld_cols4(const uint32_t *p)
-{
-    uint4 r;
-    asm volatile("ld.global.cs.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "l"(p));
-    return r;
-}
-
-__device__ __forceinline__ float4 ld_vals4(const float *p)
-{
-    float4 r;
-    asm volatile("ld.global.cs.v4.f32 {%0,%1,%2,%3}, [%4];"
-                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-                 : "l"(p));
-    return r;
-}
-
-// Wait (bounded) for the carry-out word w of the current launch (tag `want`
-// in bits 33.., row-start flag in bit 32); returns the word, or a zero value
-// with the error flag raised when the wait gives up.  Once any wait of the
-// launch has given up, every other wait returns at once, so a launch ends
-// within about one wait limit whatever happens.
-__device__ __forceinline__ unsigned long long seg_wait(const unsigned long long *w, uint32_t want, Ctl *hdr)
-{
-    unsigned long long v = ld_relaxed_u64(w);
-    long long spins = 0;
-    unsigned ns = 32;
-    while ((uint32_t)(v >> 33) != want) {
-        if (++spins > SEG_SPIN_LIMIT || *(volatile int32_t *)&hdr->error) {
-            atomicOr(&hdr->error, 1);
-            return 0ull;
-        }
-        __nanosleep(ns);
-        if (ns < 256) ns <<= 1;
-        v = ld_relaxed_u64(w);
-    }
-    return v;
-}
-
 // Sum of the carry-outs of tiles t-1, t-2, ... back to and including the
 // nearest one in which a row starts (all of them down to tile 0 if none),
 // nearest first.  Warp-cooperative: tile t-1 first (lane j reads its word j),

@@ -144,8 +144,10 @@ def rmat17():
 
 
 def segmented_ids():
+    """Variants without a fixup launch: the segmented walks and the pipelined
+    kernel that finishes its deferred rows itself."""
     try:
-        return [v["index"] for v in tpa().variants() if v["name"].startswith("seg")]
+        return [v["index"] for v in tpa().variants() if v["name"].startswith(("seg", "pipef"))]
     except Exception:
         return [0]
 
@@ -153,8 +155,9 @@ def segmented_ids():
 @pytest.mark.parametrize("forced", segmented_ids(), indirect=True)
 def test_segmented_walk_many_tiles_per_warp(rmat17, forced, pattern):
     """R-MAT scale 17 (about 2 million nonzeros): every warp of the persistent
-    segmented grid walks several tiles, so the stage ring, the gathers sent
-    one tile ahead, the deferred rows and the look-back across warps all run."""
+    grid walks several tiles, so the stage ring, the gathers sent one tile
+    ahead, the rows deferred to the warp's next tile and the waits on other
+    warps' carry-outs all run."""
     t = tpa()
     kp = forced["kp"]
     if kp == 1:
