@@ -334,8 +334,8 @@ template <int G, int V, int ITEMS, int PF, int WARPS, int MINB, bool FUSE = fals
 static int64_t launch_spmvp(const Params &p, cudaStream_t s)
 {
     // one instantiation per product mode, so the valued kernel carries no test of it
-    constexpr size_t smem_v = WARPS * PipeSmem<G, V, ITEMS, false, FUSE>::PER_WARP;
-    constexpr size_t smem_p = WARPS * PipeSmem<G, V, ITEMS, true, FUSE>::PER_WARP;
+    constexpr size_t smem_v = WARPS * PipeSmem<G, V, ITEMS, false>::PER_WARP;
+    constexpr size_t smem_p = WARPS * PipeSmem<G, V, ITEMS, true>::PER_WARP;
     static_assert(smem_v <= 227 * 1024 && smem_p <= 227 * 1024, "shared memory per block");
     auto *const valued = spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB, false, FUSE>;
     auto *const pattern = spmvp_tile_k<G, V, ITEMS, PF, WARPS, MINB, true, FUSE>;

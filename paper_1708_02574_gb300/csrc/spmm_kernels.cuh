@@ -1175,13 +1175,11 @@ __device__ __forceinline__ void stage_tile(const Params &p, const TileMeta &m, c
     if (lane == 0) rp_s[nrows] = m.y0 + 0x7fffffff;
 }
 
-// FUSE: the deferred row's part goes to pend_s (shared memory) instead of
-// p.head, and the carry-out to the tagged words p.agg instead of p.carry.
+// FUSE: the carry-out goes to the tagged words p.agg instead of p.carry.
 template <int G, int V, int ITEMS, int PF, bool PAT, bool FUSE = false>
 __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, int64_t t, const int64_t *rp_s,
                                           const int32_t *cv_s, const float *inv_s, float *rs_s, int lane,
-                                          const int (&alive)[V], float (&l1)[V], float *pend_s = nullptr,
-                                          uint32_t tag = 0)
+                                          const int (&alive)[V], float (&l1)[V], uint32_t tag = 0)
 {
     constexpr int NW = 32 / G, KP = G * V;
     const int w = lane / G, col0 = (lane % G) * V;
@@ -1273,14 +1271,10 @@ __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, in
         float tot[V];
 #pragma unroll
         for (int j = 0; j < V; ++j) tot[j] = first_val[j] + (w > 0 ? prev[j] : 0.0f);
-        if (first_row == 0 && m.defer) {
-            if constexpr (FUSE)
-                st_row<V>(pend_s + col0, tot);
-            else
-                st_row<V>(p.head + t * KP + col0, tot);
-        } else {
+        if (first_row == 0 && m.defer)
+            st_row<V>(p.head + t * KP + col0, tot);
+        else
             st_row<V>(rs_s + first_row * KP + col0, tot);
-        }
     }
     if (w == NW - 1) {
         if constexpr (FUSE) {
@@ -1306,81 +1300,101 @@ __device__ __forceinline__ void walk_tile(const Params &p, const TileMeta &m, in
     }
 }
 
-// Shared memory per warp: two tile buffers and the row sums of one tile
-// (FUSE: and two slots for the part of a deferred row).
-template <int G, int V, int ITEMS, bool PAT, bool FUSE = false>
+// Shared memory per warp: two tile buffers and the row sums of one tile.
+template <int G, int V, int ITEMS, bool PAT>
 struct PipeSmem {
     using PT = PipeTile<G, V, ITEMS, PAT>;
     static constexpr size_t RS = (size_t)PT::L * G * V * sizeof(float);
-    static constexpr size_t PEND = FUSE ? ((size_t)2 * G * V * sizeof(float) + 15) / 16 * 16 : 0;
-    static constexpr size_t PER_WARP = 2 * sizeof(PT) + RS + PEND;
+    static constexpr size_t PER_WARP = 2 * sizeof(PT) + RS;
 };
 
-// Finish the deferred row `row` of tile pend_t inside the SpMM: its part in
-// pend_t (pend_s, KP floats) plus the carry-outs of tiles first .. pend_t-1,
-// read from the tagged words (bounded waits).  Lane (c, i) = (lane % KP,
-// lane / KP) adds column c of tiles first+i, first+i+32/KP, ... in order,
-// the lanes of a column are added in a fixed xor tree, and the G lanes of
-// walker 0 run the epilogue.  probe: the word of tile first+i loaded early.
-template <int G, int V, bool PAT>
-__device__ __forceinline__ void pipe_finish(const Params &p, int64_t pend_t, int64_t first, int32_t row, float w_row,
-                                            float *pend_s, unsigned long long probe, uint32_t ep, Ctl *hdr, int lane,
-                                            const int (&alive)[V], float (&l1)[V])
+// The deferred rows of one warp's tiles, finished after its last tile (the
+// fixup's work, inside the SpMM): lane l takes the warp's tiles l, l+32, ...
+// in turn; a row whose part began at most TAIL_SHORT tiles back is summed by
+// its lane (head part, then the carry-outs of the tiles it spans, in tile
+// order), a longer one (a hub's) by the whole warp in a fixed lane-strided
+// order.  Carry-outs are read from the tagged words (bounded waits; by now
+// nearly all of them are published).  The same sums in the same order as
+// fixup_small_k, so rows come out bit-identical to the launch with a fixup.
+constexpr int TAIL_SHORT = 32;
+
+// Add the KP carry-out words of tile u to acc: the loads first (all in
+// flight together), then the tag checks; a word of an earlier launch is
+// waited for (bounded).
+template <int KP>
+__device__ __forceinline__ void add_tagged_row(const Params &p, int64_t u, uint32_t ep, Ctl *hdr, float (&acc)[KP])
 {
-    constexpr int KP = G * V, LPC = 32 / KP;
-    static_assert(32 % KP == 0, "KP");
-    const int c = lane % KP, i = lane / KP;
-    float part = 0.0f;
-    int64_t u = first + i;
-    if (u < pend_t) {
-        unsigned long long w = probe;
-        if ((uint32_t)(w >> 33) != ep) w = seg_wait(p.agg + u * KP + c, ep, hdr);
-        part = __uint_as_float((uint32_t)w);
+    unsigned long long w[KP];
+#pragma unroll
+    for (int c = 0; c < KP; ++c) w[c] = ld_relaxed_u64(p.agg + u * KP + c);
+#pragma unroll
+    for (int c = 0; c < KP; ++c) {
+        if ((uint32_t)(w[c] >> 33) != ep) w[c] = seg_wait(p.agg + u * KP + c, ep, hdr);
+        acc[c] += __uint_as_float((uint32_t)w[c]);
     }
-    // longer spans (rows of hubs): four words in flight per lane
-    for (u += LPC; u < pend_t; u += 4 * LPC) {
-        unsigned long long w[4];
+}
+
+template <int KP>
+__device__ __forceinline__ void pipe_tail(const Params &p, int64_t t0, int64_t stride, uint32_t ep, const CtlView &cv,
+                                          int lane, float (&l1)[KP])
+{
+    int alive[KP];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int64_t uu = u + q * LPC;
-            w[q] = uu < pend_t ? ld_relaxed_u64(p.agg + uu * KP + c) : 0ull;
+    for (int c = 0; c < KP; ++c) alive[c] = cv.alive[c];
+    const int64_t mine = t0 < p.tiles ? (p.tiles - 1 - t0) / stride + 1 : 0;
+    for (int64_t j0 = 0; j0 < mine; j0 += 32) {
+        const int64_t j = j0 + lane;
+        const int64_t t = t0 + j * stride;
+        int32_t h = -1;
+        int64_t first = 0;
+        if (j < mine) {
+            h = __ldg(p.head_row + t);
+            if (h >= 0) first = __ldg(p.head_first + t);
         }
+        const bool longspan = h >= 0 && t - first > TAIL_SHORT;
+        if (h >= 0 && !longspan) {
+            float sum[KP];
+            ld_row_rw<KP>(p.head + t * KP, sum);
+            for (int64_t u = first; u < t; ++u) add_tagged_row<KP>(p, u, ep, cv.hdr, sum);
+            epilogue<KP, KP>(p, (int64_t)h, 0, sum, alive, l1);
+        }
+        unsigned lm = __ballot_sync(0xffffffffu, longspan);
+        while (lm) {
+            const int src = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const int64_t tt = __shfl_sync(0xffffffffu, t, src);
+            const int64_t ff = __shfl_sync(0xffffffffu, first, src);
+            float part[KP];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int64_t uu = u + q * LPC;
-            if (uu < pend_t) {
-                if ((uint32_t)(w[q] >> 33) != ep) w[q] = seg_wait(p.agg + uu * KP + c, ep, hdr);
-                part += __uint_as_float((uint32_t)w[q]);
+            for (int c = 0; c < KP; ++c) part[c] = 0.0f;
+            for (int64_t u = ff + lane; u < tt; u += 32) add_tagged_row<KP>(p, u, ep, cv.hdr, part);
+#pragma unroll
+            for (int c = 0; c < KP; ++c) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part[c] += __shfl_xor_sync(0xffffffffu, part[c], o);
+            }
+            if (lane == src) {
+                float sum[KP];
+                ld_row_rw<KP>(p.head + tt * KP, sum);
+#pragma unroll
+                for (int c = 0; c < KP; ++c) sum[c] += part[c];
+                epilogue<KP, KP>(p, (int64_t)h, 0, sum, alive, l1);
             }
         }
     }
-#pragma unroll
-    for (int o = KP; o < 32; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (lane < KP) pend_s[lane] += part;
-    __syncwarp();
-    if (lane < G) {
-        float sv[V];
-        ld_row_smem<V>(pend_s + lane * V, sv);
-        if (p.mode == MODE_ACC)
-            epilogue_red<KP, V, PAT ? PM_PATTERN : PM_VALUED>(p, (int64_t)row, lane * V, sv, alive, l1, w_row);
-        else
-            epilogue<KP, V, PAT ? PM_PATTERN : PM_VALUED>(p, (int64_t)row, lane * V, sv, alive, l1);
-    }
-    __syncwarp();
 }
 
 // MINB: resident blocks per SM requested from the register allocator.
-// FUSE: no fixup launch.  A tile whose first row began in an earlier tile
-// keeps that row's part in shared memory and finishes the row after the
-// warp's next tile (pipe_finish), from the carry-outs the earlier tiles
-// published as tagged words; the last CTA to finish reduces the L1 partials
-// and applies the break test.  The waits need every CTA resident: the grid
-// is launched cooperatively.
+// FUSE: no fixup launch.  Tiles publish their carry-outs as tagged words;
+// after its last tile each warp finishes the rows its tiles deferred
+// (pipe_tail), and the last CTA to finish reduces the L1 partials and
+// applies the break test.  The waits need every CTA resident: the grid is
+// launched cooperatively.
 template <int G, int V, int ITEMS, int PF, int WARPS, int MINB, bool PAT, bool FUSE = false>
 __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
 {
     using PT = PipeTile<G, V, ITEMS, PAT>;
-    using SM = PipeSmem<G, V, ITEMS, PAT, FUSE>;
+    using SM = PipeSmem<G, V, ITEMS, PAT>;
     constexpr int KP = G * V;
     static_assert(ITEMS % PF == 0, "PF");
     static_assert(PF <= 32, "PF");
@@ -1394,17 +1408,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
     unsigned char *base = pipe_smem + (size_t)warp * SM::PER_WARP;
     PT *buf = reinterpret_cast<PT *>(base);
     float *rs_s = reinterpret_cast<float *>(base + 2 * sizeof(PT));
-    float *pend_s = reinterpret_cast<float *>(base + 2 * sizeof(PT) + SM::RS);   // FUSE: 2 x KP floats
     uint32_t ep_raw = 0, ep = 0;
     if constexpr (FUSE) {
         ep_raw = *(volatile uint32_t *)&cv.hdr->epoch;
         ep = (ep_raw + 1u) & 0x7fffffffu;
     }
-    bool pend = false;   // FUSE: a deferred row waits for the warp's next tile
-    int64_t pend_t = 0, pend_first = 0;
-    int32_t pend_row = 0;
-    float pend_w = 0.0f;
-    int pslot = 0;
     int alive[V];
     float l1[V];
 #pragma unroll
@@ -1430,52 +1438,45 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
         cp_async_commit();
         const TileMeta after = tile_meta(p, t + 2 * stride);
         load_chunks<RC, PAT>(p, after, rg, lane);   // in flight during this walk
-        // FUSE: the first carry-out word the deferred row needs, loaded early
-        unsigned long long probe = 0ull;
-        if constexpr (FUSE) {
-            const int64_t u = pend_first + lane / KP;
-            if (pend && u < pend_t) probe = ld_relaxed_u64(p.agg + u * KP + lane % KP);
-        }
         cp_async_wait_group<1>();              // this tile's copies have landed
         __syncwarp();
         walk_tile<G, V, ITEMS, PF, PAT, FUSE>(p, cur, t, buf[b].rp, buf[b].cv, buf[b].inv, rs_s, lane, alive, l1,
-                                              pend_s + b * KP, ep << 1);
+                                              ep << 1);
         __syncwarp();                          // buffers and row sums are rewritten next iteration
-        if constexpr (FUSE) {
-            if (pend) {
-                pipe_finish<G, V, PAT>(p, pend_t, pend_first, pend_row, pend_w, pend_s + pslot * KP, probe, ep,
-                                       cv.hdr, lane, alive, l1);
-                pend = false;
-            }
-            if (cur.defer) {
-                pend = true;
-                pend_t = t;
-                pend_row = cur.x0;
-                pend_first = __ldg(p.head_first + t);
-                pend_w = PAT && p.mode == MODE_ACC ? __ldg(p.inv_deg + cur.x0) : 0.0f;
-                pslot = b;
-            }
-        }
         cur = nxt;
         nxt = after;
         b ^= 1;
     }
     cp_async_wait_group<0>();
     if constexpr (FUSE) {
-        if (pend)
-            pipe_finish<G, V, PAT>(p, pend_t, pend_first, pend_row, pend_w, pend_s + pslot * KP, 0ull, ep, cv.hdr,
-                                   lane, alive, l1);
+        // the rows this warp's tiles deferred (the head parts it stored are
+        // visible to its own lanes after the barrier)
+        __syncwarp();
+        float l1t[KP];
+#pragma unroll
+        for (int c = 0; c < KP; ++c) l1t[c] = 0.0f;
+        pipe_tail<KP>(p, (int64_t)blockIdx.x * WARPS + warp, stride, ep, cv, lane, l1t);
         // L1 partial of the CTA; the last CTA to finish sums the partials in a
         // fixed order and applies the break test of Algorithm 1 per column
         __shared__ float s_l1[WARPS][KP];
         __shared__ double s_fin[256];
         __shared__ int s_last;
 #pragma unroll
+        for (int c = 0; c < KP; ++c) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) l1t[c] += __shfl_xor_sync(0xffffffffu, l1t[c], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < KP; ++c) s_l1[warp][c] = l1t[c];
+        }
+        __syncwarp();
+#pragma unroll
         for (int j = 0; j < V; ++j) {
             float a = l1[j];
 #pragma unroll
             for (int o = G; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane < G) s_l1[warp][col0 + j] = a;
+            if (lane < G) s_l1[warp][col0 + j] += a;
         }
         __syncthreads();
         if (threadIdx.x < KP) {

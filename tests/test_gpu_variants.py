@@ -176,6 +176,13 @@ def test_segmented_walk_many_tiles_per_warp(rmat17, forced, pattern):
     out = t.query(rmat17["g"], seeds, S).cpu().numpy()
     again = t.query(rmat17["g"], seeds, S).cpu().numpy()
     assert np.array_equal(out, again), forced_name
+    if forced_name.startswith("pipef"):
+        # the same sums in the same order as the kernel with a fixup launch
+        t.set_variant(kp, -1)
+        base = t.query(rmat17["g"], seeds, S).cpu().numpy()
+        t.set_variant(kp, forced["index"])
+        if t.variants()[t.get_variant(kp)]["name"] == forced_name.replace("pipef", "pipe"):
+            assert np.array_equal(out, base), forced_name
     for j in sorted({0, kp // 2, kp - 1}):
         ref = oracle.query(rmat17["og"], int(seeds[j]), C, S, T, rmat17["rs"], EPS)
         parity(out[:, j], ref, f"{forced_name} col {j} seed {seeds[j]}")
