@@ -466,17 +466,20 @@ template <int KP>
 static void launch_fix(const Params &p, unsigned blocks, cudaStream_t s)
 {
     if constexpr (KP <= 8) {
-        (void)blocks;
-        fixup_small_k<KP><<<(unsigned)((p.tiles + 255) / 256), 256, 0, s>>>(p);
+        fixup_small_k<KP><<<blocks, 256, 0, s>>>(p);
     } else {
         fixup_k<KP><<<blocks, FIX_WARPS * 32, 0, s>>>(p);
     }
 }
 
-// Blocks of the fixup grid (the L1 partial buffer holds one row per block).
+// Blocks of the fixup grid (the L1 partial buffer holds one row per block);
+// the narrow fixup runs a persistent grid of FIX_SMALL_PER_SM blocks per SM.
+constexpr int FIX_SMALL_PER_SM = 4;
 static unsigned fix_grid(int KP, int64_t tiles)
 {
-    if (KP <= 8) return (unsigned)((tiles + 255) / 256);
+    if (KP <= 8)
+        return (unsigned)std::max<int64_t>(
+            1, std::min<int64_t>((tiles + 255) / 256, (int64_t)FIX_SMALL_PER_SM * num_sms()));
     return (unsigned)std::min<int64_t>((tiles + FIX_WARPS - 1) / FIX_WARPS, (int64_t)4 * num_sms());
 }
 

@@ -1643,52 +1643,58 @@ __global__ void __launch_bounds__(256) fixup_small_k(Params p)
 #pragma unroll
     for (int q = 0; q < V; ++q) alive[q] = cv.alive[q];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    const bool mine = t < p.tiles;
-    const int32_t h = mine ? p.head_row[t] : -1;
-    const int64_t first = mine ? (int64_t)p.head_first[t] : 0;
     float l1[V];
-    const bool has_l1 = mine && t < (p.l1_slots ? p.l1_slots : p.tiles);
 #pragma unroll
-    for (int q = 0; q < V; ++q) l1[q] = has_l1 ? p.tl1[t * V + q] : 0.0f;
-    const bool longspan = h >= 0 && t - first > FIX_SHORT;
-    if (h >= 0 && !longspan) {
-        float sum[V];
-        ld_row<V>(p.head + t * V, sum);
-        for (int64_t u = first; u < t; ++u) {
-            float c[V];
-            ld_row<V>(p.carry + u * V, c);
+    for (int q = 0; q < V; ++q) l1[q] = 0.0f;
+    // a persistent grid: each thread takes tiles blockIdx*256 + tid, then one
+    // grid further on (the block's loop count is uniform)
+    for (int64_t base = (int64_t)blockIdx.x * 256; base < p.tiles; base += (int64_t)gridDim.x * 256) {
+        const int64_t t = base + threadIdx.x;
+        const bool mine = t < p.tiles;
+        const int32_t h = mine ? p.head_row[t] : -1;
+        const int64_t first = mine ? (int64_t)p.head_first[t] : 0;
+        const bool has_l1 = mine && t < (p.l1_slots ? p.l1_slots : p.tiles);
 #pragma unroll
-            for (int q = 0; q < V; ++q) sum[q] += c[q];
-        }
-        epilogue<V, V>(p, (int64_t)h, 0, sum, alive, l1);
-    }
-    unsigned lm = __ballot_sync(0xffffffffu, longspan);
-    while (lm) {
-        const int src = __ffs(lm) - 1;
-        lm &= lm - 1;
-        const int64_t tt = __shfl_sync(0xffffffffu, t, src);
-        const int64_t ff = __shfl_sync(0xffffffffu, first, src);
-        float part[V];
-#pragma unroll
-        for (int q = 0; q < V; ++q) part[q] = 0.0f;
-        for (int64_t u = ff + lane; u < tt; u += 32) {
-            float c[V];
-            ld_row<V>(p.carry + u * V, c);
-#pragma unroll
-            for (int q = 0; q < V; ++q) part[q] += c[q];
-        }
-#pragma unroll
-        for (int q = 0; q < V; ++q) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part[q] += __shfl_xor_sync(0xffffffffu, part[q], o);
-        }
-        if (lane == src) {
+        for (int q = 0; q < V; ++q) l1[q] += has_l1 ? p.tl1[t * V + q] : 0.0f;
+        const bool longspan = h >= 0 && t - first > FIX_SHORT;
+        if (h >= 0 && !longspan) {
             float sum[V];
             ld_row<V>(p.head + t * V, sum);
+            for (int64_t u = first; u < t; ++u) {
+                float c[V];
+                ld_row<V>(p.carry + u * V, c);
 #pragma unroll
-            for (int q = 0; q < V; ++q) sum[q] += part[q];
+                for (int q = 0; q < V; ++q) sum[q] += c[q];
+            }
             epilogue<V, V>(p, (int64_t)h, 0, sum, alive, l1);
+        }
+        unsigned lm = __ballot_sync(0xffffffffu, longspan);
+        while (lm) {
+            const int src = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const int64_t tt = __shfl_sync(0xffffffffu, t, src);
+            const int64_t ff = __shfl_sync(0xffffffffu, first, src);
+            float part[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) part[q] = 0.0f;
+            for (int64_t u = ff + lane; u < tt; u += 32) {
+                float c[V];
+                ld_row<V>(p.carry + u * V, c);
+#pragma unroll
+                for (int q = 0; q < V; ++q) part[q] += c[q];
+            }
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part[q] += __shfl_xor_sync(0xffffffffu, part[q], o);
+            }
+            if (lane == src) {
+                float sum[V];
+                ld_row<V>(p.head + t * V, sum);
+#pragma unroll
+                for (int q = 0; q < V; ++q) sum[q] += part[q];
+                epilogue<V, V>(p, (int64_t)h, 0, sum, alive, l1);
+            }
         }
     }
     // block partial of the L1 norm, fixed order
