@@ -644,6 +644,10 @@ def main(argv=None):
 
     hbm, peak_kind = peaks()
 
+    # the gathers alone at this column pattern (tpa_probe_gather), the floor
+    # the SpMV/SpMM launches are compared with in the roofline objects
+    probe_ms = {kp: tpa.probe_gather(g, kp, reps=5) for kp in (1, 8)}
+
     names = {v["index"]: v["name"] for v in tpa.variants()}
 
     def roofline_of(fam):
@@ -668,6 +672,10 @@ def main(argv=None):
                 "traffic_over_alg": traffic / per_launch if traffic else None,
                 # edges traversed per second (each nonzero of CSR(A~^T) once per launch)
                 "gteps": m / avg_s / 1e9,
+                # one pass of the gathers alone (column ids in order, a row of kp
+                # floats gathered per nonzero, no row logic) and the launch over it
+                "gather_probe_ms": probe_ms.get(kp),
+                "launch_over_gather_probe": 1000.0 * avg_s / probe_ms[kp] if probe_ms.get(kp) else None,
                 "products": products,
                 "kernel": f"{fam}: SpMV/SpMM over CSR(A~^T), {variant}, {products} products",
                 "launches": sp["launches"], "avg_launch_ms": 1000.0 * avg_s,

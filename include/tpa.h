@@ -396,6 +396,14 @@ tpa_status tpa_profile_reset(int timing);
  * entries to out and the number of families to *count. */
 tpa_status tpa_profile_read(tpa_kernel_stat *out, int cap, int *count);
 
+/* Milliseconds per pass of a gather-only probe over the graph's CSR(A~^T):
+ * every column id read in order and the row of kp floats (1 or 8) of an
+ * iterate at that column gathered, with no rows, carries or epilogue - the
+ * floor the SpMV/SpMM kernels' gathers set at this column pattern.  Averaged
+ * over reps passes after one warm-up, on `stream` (synchronises it).  Uses
+ * a temporary n x kp buffer.  TPA_EINVAL for another kp or reps < 1. */
+tpa_status tpa_probe_gather(tpa_graph *g, int kp, int reps, void *stream, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,6 +32,7 @@ from .tpa import (  # noqa: F401
     launch_count,
     library,
     profile_read,
+    probe_gather,
     profile_reset,
     load_preprocessed,
     preprocess,

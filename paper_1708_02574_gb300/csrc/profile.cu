@@ -7,6 +7,7 @@
 // bandwidth of a kernel from event durations taken inside its timed region.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -97,6 +98,46 @@ void prof_end(const ProfMark &m, const char *family, double bytes, cudaStream_t 
     g_pending.push_back(Pending{family, m.a, b, bytes});
 }
 
+// Gather-rate probe: the column ids of CSR(A~^T) read in order and, for
+// each, the row of KP floats of an iterate at that column gathered and
+// summed, with no row structure, no carries and no epilogue: the cost of the
+// gathers alone at the graph's column pattern, against which the SpMM
+// kernels are compared.  Four gathers in flight per thread.
+template <int KP>
+__global__ void gather_probe_k(const int32_t *col, int64_t m, const float *x, float *out)
+{
+    constexpr int U = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float acc = 0.0f;
+    for (int64_t e0 = tid; e0 < m; e0 += U * stride) {
+        float v[U][KP];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = e0 + u * stride;
+#pragma unroll
+            for (int j = 0; j < KP; ++j) v[u][j] = 0.0f;
+            if (e < m) {
+                const float *row = x + (int64_t)__ldcs(col + e) * KP;
+                if constexpr (KP == 8) {
+                    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                        : "=f"(v[u][0]), "=f"(v[u][1]), "=f"(v[u][2]), "=f"(v[u][3]), "=f"(v[u][4]),
+                          "=f"(v[u][5]), "=f"(v[u][6]), "=f"(v[u][7])
+                        : "l"(row));
+                } else {
+                    v[u][0] = __ldg(row);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int j = 0; j < KP; ++j) acc += v[u][j];
+        }
+    }
+    out[tid] = acc;
+}
+
 }  // namespace tpa
 
 using namespace tpa;
@@ -150,6 +191,53 @@ tpa_status tpa_profile_read(tpa_kernel_stat *out, int cap, int *count)
             ++i;
         }
         if (count) *count = i;
+    } catch (const Fail &f) {
+        return f.st;
+    }
+    return TPA_OK;
+}
+
+tpa_status tpa_probe_gather(tpa_graph *g, int kp, int reps, void *stream, double *ms)
+{
+    clear_error();
+    try {
+        TPA_REQUIRE(g && ms, "tpa_probe_gather: NULL argument");
+        TPA_REQUIRE(kp == 1 || kp == 8, "tpa_probe_gather: kp = %d is neither 1 nor 8", kp);
+        TPA_REQUIRE(reps >= 1, "tpa_probe_gather: reps = %d < 1", reps);
+        cudaStream_t s = (cudaStream_t)stream;
+        int dev = 0, sms = 0;
+        TPA_CUDA(cudaGetDevice(&dev));
+        TPA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const unsigned blocks = (unsigned)sms * 8, threads = 256;
+        DevBuf x, out;
+        x.ensure((size_t)std::max<int64_t>(1, g->n) * kp * sizeof(float), s);
+        out.ensure((size_t)blocks * threads * sizeof(float), s);
+        TPA_CUDA(cudaMemsetAsync(x.p, 0, x.bytes, s));
+        cudaEvent_t a = nullptr, b = nullptr;
+        TPA_CUDA(cudaEventCreate(&a));
+        TPA_CUDA(cudaEventCreate(&b));
+        auto pass = [&]() {
+            if (kp == 8)
+                gather_probe_k<8><<<blocks, threads, 0, s>>>(g->col_t.as<int32_t>(), g->m, x.as<float>(),
+                                                             out.as<float>());
+            else
+                gather_probe_k<1><<<blocks, threads, 0, s>>>(g->col_t.as<int32_t>(), g->m, x.as<float>(),
+                                                             out.as<float>());
+            note_launch("probe");
+        };
+        pass();   // warm-up
+        TPA_CUDA(cudaEventRecord(a, s));
+        for (int i = 0; i < reps; ++i) pass();
+        TPA_CUDA(cudaEventRecord(b, s));
+        TPA_CUDA(cudaEventSynchronize(b));
+        float t = 0.0f;
+        TPA_CUDA(cudaEventElapsedTime(&t, a, b));
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        TPA_CHECK_LAUNCH();
+        x.release(s);
+        out.release(s);
+        *ms = (double)t / reps;
     } catch (const Fail &f) {
         return f.st;
     }

@@ -82,6 +82,7 @@ def library():
         "tpa_seed_order": (i32, [P, i32, i32, P]),
         "tpa_profile_reset": (i32, [i32]),
         "tpa_profile_read": (i32, [P, i32, ctypes.POINTER(i32)]),
+        "tpa_probe_gather": (i32, [P, i32, i32, P, ctypes.POINTER(f64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -314,6 +315,13 @@ def launch_count() -> int:
 def profile_reset(timing: bool = False) -> None:
     """Clear kernel statistics; with timing, bracket SpMV/SpMM and fixup launches with CUDA events."""
     _check(library().tpa_profile_reset(1 if timing else 0))
+
+
+def probe_gather(g, kp: int, reps: int = 5) -> float:
+    """tpa_probe_gather: ms per pass of the gather-only probe (kp = 1 or 8) over g's CSR(A~^T)."""
+    ms = ctypes.c_double(0.0)
+    _check(library().tpa_probe_gather(g.handle, int(kp), int(reps), _stream(), ctypes.byref(ms)))
+    return ms.value
 
 
 def profile_read() -> dict:
