@@ -312,8 +312,10 @@ void tpa_free_graph(tpa_graph *g)
     for (DevBuf *b : bufs) b->release(s);
     g->ws.cpart.release(s);
     g->ws.agg.release(s);
+    g->ws.lrec.release(s);
+    g->ws.ltail.release(s);
     for (tpa::SegRows *R : {&g->seg_t, &g->seg_a})
-        for (DevBuf *b : {&R->colf, &R->nz_rows, &R->empty_rows, &R->nzpos}) b->release(s);
+        for (DevBuf *b : {&R->colf, &R->nz_rows, &R->empty_rows, &R->nzpos, &R->nzrp}) b->release(s);
     for (auto *tiles : {&g->segt_t, &g->segt_a})
         for (auto &kv : *tiles) kv.second.crow0.release(s);
     for (tpa::BinPlan *B : {&g->bins_t, &g->bins_a})

@@ -40,6 +40,7 @@
 #include "spmm_kernels.cuh"
 #include "spmm_binned.cuh"
 #include "spmm_seg.cuh"
+#include "spmm_lane.cuh"
 
 namespace tpa {
 
@@ -402,6 +403,37 @@ static int64_t launch_seg(const Params &p, cudaStream_t s)
 // Upper bound of the CTAs of any persistent grid (32 resident blocks per SM at most).
 static int64_t seg_grid_bound() { return (int64_t)32 * num_sms(); }
 
+// Lane-segment walk (spmm_lane.cuh): the walk over segments of R nonzeros,
+// then the finishing launch (rows, epilogue, L1, break test) in the fixup's
+// place; returns the CTAs of the walk.
+template <int V, int R, int PF>
+static int64_t launch_lane(const Params &p, cudaStream_t s)
+{
+    auto *const valued = spmm_lane_k<V, R, PF, false>;
+    auto *const pattern = spmm_lane_k<V, R, PF, true>;
+    static int per_sm_v = 0, per_sm_p = 0;
+    if (!per_sm_v) {
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_v, valued, 256, 0));
+        TPA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_p, pattern, 256, 0));
+        per_sm_v = std::max(per_sm_v, 1);
+        per_sm_p = std::max(per_sm_p, 1);
+    }
+    const int per_sm = p.inv_deg ? per_sm_p : per_sm_v;
+    const int64_t grid =
+        std::max<int64_t>(1, std::min<int64_t>((p.seg_tiles + 255) / 256, (int64_t)per_sm * num_sms()));
+    if (p.inv_deg) pattern<<<(unsigned)grid, 256, 0, s>>>(p);
+    else valued<<<(unsigned)grid, 256, 0, s>>>(p);
+    return grid;
+}
+
+template <int V, int R>
+static void launch_lane_finish(const Params &p, unsigned, cudaStream_t s)
+{
+    const int64_t rows = std::max<int64_t>(1, p.n - p.n_empty);
+    const unsigned grid = (unsigned)std::min<int64_t>((rows + 255) / 256, (int64_t)8 * num_sms());
+    lane_finish_k<V, R><<<grid, 256, 0, s>>>(p);
+}
+
 // Binned-row kernels (spmm_binned.cuh): short, medium, chunks of long rows,
 // long-row combine, empty rows; returns the rows of tl1 written.
 template <int KP>
@@ -490,6 +522,7 @@ struct Variant {
     const char *name;
     bool binned = false;   // binned-row kernels (need the row bins bound to Params)
     bool seg = false;      // segmented flag walk: no fixup; tiles of cfg.L() nonzeros
+    bool lane = false;     // lane-segment walk (with seg): segments of cfg.L() nonzeros, a finishing launch
 };
 
 #define TPA_VARIANT(G, V, I, PF) \
@@ -501,6 +534,8 @@ struct Variant {
 #define TPA_VARIANTB(KP) {{1, KP, 4, 4, 32}, launch_binned<KP>, launch_bin_finish<KP>, "bins<" #KP ">", true}
 #define TPA_VARIANTS(V, R, PF, NB) \
     {{1, V, R, PF, 32}, launch_seg<V, R, PF, NB, false>, nullptr, "seg<" #V "," #R "," #PF "," #NB ">", false, true}
+#define TPA_VARIANTL(V, R, PF) \
+    {{1, V, R, PF, 1}, launch_lane<V, R, PF>, launch_lane_finish<V, R>, "lane<" #V "," #R "," #PF ">", false, true, true}
 #define TPA_VARIANTA(V, R, PF, NB) \
     {{1, V, R, PF, 32}, launch_seg<V, R, PF, NB, true>, nullptr, "sega<" #V "," #R "," #PF "," #NB ">", false, true}
 #define TPA_VARIANTPF(G, V, I, PF, W, MB)                                \
@@ -521,6 +556,9 @@ static const Variant kVariants[] = {
     TPA_VARIANTS(2, 8, 8, 3),
     TPA_VARIANTS(4, 8, 8, 3),
     TPA_VARIANTPF(2, 4, 8, 8, 4, 5),
+    TPA_VARIANTL(8, 32, 4),
+    TPA_VARIANTL(8, 32, 2),
+    TPA_VARIANTL(1, 32, 8),
     TPA_VARIANTS(8, 8, 4, 2),
     TPA_VARIANTS(1, 4, 4, 4),
     TPA_VARIANTS(8, 8, 8, 2),
@@ -711,6 +749,27 @@ static unsigned size_for_variant(tpa_graph *g, const Variant &var, int which, in
         need(W.fix, fix_bytes, "L1 partials");
         bind_seg(p, g, which, var.cfg.L(), KP, s);
         p.tiles = 0;
+        if (var.lane) {   // row parts by rank, segment-end sums, row bounds by rank
+            SegRows &SR = which ? g->seg_a : g->seg_t;
+            if (!SR.nzrp.p) {
+                SR.nzrp.ensure((size_t)(SR.n_nz + 1) * sizeof(int64_t), s);
+                lane_bounds_k<<<grid_1d(SR.n_nz + 1, 256), 256, 0, s>>>(
+                    which ? g->rp_a.as<int64_t>() : g->rp_t.as<int64_t>(), SR.nz_rows.as<int32_t>(), SR.n_nz, g->m,
+                    SR.nzrp.as<int64_t>());
+                note_launch("plan");
+                TPA_CHECK_LAUNCH();
+            }
+            need(SR.nzrp, (size_t)(SR.n_nz + 1) * sizeof(int64_t), "row bounds");
+            p.nzrp = SR.nzrp.as<int64_t>();
+            const size_t rec_bytes = (size_t)std::max<int64_t>(1, g->n - p.n_empty) * KP * sizeof(float);
+            const size_t tail_bytes = (size_t)std::max<int64_t>(1, (p.seg_tiles + 31) / 32) * KP * sizeof(float);
+            W.lrec.ensure(rec_bytes, s);
+            W.ltail.ensure(tail_bytes, s);
+            need(W.lrec, rec_bytes, "row parts");
+            need(W.ltail, tail_bytes, "segment sums");
+            p.lrec = W.lrec.as<float>();
+            p.ltail = W.ltail.as<float>();
+        }
         return 0;
     }
     const Plan &P = get_plan(g, var.cfg.L(), s, which);

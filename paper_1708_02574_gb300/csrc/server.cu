@@ -107,7 +107,7 @@ std::vector<uint64_t> identity(const tpa_graph *g)
     };
     const Workspace &w = g->ws;
     for (const DevBuf *b : {&w.x, &w.y, &w.r, &w.carry, &w.head, &w.tl1, &w.fix, &w.ctl, &w.seeds, &w.sets,
-                            &w.seeds_g, &w.cols, &w.out, &w.iters, &w.u, &w.touched, &w.x2, &w.cpart, &w.agg})
+                            &w.seeds_g, &w.cols, &w.out, &w.iters, &w.u, &w.touched, &w.x2, &w.cpart, &w.agg, &w.lrec, &w.ltail})
         addr(*b);
     v.push_back((uint64_t)(uintptr_t)w.hflag);
     for (const DevBuf *b : {&g->rp_t, &g->col_t, &g->val_t, &g->rp_a, &g->col_a, &g->val_a, &g->outdeg, &g->inv_deg32,
@@ -121,7 +121,7 @@ std::vector<uint64_t> identity(const tpa_graph *g)
                 addr(*b);
         }
     for (const SegRows *R : {&g->seg_t, &g->seg_a})
-        for (const DevBuf *b : {&R->colf, &R->nz_rows, &R->empty_rows, &R->nzpos}) addr(*b);
+        for (const DevBuf *b : {&R->colf, &R->nz_rows, &R->empty_rows, &R->nzpos, &R->nzrp}) addr(*b);
     for (const auto *tiles : {&g->segt_t, &g->segt_a})
         for (const auto &kv : *tiles) {
             v.push_back((uint64_t)kv.first);

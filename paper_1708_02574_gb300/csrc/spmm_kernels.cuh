@@ -114,6 +114,12 @@ struct Params {
     int zero_mode;
     int zk;
     const int32_t *zseeds;
+    // Lane-segment walk (spmm_lane.cuh): the part of every row that ends
+    // inside a segment, by the row's rank among the nonempty rows, and the
+    // running sum at the end of every segment ([n_nz][KP] and [segments][KP]).
+    float *lrec;
+    float *ltail;
+    const int64_t *nzrp;   // first nonzero of each nonempty row by rank, then m
 };
 
 enum Gate : int { GATE_NONE = 0, GATE_PULL = 1, GATE_PUSH = 2 };
@@ -1509,21 +1515,21 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spmvp_tile_k(Params p)
             cv.hdr->ticket = 0;
             cv.hdr->epoch = ep_raw + 1u;
         }
-        return;
-    }
-    // this warp's L1 partial over all its tiles (fixed order: deterministic
-    // for a given grid), one row of tl1 per warp of the grid
+    } else {
+        // this warp's L1 partial over all its tiles (fixed order: deterministic
+        // for a given grid), one row of tl1 per warp of the grid
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-        float a = l1[j];
+        for (int j = 0; j < V; ++j) {
+            float a = l1[j];
 #pragma unroll
-        for (int o = G; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        l1[j] = a;
-    }
-    if (lane < G) {
-        const int64_t slot = (int64_t)blockIdx.x * WARPS + warp;
+            for (int o = G; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            l1[j] = a;
+        }
+        if (lane < G) {
+            const int64_t slot = (int64_t)blockIdx.x * WARPS + warp;
 #pragma unroll
-        for (int j = 0; j < V; ++j) p.tl1[slot * (G * V) + col0 + j] = l1[j];
+            for (int j = 0; j < V; ++j) p.tl1[slot * (G * V) + col0 + j] = l1[j];
+        }
     }
 }
 

@@ -105,6 +105,7 @@ struct SegRows {
     bool built = false;
     int64_t n_nz = 0, n_empty = 0, padded = 0;
     DevBuf colf, nz_rows, empty_rows, nzpos;
+    DevBuf nzrp;   // lane-segment walk: first nonzero of every nonempty row, then m (int64[n_nz + 1])
 };
 // Tiles of tn nonzeros: crow0[t] (int32[tiles + 1]) is the number of rows
 // that start before tile t.
@@ -144,6 +145,7 @@ struct Workspace {
     DevBuf x2;              // push path: x2 [n][KP <= 16], zero outside the marked rows
     DevBuf cpart;           // binned-row kernels: chunk sums of long rows [chunks][KP]
     DevBuf agg;             // segmented kernel: tagged carry-out words [tiles][KP] (zeroed when allocated)
+    DevBuf lrec, ltail;     // lane-segment walk: row parts [n_nz][KP], segment-end sums [segments][KP]
     bool u_clean = false;   // u, touched and x2 are known to be all zero
     // The segmented walk never writes the rows of y without in-edges, so they
     // must already read as zero.  x_zkp / y_zkp: the padded width KP for

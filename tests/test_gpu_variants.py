@@ -144,10 +144,11 @@ def rmat17():
 
 
 def segmented_ids():
-    """Variants without a fixup launch: the segmented walks and the pipelined
-    kernel that finishes its deferred rows itself."""
+    """Variants without the merge-path fixup: the segmented walks, the
+    pipelined kernel that finishes its deferred rows itself, and the
+    lane-segment walk with its finishing launch."""
     try:
-        return [v["index"] for v in tpa().variants() if v["name"].startswith(("seg", "pipef"))]
+        return [v["index"] for v in tpa().variants() if v["name"].startswith(("seg", "pipef", "lane"))]
     except Exception:
         return [0]
 
