@@ -655,7 +655,12 @@ def main(argv=None):
         if sp.get("total_ms", 0) <= 0:
             return None
         kp = int(fam[len("spmm_kp"):])
-        avg_s = sp["total_ms"] / 1000.0 / max(1, sp["launches"])
+        # one SpMV/SpMM = the walk and, for the lane-segment walk, its finishing
+        # launch (rows, epilogue, L1 norm, break test), timed as finish_kpK
+        fin = stats.get(f"finish_kp{kp}", {})
+        walk_s = sp["total_ms"] / 1000.0 / max(1, sp["launches"])
+        fin_s = fin.get("total_ms", 0.0) / 1000.0 / max(1, fin.get("launches", 0)) if fin.get("launches") else 0.0
+        avg_s = walk_s + fin_s
         # the contract's bytes: 8m + 20n per SpMV, 8m + 4n + 16nk per k-column
         # SpMM (every launch of the bench's chunks has k = kp columns)
         per_launch = s8d_bytes(n, m, kp)
@@ -677,14 +682,16 @@ def main(argv=None):
                 "gather_probe_ms": probe_ms.get(kp),
                 "launch_over_gather_probe": 1000.0 * avg_s / probe_ms[kp] if probe_ms.get(kp) else None,
                 "products": products,
-                "kernel": f"{fam}: SpMV/SpMM over CSR(A~^T), {variant}, {products} products",
+                "kernel": (f"{fam} + finish_kp{kp}" if fin_s else fam)
+                          + f": SpMV/SpMM over CSR(A~^T), {variant}, {products} products",
                 "launches": sp["launches"], "avg_launch_ms": 1000.0 * avg_s,
+                "walk_ms": 1000.0 * walk_s, "finish_ms": 1000.0 * fin_s,
                 "alg_bytes_per_launch": per_launch,
                 "alg_bytes_rule": "8m + 20n (k = 1) or 8m + 4n + 16nk per launch, m after merging duplicates",
                 "moved_bytes_per_launch": moved, "achieved_moved": moved / avg_s / 1e9,
                 "frac_moved": moved / avg_s / 1e9 / hbm,
                 "peak_source": f"{peak_kind} hbm_gbs (copy), burst",
-                "kernel_share_of_step": sp["total_ms"] / (1000.0 * t_rank)}
+                "kernel_share_of_step": (sp["total_ms"] + fin.get("total_ms", 0.0)) / (1000.0 * t_rank)}
 
     fams = [f for f in stats if f.startswith("spmm_kp")]
     dominant = max(fams, key=lambda f: stats[f]["total_ms"]) if fams else None
@@ -774,8 +781,8 @@ def measure_e2e(args, tpa, torch, n, src, dst, seeds):
         step()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    # what the host link gives a plain copy of the same bytes (the scores are
-    # written by the kernels straight into the pinned buffer instead)
+    # what the host link gives a plain copy of the same bytes (tpa_query
+    # copies the scores by column groups while the next group computes)
     link = {}
     try:
         dev = torch.empty((n, Q), dtype=torch.float32, device="cuda")

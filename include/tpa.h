@@ -99,14 +99,15 @@ tpa_status tpa_get_stranger(const tpa_graph *g, float *out, int64_t *iters, void
  * push branch takes (256) are swapped into the last chunks of the query, so
  * that the other chunks push x1 and x2, and the swapped columns are put back
  * at the end; results then agree with unmoved seeds to FP32 rounding.
- * With out in page-locked host memory the kernels write the scores into it
- * directly (no swap) when its rows are 16-byte aligned (k a multiple of 4;
- * otherwise the scores are staged in device memory and copied once), or,
- * with tpa_set_output_group_width(w) and k >= 2w,
- * the seeds run in column groups of w: each group is computed into a device
- * buffer (two are kept, n x w floats each), with the swap above inside the
- * group, and copied to out while the next group computes.  Host outputs are
- * complete when the call returns.
+ * With out in page-locked host memory and k >= 2w (w = 128 columns where
+ * two device buffers of n x 128 floats fit in 8 GiB, else 64 where those
+ * fit; see tpa_set_output_group_width), the seeds run in column groups of w:
+ * each group is computed into one of two device buffers (n x w floats
+ * each), with the swap above inside the group, and copied to out by the copy
+ * engine while the next group computes.  Otherwise the kernels write the
+ * scores into page-locked memory directly (no swap) when its rows are
+ * 16-byte aligned (k a multiple of 4), else the scores are staged in device
+ * memory and copied once.  Host outputs are complete when the call returns.
  * Requires 1 <= S <= T, k >= 1, 0 <= seeds[j] < n.
  * Errors: TPA_ESTATE before tpa_preprocess; TPA_EINVAL.
  */
@@ -283,11 +284,10 @@ tpa_status tpa_set_cpi_batch_width(int width);
 int tpa_get_cpi_batch_width(void);
 
 /* Column groups of a tpa_query whose output is page-locked host memory (see
- * tpa_query): width = 0 (the default) has the kernels write the host memory
- * directly; a multiple of 8 in [8, 4096] computes groups of that many
- * columns in device memory and copies each to the host while the next one
- * computes (for k >= 2 x width).  TPA_EINVAL for another value.  The getter
- * returns the setting. */
+ * tpa_query): width = 0 (the default) picks 128 or 64 columns from the graph
+ * size, -1 has the kernels write the host memory directly, and a multiple of
+ * 8 in [8, 4096] fixes the group width (for k >= 2 x width).  TPA_EINVAL for
+ * another value.  The getter returns the setting. */
 tpa_status tpa_set_output_group_width(int width);
 int tpa_get_output_group_width(void);
 

@@ -208,15 +208,23 @@ using namespace tpa;
     return TPA_OK;
 
 // Columns per group when a query's scores go to page-locked host memory
-// through device buffers (tpa_set_output_group_width; 0: the kernels write
-// the host memory directly, the default).  Grouping applies from two groups
-// on, so that a copy overlaps a computation.
+// through device buffers (tpa_set_output_group_width): -1 makes the kernels
+// write the host memory directly; 0, the default, takes 128 columns where
+// two buffers of n x 128 floats fit in 8 GiB, else 64 where those fit, else
+// direct writes.  Grouping applies from two groups on, so that a copy
+// overlaps a computation.
 static std::atomic<int> g_group_width{0};
 
-static int stage_width(int k)
+static int stage_width(int64_t n, int k)
 {
-    const int w = g_group_width.load();
-    return w > 0 && k >= 2 * w ? w : 0;
+    int w = g_group_width.load();
+    if (w < 0) return 0;
+    if (w == 0) {
+        w = 128;
+        while (w >= 64 && 2.0 * (double)n * w * sizeof(float) > (double)(8ull << 30)) w /= 2;
+        if (w < 64) return 0;
+    }
+    return k >= 2 * w ? w : 0;
 }
 
 // Algorithm 3 for the columns of a host output in groups of gw: group i is
@@ -443,17 +451,17 @@ tpa_status tpa_query(tpa_graph *g, const int32_t *seeds, int k, int S, float *ou
     std::vector<int32_t> hs = read_seeds(seeds, k, g->n, s);
     g->ws.seeds.ensure((size_t)k * sizeof(int32_t), s);
     TPA_CUDA(cudaMemcpyAsync(g->ws.seeds.p, hs.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    // Host output.  Page-locked memory is written by the kernels directly
-    // (over the host link, while later chunks compute), or, with a group
-    // width set, filled by column groups: each group is computed into a
-    // device buffer and copied to the host by the copy engine while the next
-    // group computes.  Other host memory is staged and copied at the end.
+    // Host output.  Page-locked memory is filled by column groups: each group
+    // is computed into a device buffer and copied to the host by the copy
+    // engine while the next group computes (or, for few columns or
+    // tpa_set_output_group_width(-1), written by the kernels directly).
+    // Other host memory is staged and copied at the end.
     const bool host_out = !is_device_ptr(out);
     float *mapped = host_out ? static_cast<float *>(mapped_host_ptr(out)) : nullptr;
     // rows not 16-byte aligned would take 4-byte stores over the host link:
     // stage those in device memory and copy once
     if (mapped && (k * sizeof(float)) % 16 != 0) mapped = nullptr;
-    const int gw = mapped ? stage_width(k) : 0;
+    const int gw = mapped ? stage_width(g->n, k) : 0;
     float *dout = out;
     if (host_out && !gw) {
         if (mapped) {
@@ -769,8 +777,8 @@ tpa_status tpa_load_preprocessed(tpa_graph *g, const char *path, void *stream)
 tpa_status tpa_set_output_group_width(int width)
 {
     clear_error();
-    if (!(width == 0 || (width >= 8 && width <= 4096 && width % 8 == 0))) {
-        set_error("tpa_set_output_group_width: %d is neither 0 nor a multiple of 8 in [8, 4096]", width);
+    if (!(width == 0 || width == -1 || (width >= 8 && width <= 4096 && width % 8 == 0))) {
+        set_error("tpa_set_output_group_width: %d is not 0, -1 or a multiple of 8 in [8, 4096]", width);
         return TPA_EINVAL;
     }
     g_group_width.store(width);

@@ -547,6 +547,10 @@ struct Variant {
 // The first variant of each padded width is its default (the fastest measured
 // on R-MAT scale 22 queries); the autotuner may pick any other.
 static const Variant kVariants[] = {
+    TPA_VARIANTL(1, 32, 8),
+    TPA_VARIANTL(2, 32, 8),
+    TPA_VARIANTL(4, 32, 4),
+    TPA_VARIANTL(8, 32, 4),
     TPA_VARIANTW(1, 6, 8),
     TPA_VARIANTW(2, 6, 8),
     TPA_VARIANTP(1, 4, 4, 4, 8, 1),
@@ -556,9 +560,7 @@ static const Variant kVariants[] = {
     TPA_VARIANTS(2, 8, 8, 3),
     TPA_VARIANTS(4, 8, 8, 3),
     TPA_VARIANTPF(2, 4, 8, 8, 4, 5),
-    TPA_VARIANTL(8, 32, 4),
     TPA_VARIANTL(8, 32, 2),
-    TPA_VARIANTL(1, 32, 8),
     TPA_VARIANTS(8, 8, 4, 2),
     TPA_VARIANTS(1, 4, 4, 4),
     TPA_VARIANTS(8, 8, 8, 2),
@@ -718,6 +720,17 @@ static const char *spmm_family(int KP)
 {
     static const char *names[] = {"spmm_kp1", "spmm_kp2", "spmm_kp4", "spmm_kp8", "spmm_kp16",
                                   "spmm_kp32", "spmm_kp64", "spmm_kp128", "spmm_kp256"};
+    int i = 0;
+    while ((1 << i) < KP && i < 8) ++i;
+    return names[i];
+}
+
+// The finishing launch of the lane-segment walk (the rows, their epilogue,
+// the L1 norm and the break test), timed apart from the walk.
+static const char *finish_family(int KP)
+{
+    static const char *names[] = {"finish_kp1", "finish_kp2", "finish_kp4", "finish_kp8", "finish_kp16",
+                                  "finish_kp32", "finish_kp64", "finish_kp128", "finish_kp256"};
     int i = 0;
     while ((1 << i) < KP && i < 8) ++i;
     return names[i];
@@ -1023,10 +1036,11 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
             prof_end(pm, spmm_family(KP), spmm_bytes(n, g->m, KP, kc, p.mode, p.accumulate, p.inv_deg != nullptr), s);
             note_launch(spmm_family(KP));
             if (var.fix) {
+                const char *fam = var.lane ? finish_family(KP) : "fixup";
                 ProfMark pf = prof_begin(s);
                 var.fix(p, fix_blocks, s);
-                prof_end(pf, "fixup", 0.0, s);
-                note_launch("fixup");
+                prof_end(pf, fam, 0.0, s);
+                note_launch(fam);
             }
             if (p.mode == MODE_FINAL) {
                 if (var.seg)
@@ -1240,8 +1254,11 @@ void spmv_apply(tpa_graph *g, int which, const float *x, float *y, int kc, float
     note_launch("init");
     note_launch(spmm_family(KP));
     if (var.fix) {
+        const char *fam = var.lane ? finish_family(KP) : "fixup";
+        ProfMark pf = prof_begin(s);
         var.fix(p, fix_blocks, s);
-        note_launch("fixup");
+        prof_end(pf, fam, 0.0, s);
+        note_launch(fam);
     }
     TPA_CHECK_LAUNCH();
 }

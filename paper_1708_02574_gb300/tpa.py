@@ -380,7 +380,7 @@ def cpi_step_noalloc(n: int, m: int, row_ptr, col, val, c: float, x, y, r=None, 
 
 
 def set_output_group_width(width: int) -> None:
-    """Column groups of a query into page-locked host memory: 0 direct writes (default), else the width."""
+    """Column groups of a query into page-locked host memory: 0 automatic (default), -1 direct writes, else the width."""
     _check(library().tpa_set_output_group_width(int(width)))
 
 

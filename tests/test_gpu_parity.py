@@ -161,14 +161,14 @@ def test_host_buffers_through_c_abi(rmat14):
     assert np.array_equal(out, dev)
 
 
-@pytest.mark.parametrize("k,group", [(13, 0), (152, 0), (150, 72), (600, 256)])
+@pytest.mark.parametrize("k,group", [(13, -1), (152, -1), (150, 72), (600, 256), (600, 0)])
 def test_pinned_host_output(rmat14, k, group):
     """Page-locked host output: the kernels write the scores straight into it
     (152 columns: 16-byte rows), or it is staged in device memory and copied
     once (13 columns: rows not 16-byte aligned), or column groups are computed
     in device buffers and copied while the next group computes (150 columns
     in groups of 72: three groups, the third reusing the first one's buffer;
-    600 in groups of 256)."""
+    600 in groups of 256; 600 with the default groups of 128)."""
     import torch
     t = tpa()
     seeds = synth.query_seeds(rmat14["cand"], k, key=14)
