@@ -369,7 +369,7 @@ def peaks():
 def kernel_source_hash() -> str:
     """Identity of the SpMV/SpMM device code (the files that define the kernels and Params)."""
     h = hashlib.sha256()
-    for f in ("spmm_kernels.cuh", "spmm_binned.cuh"):
+    for f in ("spmm_kernels.cuh", "spmm_binned.cuh", "spmm_lane.cuh"):
         with open(os.path.join(ROOT, "paper_1708_02574_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

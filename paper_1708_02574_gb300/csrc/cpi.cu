@@ -1044,7 +1044,7 @@ void run_cpi_chunk(tpa_graph *g, const CpiArgs &a, int k0, int kc, cudaStream_t 
             }
             if (p.mode == MODE_FINAL) {
                 if (var.seg)
-                    finalize_seg_k<<<grid_1d(n * kc, 256), 256, 0, s>>>(W.ctl.p, p.empty_rows, p.n_empty, r, ldr,
+                    finalize_seg_k<<<grid_1d(n, 256), 256, 0, s>>>(W.ctl.p, p.empty_rows, p.n_empty, r, ldr,
                                                                         a.r_str, p.one_plus_alpha, p.out, p.ldo, n,
                                                                         kc);
                 else   // usually returns at once: a grid of 8 blocks per SM (grid-stride when it works)

@@ -941,13 +941,23 @@ __global__ void finalize_seg_k(const void *ctl, const int32_t *empty_rows, int64
     const CtlView cv = ctl_view(const_cast<void *>(ctl));
     const bool all = *(volatile int32_t *)&cv.hdr->done != 0;
     const int64_t rows = all ? n : n_empty;
-    const int64_t total = rows * k;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t rr = i / k;
-        const int j = (int)(i % k);
+    // thread per row; 16-byte loads and stores when the rows allow them
+    const bool vec = k % 4 == 0 && ldr % 4 == 0 && ldo % 4 == 0 && (reinterpret_cast<uintptr_t>(r) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    for (int64_t rr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; rr < rows; rr += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = all ? rr : (int64_t)empty_rows[rr];
-        out[v * ldo + j] = fmaf(opa, r[v * ldr + j], r_str[v]);
+        const float rs = r_str[v];
+        if (vec) {
+            for (int j = 0; j < k; j += 4) {
+                const float4 a = *reinterpret_cast<const float4 *>(r + v * ldr + j);
+                *reinterpret_cast<float4 *>(out + v * ldo + j) =
+                    make_float4(fmaf(opa, a.x, rs), fmaf(opa, a.y, rs), fmaf(opa, a.z, rs), fmaf(opa, a.w, rs));
+            }
+        } else {
+            for (int j = 0; j < k; ++j) out[v * ldo + j] = fmaf(opa, r[v * ldr + j], rs);
+        }
     }
+}
 }
 
 // ---------------------------------------------------- plan of the walk ---
