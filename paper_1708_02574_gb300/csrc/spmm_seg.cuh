@@ -958,7 +958,6 @@ __global__ void finalize_seg_k(const void *ctl, const int32_t *empty_rows, int64
         }
     }
 }
-}
 
 // ---------------------------------------------------- plan of the walk ---
 // nzf[v] = 1 when row v has a nonzero, ef[v] = 1 when it has none.
