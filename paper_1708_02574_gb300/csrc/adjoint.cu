@@ -258,6 +258,7 @@ void set_edge_weights(tpa_graph *g, const float *w_any, cudaStream_t s, bool dro
     g->w_a.ensure((size_t)std::max<int64_t>(m, 1) * sizeof(float), s);
     g->inv_d.ensure((size_t)n * sizeof(double), s);
     if (m) copy_in(g->w_a.p, w_any, (size_t)m * sizeof(float), s);
+    ensure_perm_a2t(g, s);
     normalise_k<<<grid_for(n * 32), 256, 0, s>>>(g->rp_a.as<int64_t>(), g->w_a.as<float>(), g->perm_a2t.as<uint32_t>(),
                                                 n, g->val_a.as<float>(), g->val_t.as<float>(), g->inv_d.as<double>());
     note_launch("adjoint");

@@ -310,18 +310,36 @@ __global__ void run_lengths_k(const uint64_t *key, int64_t m, int32_t *count)
     }
 }
 
-// CSR(A~^T) columns and values from keys dst<<32|src; also the swapped keys src<<32|dst with index payload.
-__global__ void split_t_k(const uint64_t *key, int64_t m, const int32_t *outdeg, int32_t *col, float *val,
-                          uint64_t *swapped, uint32_t *idx)
+// CSR(A~^T) columns from keys dst<<32|src; also the swapped keys src<<32|dst.
+__global__ void split_t_k(const uint64_t *key, int64_t m, int32_t *col, uint64_t *swapped)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = key[i];
-        const uint32_t u = (uint32_t)k;
-        col[i] = (int32_t)u;
-        if (outdeg) val[i] = 1.0f / (float)outdeg[u];
-        if (swapped) {
-            swapped[i] = (k << 32) | (k >> 32);
-            idx[i] = (uint32_t)i;
+        col[i] = (int32_t)(uint32_t)k;
+        swapped[i] = (k << 32) | (k >> 32);
+    }
+}
+
+// perm[e] = position in CSR(A~^T) of CSR(A~) edge e = (u, v): row v of
+// CSR(A~^T) holds its sources once each, ascending, so u's place there is the
+// row start plus the count of smaller sources (a lower-bound search).  One
+// warp per row u of CSR(A~).
+__global__ void perm_a2t_k(const int64_t *rp_a, const int32_t *col_a, const int64_t *rp_t, const int32_t *col_t,
+                           int64_t n, uint32_t *perm)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const int64_t e1 = rp_a[u + 1];
+        for (int64_t e = rp_a[u] + lane; e < e1; e += 32) {
+            const int32_t v = __ldg(col_a + e);
+            int64_t lo = __ldg(rp_t + v), hi = __ldg(rp_t + v + 1);
+            while (lo < hi) {
+                const int64_t mid = lo + ((hi - lo) >> 1);
+                if (__ldg(col_t + mid) < (int32_t)u) lo = mid + 1;
+                else hi = mid;
+            }
+            perm[e] = (uint32_t)lo;
         }
     }
 }
@@ -371,7 +389,7 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
     const int64_t n = g->n;
     int nbits = 0;
     while (nbits < 31 && ((int64_t)1 << nbits) < n) ++nbits;
-    DevBuf ka, kb, hist, tmp, flags, pos, ia, ib, cnt;
+    DevBuf ka, kb, hist, tmp, flags, pos, cnt;
 
     // 1. validate ids
     {
@@ -429,7 +447,6 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
     pos.release(s);
 
     // 4. allocate the graph arrays
-    const size_t mb = (size_t)std::max<int64_t>(m, 1);
     const size_t mp = (size_t)csr_len(m);
     g->rp_t.ensure((size_t)(n + 1) * sizeof(int64_t), s);
     g->col_t.ensure(mp * sizeof(int32_t), s);
@@ -452,20 +469,17 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
     TPA_CHECK_LAUNCH();
     exclusive_scan<int32_t, int64_t>(cnt.as<int32_t>(), g->rp_t.as<int64_t>(), n, true, tmp, s);
 
-    // 6. columns of A~^T and swapped keys (src, dst) with their A~^T index
+    // 6. columns of A~^T and swapped keys (src, dst)
     uint64_t *sw = sorted;   // raw sorted keys are no longer needed
-    ia.ensure(mb * sizeof(uint32_t), s);
-    ib.ensure(mb * sizeof(uint32_t), s);
     if (m > 0) {
-        split_t_k<<<grid_for(m, 256), 256, 0, s>>>(uk, m, nullptr, g->col_t.as<int32_t>(), nullptr, sw,
-                                                   ia.as<uint32_t>());
+        split_t_k<<<grid_for(m, 256), 256, 0, s>>>(uk, m, g->col_t.as<int32_t>(), sw);
         note_launch("build");
     }
     TPA_CHECK_LAUNCH();
 
-    // 7. stable sort by source -> CSR(A~)
+    // 7. stable sort by source -> CSR(A~) (within a source, destinations stay ascending)
     std::vector<int> sh_src = digit_shifts(nbits, 32);
-    int cur2 = radix_sort(sw, uk, ia.as<uint32_t>(), ib.as<uint32_t>(), m, sh_src, hist, tmp, s);
+    int cur2 = radix_sort(sw, uk, nullptr, nullptr, m, sh_src, hist, tmp, s);
     uint64_t *ak = cur2 ? uk : sw;
     TPA_CUDA(cudaMemsetAsync(g->outdeg.p, 0, (size_t)n * sizeof(int32_t), s));
     if (m > 0) {
@@ -486,14 +500,23 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
         note_launch("build");
     }
     TPA_CHECK_LAUNCH();
-    // keep the payload of the source sort: for each CSR(A~) edge, its index in CSR(A~^T)
-    DevBuf &perm = cur2 ? ib : ia;
+    // the edge map between the two CSRs is built when edge weights first need it
     g->perm_a2t.release(s);
-    g->perm_a2t = perm;
-    perm.p = nullptr;
-    perm.bytes = 0;
     TPA_CUDA(cudaStreamSynchronize(s));
-    ka.release(s); kb.release(s); hist.release(s); tmp.release(s); ia.release(s); ib.release(s); cnt.release(s);
+    ka.release(s); kb.release(s); hist.release(s); tmp.release(s); cnt.release(s);
+}
+
+void ensure_perm_a2t(tpa_graph *g, cudaStream_t s)
+{
+    if (g->perm_a2t.p) return;
+    g->perm_a2t.ensure((size_t)std::max<int64_t>(g->m, 1) * sizeof(uint32_t), s);
+    if (g->m > 0) {
+        perm_a2t_k<<<grid_for(g->n * 32, 256), 256, 0, s>>>(g->rp_a.as<int64_t>(), g->col_a.as<int32_t>(),
+                                                            g->rp_t.as<int64_t>(), g->col_t.as<int32_t>(), g->n,
+                                                            g->perm_a2t.as<uint32_t>());
+        note_launch("build");
+    }
+    TPA_CHECK_LAUNCH();
 }
 
 void exclusive_scan_i32_i64(const int32_t *in, int64_t *out, int64_t len, DevBuf &tmp, cudaStream_t s)

@@ -168,7 +168,7 @@ struct tpa_graph {
     tpa::DevBuf rp_a, col_a, val_a;
     tpa::DevBuf outdeg;
     tpa::DevBuf inv_deg32;  // float[n] RN32(1/outdeg), 0 for deadends: the value of every edge out of a node
-    tpa::DevBuf perm_a2t;   // uint32[m]: position in CSR(A~^T) of each CSR(A~) edge
+    tpa::DevBuf perm_a2t;   // uint32[m]: position in CSR(A~^T) of each CSR(A~) edge (ensure_perm_a2t)
     // weighted graphs (tpa_set_edge_weights)
     tpa::DevBuf w_a;        // float[m] edge weights, CSR(A~) order
     tpa::DevBuf inv_d;      // double[n] 1 / weighted out-degree
@@ -206,6 +206,8 @@ struct Ctl {
 // build.cu
 void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t m_in,
                cudaStream_t s);
+// g->perm_a2t (position in CSR(A~^T) of each CSR(A~) edge), built on first use
+void ensure_perm_a2t(tpa_graph *g, cudaStream_t s);
 // out[0..len] = exclusive prefix sums of in[0..len) and the total (device arrays)
 void exclusive_scan_i32_i64(const int32_t *in, int64_t *out, int64_t len, DevBuf &tmp, cudaStream_t s);
 
