@@ -320,27 +320,12 @@ __global__ void split_t_k(const uint64_t *key, int64_t m, int32_t *col, uint64_t
     }
 }
 
-// perm[e] = position in CSR(A~^T) of CSR(A~) edge e = (u, v): row v of
-// CSR(A~^T) holds its sources once each, ascending, so u's place there is the
-// row start plus the count of smaller sources (a lower-bound search).  One
-// warp per row u of CSR(A~).
-__global__ void perm_a2t_k(const int64_t *rp_a, const int32_t *col_a, const int64_t *rp_t, const int32_t *col_t,
-                           int64_t n, uint32_t *perm)
+// Sort keys for the edge map: key[i] = source of CSR(A~^T) edge i, idx[i] = i.
+__global__ void src_keys_k(const int32_t *col_t, int64_t m, uint64_t *key, uint32_t *idx)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
-        const int64_t e1 = rp_a[u + 1];
-        for (int64_t e = rp_a[u] + lane; e < e1; e += 32) {
-            const int32_t v = __ldg(col_a + e);
-            int64_t lo = __ldg(rp_t + v), hi = __ldg(rp_t + v + 1);
-            while (lo < hi) {
-                const int64_t mid = lo + ((hi - lo) >> 1);
-                if (__ldg(col_t + mid) < (int32_t)u) lo = mid + 1;
-                else hi = mid;
-            }
-            perm[e] = (uint32_t)lo;
-        }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        key[i] = (uint64_t)(uint32_t)col_t[i];
+        idx[i] = (uint32_t)i;
     }
 }
 
@@ -509,14 +494,29 @@ void build_csr(tpa_graph *g, const int32_t *d_src, const int32_t *d_dst, int64_t
 void ensure_perm_a2t(tpa_graph *g, cudaStream_t s)
 {
     if (g->perm_a2t.p) return;
-    g->perm_a2t.ensure((size_t)std::max<int64_t>(g->m, 1) * sizeof(uint32_t), s);
-    if (g->m > 0) {
-        perm_a2t_k<<<grid_for(g->n * 32, 256), 256, 0, s>>>(g->rp_a.as<int64_t>(), g->col_a.as<int32_t>(),
-                                                            g->rp_t.as<int64_t>(), g->col_t.as<int32_t>(), g->n,
-                                                            g->perm_a2t.as<uint32_t>());
+    const int64_t n = g->n, m = g->m;
+    int nbits = 0;
+    while (nbits < 31 && ((int64_t)1 << nbits) < n) ++nbits;
+    // CSR(A~^T) lists the edges by (dst, src); a stable sort by src puts them
+    // in CSR(A~)'s (src, dst) order, carrying each edge's CSR(A~^T) index
+    DevBuf ka, kb, ia, ib, hist, tmp;
+    const size_t mb = (size_t)std::max<int64_t>(m, 1);
+    ka.ensure(mb * sizeof(uint64_t), s);
+    kb.ensure(mb * sizeof(uint64_t), s);
+    ia.ensure(mb * sizeof(uint32_t), s);
+    ib.ensure(mb * sizeof(uint32_t), s);
+    if (m > 0) {
+        src_keys_k<<<grid_for(m, 256), 256, 0, s>>>(g->col_t.as<int32_t>(), m, ka.as<uint64_t>(), ia.as<uint32_t>());
         note_launch("build");
     }
     TPA_CHECK_LAUNCH();
+    const int cur = radix_sort(ka.as<uint64_t>(), kb.as<uint64_t>(), ia.as<uint32_t>(), ib.as<uint32_t>(), m,
+                               digit_shifts(nbits, 0), hist, tmp, s);
+    DevBuf &perm = cur ? ib : ia;
+    g->perm_a2t = perm;
+    perm.p = nullptr;
+    perm.bytes = 0;
+    ka.release(s); kb.release(s); ia.release(s); ib.release(s); hist.release(s); tmp.release(s);
 }
 
 void exclusive_scan_i32_i64(const int32_t *in, int64_t *out, int64_t len, DevBuf &tmp, cudaStream_t s)
