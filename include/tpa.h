@@ -200,7 +200,9 @@ tpa_status tpa_cpi_step_noalloc(int64_t n, int64_t m, const int64_t *row_ptr, co
 /* Use weights w (float32[m], device or host, in CSR(A~) edge order as
  * returned by tpa_get_csr(g, 1, ...)).  Recomputes A~ in both CSR orders;
  * the previous preprocessing result is dropped (TPA_ESTATE until
- * tpa_preprocess runs again). */
+ * tpa_preprocess runs again).  The first call on a graph also builds, and
+ * keeps, the map from CSR(A~) edges to their CSR(A~^T) positions (uint32[m],
+ * allocated on `stream`). */
 tpa_status tpa_set_edge_weights(tpa_graph *g, const float *w, void *stream);
 
 /* w_e = exp(theta . f_e) for m edges with d <= 16 features (feat row-major
