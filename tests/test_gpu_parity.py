@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Bars (the benchmark spec): CSR bit-exact; every FP32 score vector within
+Bars: CSR bit-exact; every FP32 score vector within
 L1 <= 1e-5 and max-abs <= 1e-7 of the FP64 oracle, checked per result.
 Graphs: R-MAT scale 14 (16,384 nodes, edge factor 16, a/b/c/d = .57/.19/.19/.05,
 key 1) plus small named graphs; the merge-path tiles there span many tiles and
